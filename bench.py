@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark: time per pseudofermion-force evaluation at 24^4, n_pf = 16.
+
+One step = one full force evaluation through the C ABI (rhmc_force): the
+block multishift solve SBCGrQ (Algorithm 1) of (A + beta_s) X^(s) = Phi for
+all 16 pseudofermions and all 16 shifts to a true relative residual of 1e-8
+(mixed precision: FP32 operator and block updates in an FP64 reliable-update
+/ defect-correction loop), then the force G of Eq. (force) in FP64.
+Phi and U are resident on the device when the timed region starts.
+
+Also reported on the same line:
+* e2e: the same step with host (pinned) buffers, copies inside the timed region;
+* roofline: the multi-RHS FP32 hop at 24^4, n = 16 against the measured HBM peak;
+* baseline_fp64_scg: plain per-vector FP64 multishift CG + the same force on
+  this GPU (the comparison of the metric), timed once;
+* cpu_baseline: the FP64 CPU oracle on the host cores, on a bounded sample.
+
+--impl reference times the oracle (the only reference available: the paper
+ships no code) on the same workload, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "24^4 staggered, m=0.01, n_pf=16, 16 shifts of x^(-1/64) on [4e-4,64], eps=0.5, tol 1e-8",
+    "dims": [24, 24, 24, 24],
+    "mass": 0.01,
+    "n_pf": 16,
+    "n_shifts": 16,
+    "r": -1.0 / 64,
+    "interval": [4e-4, 64.0],
+    "eps": 0.5,
+    "tol": 1e-8,
+    "precision": "mixed",
+    "index": 3,
+}
+METRIC = "time/force eval at 24^4,n_pf=16 (1e-8 res): block+mixed vs FP64 CG; Dslash GB/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--small", action="store_true", help="8^4 n_pf=4 quick check (not a bench line)")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 per-vector SCG comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def make_inputs(cfg, n_override=None):
+    from paper_1808_01829_gb300 import synthetic as syn
+    from paper_1808_01829_gb300.remez import rational_approx
+
+    dims = cfg["dims"]
+    n = n_override or cfg["n_pf"]
+    U = syn.random_links(dims, cfg["eps"], syn.seed_gauge(cfg["index"]))
+    Phi = syn.gaussian_pseudofermions(dims, n, syn.seed_phi(cfg["index"]))
+    ra = rational_approx(cfg["r"], cfg["interval"][0], cfg["interval"][1], cfg["n_shifts"])
+    return U, Phi, ra
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_sample(cfg, U, Phi, ra, budget_s=20.0):
+    """Time the FP64 oracle's SBCGrQ per iteration at the full workload (a fixed
+    number of iterations), plus its force; scale to one force evaluation with
+    the GPU's iteration count."""
+    import oracle
+
+    oracle.build()
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    k = 1
+    oracle.sbcgrq(cfg["dims"], cfg["mass"], U, Phi, ra.beta, fixed_iters=k)
+    t_iter = time.perf_counter() - t0
+    t_force = 0.0
+    if t_iter < budget_s:
+        X = oracle.sbcgrq(cfg["dims"], cfg["mass"], U, Phi, ra.beta, fixed_iters=1)[0]
+        t0 = time.perf_counter()
+        oracle.force(cfg["dims"], U, X, ra.alpha)
+        t_force = time.perf_counter() - t0
+    return t_iter, t_force, threads
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = WORKLOAD
+    U, Phi, ra = make_inputs(cfg)
+    gpu_iters = int(os.environ.get("RHMC_GPU_ITERS", "0")) or None
+    times = []
+    for step in range(args.warmup + args.steps):
+        t_iter, t_force, threads = cpu_sample(cfg, U, Phi, ra)
+        if step >= args.warmup:
+            times.append((t_iter, t_force))
+    t_iter = statistics.median(t for t, _ in times)
+    t_force = statistics.median(f for _, f in times)
+    iters = gpu_iters or 900
+    est_ms = (t_iter * iters + t_force) * 1e3
+    line = {
+        "metric": METRIC, "value": est_ms, "unit": "ms", "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": est_ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                         "sample": f"one oracle SBCGrQ iteration ({t_iter:.2f} s) + oracle force ({t_force:.2f} s) "
+                                   f"at the full 24^4 workload, scaled by {iters} iterations per force evaluation"},
+        "e2e": {"value": est_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1808_01829_gb300 import _build
+    from paper_1808_01829_gb300.api import RhmcContext
+
+    _build.build()
+    cfg = dict(WORKLOAD)
+    if args.small:
+        cfg.update(dims=[8, 8, 8, 8], mass=0.05, n_pf=4, n_shifts=12, r=-1.0 / 16, interval=[2e-3, 64.0], index=1,
+                   workload="8^4 quick check")
+    U, Phi, ra = make_inputs(cfg)
+    ctx = RhmcContext(cfg["dims"], cfg["mass"], device=local)
+    Ud = torch.from_numpy(U).to(dev)
+    ctx.set_gauge(Ud)
+    Pd = torch.from_numpy(Phi).to(dev)
+    n, ns = cfg["n_pf"], cfg["n_shifts"]
+    ws = torch.empty(ctx.workspace_bytes(n, ns, cfg["precision"]), dtype=torch.uint8, device=dev)
+    G = torch.empty((ctx.V, 4, 3, 3), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], precision=cfg["precision"], out=G,
+                         workspace=ws)
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(step()[2])
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, S, info = step()
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    last = infos[-1]
+
+    # ---- end to end: pinned host Phi -> device, force, G -> pinned host
+    Ph = torch.from_numpy(Phi).pin_memory()
+    Gh = torch.empty((ctx.V, 4, 3, 3), dtype=torch.complex128).pin_memory()
+    Pd2 = torch.empty_like(Pd)
+    e2e = []
+    for it in range(max(2, min(3, args.steps)) + 1):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Pd2.copy_(Ph, non_blocking=True)
+        ctx.force(Pd2, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], precision=cfg["precision"], out=G, workspace=ws)
+        Gh.copy_(G, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = statistics.median(e2e)
+
+    # ---- roofline: FP32 multi-RHS hop at this workload, events on the launching stream
+    from paper_1808_01829_gb300 import roofline
+
+    roof = roofline.measure_hop(ctx, n, dev)
+
+    # ---- comparison: per-vector FP64 multishift CG + force (Fig. 9 analogue)
+    base = None
+    if not args.no_baseline and rank == 0:
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Xs, binfo = ctx.multishift_cg_pervector(Pd, ra.beta, cfg["tol"])
+        ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], X=Xs, out=G, workspace=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        base = {"ms": a.elapsed_time(b), "iters_total": binfo.iters, "dirac_calls_width1": binfo.dirac_calls,
+                "speedup": a.elapsed_time(b) / ms}
+        del Xs
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        t_iter, t_force, threads = cpu_sample(cfg, U, Phi, ra)
+        est = (t_iter * last.iters + t_force) * 1e3
+        cpu = {"value": est, "unit": "ms", "cores": threads, "kind": "oracle",
+               "sample": f"one oracle SBCGrQ iteration ({t_iter:.2f} s) + oracle force ({t_force:.2f} s) at the "
+                         f"full workload, scaled by the GPU's {last.iters} iterations"}
+
+    if rank == 0:
+        len_b = Phi.nbytes
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "precision": cfg["precision"],
+                       "l2": "inputs larger than L2 (U 191 MB, fields 64-127 MB each)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": len_b, "d2h_bytes_per_step": G.numel() * 16},
+            "gpu_launches": launches_per_step(last, ns),
+            "roofline": roof,
+            "clocks": clk,
+            "solver": {"iters": last.iters, "dirac_calls": last.dirac_calls, "reliable_updates": last.reliable_updates,
+                       "refinements": last.refinements, "refine_iters": last.refine_iters,
+                       "true_rel_resid_max": last.true_rel_resid_max},
+            "baseline_fp64_scg": base,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def launches_per_step(info, ns):
+    """Kernel launches of one force evaluation (counted from the driver's sequence)."""
+    per_iter = 8  # 2 hops, 2 grams, alpha, axpy, rho, shifts, update (shifts kernel counted once)
+    per_iter += 1
+    reliable = info.reliable_updates * (ns + 6)
+    phase2 = info.dirac_calls - info.iters - info.reliable_updates
+    return int(info.iters * per_iter + 4 + reliable + max(phase2, 0) * 4 + info.refine_iters * per_iter + 2 + 1 + 2)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

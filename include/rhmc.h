@@ -1,0 +1,171 @@
+/*
+ * rhmc.h -- C ABI of the GB300 block multishift RHMC library (librhmc.so).
+ *
+ * The library implements the hot path of de Forcrand & Keegan, "Rational
+ * Hybrid Monte Carlo with Block Solvers and Multiple Pseudofermions"
+ * (arXiv:1808.01829):
+ *   - the even-odd preconditioned unimproved staggered operator
+ *     A = M^dagger M on even sites (Sec. IV), applied to a block of
+ *     right-hand sides that shares each gauge-link load ("pencil", Sec. III
+ *     and the conclusions);
+ *   - the block multishift solver SBCGrQ (Algorithm 1) for
+ *     (A + sigma_s) X^(s) = B, all right-hand sides and all shifts at once;
+ *   - the pseudofermion action and force of Eqs. (RA) and (force).
+ *
+ * Conventions (all calls):
+ *   Lattice    dims = {Lx, Ly, Lz, Lt}, all even and >= 2; site lex index
+ *              x + Lx*(y + Ly*(z + Lz*t)).  Even sites have x+y+z+t even;
+ *              a site's rank among its parity is lex/2.
+ *   Operator   M = 2m + D,
+ *              (D psi)(x) = sum_mu eta_mu(x) [b_mu(x) U_mu(x) psi(x+mu)
+ *                                   - b_mu(x-mu) U_mu(x-mu)^dagger psi(x-mu)],
+ *              eta_mu(x) = (-1)^(x_0+...+x_{mu-1}), b = -1 on t-links that
+ *              wrap Lt-1 -> 0 when bc_t = -1 (antiperiodic), else +1.
+ *              A = 4 m^2 - D_eo D_oe; its spectrum lies in [4m^2, 4m^2+64].
+ *   Gauge U    device, complex128 (interleaved re,im doubles),
+ *              [Lt][Lz][Ly][Lx][mu=0..3][3][3].
+ *   Fields     device, complex128 [V/2][3][n]: one parity, the n right-hand
+ *              sides fastest.  Shifted solutions are [n_shifts][V/2][3][n].
+ *   Force G    device, complex128 [V][4][3][3], G = dS/dRe U + i dS/dIm U.
+ *   Streams    rhmc_stream_t is a cudaStream_t (NULL = legacy default).
+ *              Work is enqueued on that stream; calls that return solver
+ *              information (info, S_out) synchronise the stream first.
+ *   Ownership  the caller owns every buffer it passes.  The context owns its
+ *              staged copy of the gauge field and an internal scratch pool
+ *              (used when a call's `workspace` is NULL).  No call retains a
+ *              caller pointer after it returns.
+ *   Errors     every call returns an rhmc_status_t; no exception crosses the
+ *              ABI.  rhmc_last_error() gives a thread-local message for the
+ *              last failing call of the thread.
+ *   Threads    a context may be used by one host thread at a time.
+ */
+#ifndef RHMC_H
+#define RHMC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rhmc_ctx rhmc_ctx_t;
+typedef void *rhmc_stream_t; /* cudaStream_t */
+
+typedef enum {
+  RHMC_OK = 0,
+  RHMC_ERR_INVALID_ARG = 1,    /* null pointer, odd extent, n out of range, bad shifts/tol */
+  RHMC_ERR_NOT_CONVERGED = 2,  /* max_iter reached; results and info are still written */
+  RHMC_ERR_BREAKDOWN = 3,      /* non-positive-definite Gram matrix / non-finite coefficients */
+  RHMC_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  RHMC_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait expired */
+  RHMC_ERR_NO_GAUGE = 6        /* rhmc_set_gauge has not been called */
+} rhmc_status_t;
+
+typedef struct {
+  int dims[4];  /* Lx, Ly, Lz, Lt: even, >= 2 */
+  double mass;  /* m in M = 2m + D */
+  int bc_t;     /* -1 antiperiodic in t (default), +1 periodic */
+} rhmc_lattice_t;
+
+typedef enum {
+  RHMC_FP64 = 0,       /* everything in FP64 */
+  RHMC_MIXED_FP32 = 1  /* FP32 operator and block updates inside an FP64
+                          reliable-update / defect-correction loop; FP64 n x n
+                          coefficient algebra, true residuals and force */
+} rhmc_precision_t;
+
+/* Largest number of right-hand sides per block (n_pf). */
+#define RHMC_MAX_NRHS 16
+/* Largest number of shifts per solve. */
+#define RHMC_MAX_SHIFTS 64
+
+typedef struct {
+  int iters;                 /* SBCGrQ iterations of the main solve */
+  int dirac_calls;           /* applications of A to an n-wide block, all phases */
+  int reliable_updates;      /* FP64 residual replacements (mixed precision) */
+  int refinements;           /* per-shift defect-correction solves */
+  int refine_iters;          /* iterations spent in them */
+  double true_rel_resid_max; /* max_{s,j} ||B e_j - (A+sigma_s) X^(s) e_j|| / ||B e_j||, FP64 */
+  double *per_shift_resid;   /* optional caller array [n_shifts*n_rhs] (shift-major), or NULL */
+} rhmc_info_t;
+
+/* Create a context on CUDA device `device` for lattice `lat`.
+ * INVALID_ARG if an extent is odd or < 2, or lat/ctx is NULL. */
+rhmc_status_t rhmc_create(rhmc_ctx_t **ctx, const rhmc_lattice_t *lat, int device);
+
+/* Release the context and everything it allocated. NULL is accepted. */
+rhmc_status_t rhmc_destroy(rhmc_ctx_t *ctx);
+
+/* Stage the gauge field (Sec. IV's links U_mu(x)) into the context's internal
+ * FP64 and FP32 link arrays, phases and boundary signs folded in.  U is read
+ * on stream s and not retained; the call returns after staging completes. */
+rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *ctx, const void *U_dev, rhmc_stream_t s);
+
+/* Bytes of device workspace that rhmc_block_multishift_cg / rhmc_force need
+ * for this problem size; 0 on invalid arguments. */
+size_t rhmc_workspace_bytes(const rhmc_ctx_t *ctx, int n_rhs, int n_shifts, rhmc_precision_t p);
+
+/* Y = (A + sigma) X for an n_rhs-wide block (multi-RHS operator, each link
+ * loaded once for all right-hand sides; Sec. IV, Fig. 8 top).  X, Y complex128
+ * [V/2][3][n_rhs], may not alias.  p = RHMC_MIXED_FP32 evaluates the FP32
+ * kernel (input rounded to FP32, result widened).  1 <= n_rhs <= RHMC_MAX_NRHS. */
+rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, double sigma,
+                                    rhmc_precision_t p, rhmc_stream_t s);
+
+/* One staggered hop Y = D X onto parity out_parity (0: D_eo, input odd;
+ * 1: D_oe, input even).  Same layouts and precision rule as above. */
+rhmc_status_t rhmc_hop(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, int out_parity,
+                       rhmc_precision_t p, rhmc_stream_t s);
+
+/* SBCGrQ (Algorithm 1): solve (A + sigma_s) X^(s) = B for every shift.
+ *   B         complex128 [V/2][3][n_rhs], columns linearly independent
+ *   shifts    host array [n_shifts], each >= 0; solved in ascending order,
+ *             the smallest drives the Krylov space (sigma_0)
+ *   X         complex128 [n_shifts][V/2][3][n_rhs], in the caller's shift order
+ *   tol       relative residual target per column and shift (> 0)
+ *   max_iter  iteration cap of the main solve (<= 0: 10 sqrt(64/4m^2) ln(1/tol))
+ *   workspace device buffer of rhmc_workspace_bytes() bytes, or NULL to use
+ *             the context's pool
+ *   info      optional; filled after a stream synchronise
+ * Returns OK once every (shift, column) true FP64 residual is <= tol,
+ * NOT_CONVERGED otherwise (X still written), BREAKDOWN on a singular block. */
+rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *ctx, const void *B_dev, int n_rhs, int n_shifts,
+                                       const double *shifts, void *X_dev, double tol, int max_iter,
+                                       rhmc_precision_t p, void *workspace, rhmc_info_t *info, rhmc_stream_t s);
+
+/* Baseline: plain per-vector FP64 multishift CG (SCG, Sec. III), one
+ * right-hand side at a time with a width-1 operator.  Same arguments and
+ * output as rhmc_block_multishift_cg with p = RHMC_FP64. */
+rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *ctx, const void *B_dev, int n_rhs, int n_shifts,
+                                           const double *shifts, void *X_dev, double tol, int max_iter,
+                                           void *workspace, rhmc_info_t *info, rhmc_stream_t s);
+
+/* Pseudofermion action and force for n_pf pseudofermions Phi (Eqs. (RA),
+ * (force)):  S = sum_i [alpha0 |phi_i|^2 + sum_s alpha_s phi_i^dagger X^(s) e_i],
+ *   G_mu(x) = dS/dRe U_mu(x) + i dS/dIm U_mu(x)
+ *           = 2 eps(x) eta_mu(x) b_mu(x) sum_{s,i} alpha_s W_si(x) W_si(x+mu)^dagger,
+ * W = X^(s) on even sites, D_oe X^(s) on odd sites, eps = +1 even / -1 odd.
+ *   Phi       complex128 [V/2][3][n_pf]
+ *   alpha, beta  host [n_shifts]: residues and poles of Eq. (RA), beta > 0
+ *   X_in      optional complex128 [n_shifts][V/2][3][n_pf] solutions of
+ *             (A + beta_s) X = Phi; NULL = solve them (block solver, tol, p)
+ *   G         complex128 [V][4][3][3] output
+ *   S_out     optional host double, the action
+ * The force arithmetic is FP64 in both precision modes. */
+rhmc_status_t rhmc_force(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
+                         const double *beta, int n_shifts, double tol, int max_iter, rhmc_precision_t p,
+                         const void *X_in_dev, void *G_dev, double *S_out, void *workspace, rhmc_info_t *info,
+                         rhmc_stream_t s);
+
+/* Thread-local message describing the last failing call ("" if none). */
+const char *rhmc_last_error(void);
+
+/* Running count of kernels this library has launched in the process (all
+ * contexts and threads); differences around a call count its launches. */
+long long rhmc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHMC_H */

@@ -1,0 +1,100 @@
+"""ctypes binding of librhmc.so (include/rhmc.h).  Argument marshalling only.
+
+There is no fallback: if the shared library is missing or CUDA is not
+available, loading raises.  Build it with ``paper_1808_01829_gb300._build.build()``
+(``__graft_entry__.build()`` does so).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librhmc.so")
+
+RHMC_FP64 = 0
+RHMC_MIXED_FP32 = 1
+RHMC_MAX_NRHS = 16
+RHMC_MAX_SHIFTS = 64
+
+STATUS = {
+    0: "OK",
+    1: "INVALID_ARG",
+    2: "NOT_CONVERGED",
+    3: "BREAKDOWN",
+    4: "CUDA_ERROR",
+    5: "DEVICE_TIMEOUT",
+    6: "NO_GAUGE",
+}
+
+
+class RhmcError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("mass", ctypes.c_double), ("bc_t", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("dirac_calls", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("refinements", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
+        ("true_rel_resid_max", ctypes.c_double),
+        ("per_shift_resid", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load librhmc.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built; run paper_1808_01829_gb300._build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        PD = ctypes.POINTER(ctypes.c_double)
+        lib.rhmc_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Lattice), I]
+        lib.rhmc_destroy.argtypes = [P]
+        lib.rhmc_set_gauge.argtypes = [P, P, P]
+        lib.rhmc_workspace_bytes.argtypes = [P, I, I, I]
+        lib.rhmc_workspace_bytes.restype = S
+        lib.rhmc_apply_mdagm_mrhs.argtypes = [P, P, P, I, D, I, P]
+        lib.rhmc_hop.argtypes = [P, P, P, I, I, I, P]
+        lib.rhmc_block_multishift_cg.argtypes = [P, P, I, I, PD, P, D, I, I, P, ctypes.POINTER(Info), P]
+        lib.rhmc_multishift_cg_pervector.argtypes = [P, P, I, I, PD, P, D, I, P, ctypes.POINTER(Info), P]
+        lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
+        lib.rhmc_last_error.restype = ctypes.c_char_p
+        lib.rhmc_kernel_launches.restype = ctypes.c_longlong
+        for name in ("rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_apply_mdagm_mrhs", "rhmc_hop",
+                     "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force"):
+            getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def check(rc: int, where: str, allow=()):
+    if rc != 0 and rc not in allow:
+        msg = load().rhmc_last_error().decode(errors="replace")
+        raise RhmcError(rc, where, msg)
+    return rc
+
+
+def exported_symbols():
+    """Names declared in include/rhmc.h that the library must export."""
+    return [
+        "rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_workspace_bytes", "rhmc_apply_mdagm_mrhs",
+        "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
+    ]

@@ -1,0 +1,819 @@
+// C ABI entry points and the host-side solver driver.
+//
+// rhmc_block_multishift_cg runs SBCGrQ (Algorithm 1) for all right-hand sides
+// and shifts at once.  Per iteration k (device work only, no host round trip):
+//   AP = (A + sigma_0) P^(0)                      two hops, axpy fused   (line 4)
+//   Gram1 = P^(0)dagger AP -> alpha_k            gram + n x n kernel     (line 4)
+//   W = Q_{k-1} - AP alpha_k                      block axpy             (line 5)
+//   Gram2 = W^dagger W -> rho_k (Cholesky QR), base and shifted
+//   coefficients                                  gram + n x n kernels   (lines 5-10)
+//   Q_k = W rho_k^-1; for every live shift
+//   X^(s) += P^(s) M1^(s), P^(s) = Q_k + P^(s) M2^(s)   one fused pass   (lines 6-7, 11-12)
+// The host reads the residual estimates every few iterations to decide on
+// convergence (and, in mixed precision, on reliable updates).
+//
+// Mixed precision (RHMC_MIXED_FP32): the fields P, Q, W, AP and the solution
+// increments are FP32; the n x n algebra is FP64.  When the base residual
+// has dropped by kReliableDelta since the last reliable update, the FP32
+// solution increments are added into the FP64 solutions, the base residual
+// B - (A + sigma_0) X^(0) is recomputed with the FP64 operator and its thin
+// QR replaces (Q_k, delta_k).  After the loop every shift's true residual is
+// evaluated in FP64; a shift above tol gets a defect-correction solve
+// (A + sigma_s) E = R^(s) with the same machinery, X^(s) += E.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "scg.h"
+
+namespace rhmc {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define RHMC_TRY(...)                   \
+  do {                                  \
+    rhmc_status_t st_ = (__VA_ARGS__);  \
+    if (st_ != RHMC_OK) return st_;     \
+  } while (0)
+
+constexpr int kParts = 304;           // Gram partial sums (2 CTAs per SM)
+constexpr double kReliableDelta = 0.1;
+constexpr int kCheckEvery = 8;        // iterations between host checks
+constexpr int kMaxRefine = 4;
+
+// Bump allocator over a device buffer; with base == nullptr it only measures.
+struct Arena {
+  char *base;
+  size_t off = 0;
+  explicit Arena(void *b) : base((char *)b) {}
+  template <typename T> T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace rhmc
+
+using namespace rhmc;
+
+struct rhmc_ctx {
+  int device = 0;
+  Geom g{};
+  double mass = 0;
+  int bc_t = -1;
+  double2 *l64[2] = {nullptr, nullptr};
+  float2 *l32[2] = {nullptr, nullptr};
+  bool have_gauge = false;
+  void *pool = nullptr;
+  size_t pool_bytes = 0;
+  double *h_pin = nullptr;  // pinned host staging (readbacks)
+  size_t h_pin_bytes = 0;
+};
+
+namespace rhmc {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static rhmc_status_t ensure_pool(rhmc_ctx *c, size_t bytes) {
+  if (c->pool_bytes >= bytes) return RHMC_OK;
+  if (c->pool) {
+    RHMC_CUDA_TRY(cudaDeviceSynchronize());
+    RHMC_CUDA_TRY(cudaFree(c->pool));
+    c->pool = nullptr;
+    c->pool_bytes = 0;
+  }
+  RHMC_CUDA_TRY(cudaMalloc(&c->pool, bytes));
+  c->pool_bytes = bytes;
+  return RHMC_OK;
+}
+
+static rhmc_status_t ensure_pinned(rhmc_ctx *c, size_t bytes) {
+  if (c->h_pin_bytes >= bytes) return RHMC_OK;
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  c->h_pin = nullptr;
+  RHMC_CUDA_TRY(cudaMallocHost(&c->h_pin, bytes));
+  c->h_pin_bytes = bytes;
+  return RHMC_OK;
+}
+
+// ------------------------------------------------------------ operator helpers
+template <typename T> struct LinksOf;
+template <> struct LinksOf<float> {
+  static const float2 *get(const rhmc_ctx *c, int p) { return c->l32[p]; }
+};
+template <> struct LinksOf<double> {
+  static const double2 *get(const rhmc_ctx *c, int p) { return c->l64[p]; }
+};
+
+// Y = (A + sigma) X, tmp: odd-parity field of the same width.
+template <typename T>
+static rhmc_status_t apply_A(const rhmc_ctx *c, const C<T> *X, C<T> *Y, C<T> *tmp, int n, double sigma,
+                             cudaStream_t s) {
+  RHMC_TRY(hop<T>(c->g, 1, LinksOf<T>::get(c, 1), X, tmp, nullptr, 0.0, n, 1, 0, s));
+  RHMC_TRY(hop<T>(c->g, 0, LinksOf<T>::get(c, 0), tmp, Y, X, 4.0 * c->mass * c->mass + sigma, n, 1, 0, s));
+  return RHMC_OK;
+}
+
+// ------------------------------------------------------------ solver workspace
+struct SolveBufs {
+  // precision-specific fields (T = float or double)
+  void *P, *Q, *W, *AP, *Todd, *Xinc;  // Xinc: FP32 increments (mixed only)
+  void *coef, *mw;
+  // FP64 helpers
+  double2 *R64, *T64, *AP64, *rinv64;
+  double2 *partial;
+  double *npart;
+  SolverState *st;
+};
+
+static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, SolveBufs &b) {
+  const size_t len = (size_t)g.Vh * 3 * n;
+  const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
+  auto field = [&](size_t count) { return (void *)a.take<char>(count * len * esz); };
+  b.P = field(ns);
+  b.Q = field(1);
+  b.W = field(1);
+  b.AP = field(1);
+  b.Todd = field(1);
+  b.Xinc = mixed ? field(ns) : nullptr;
+  b.coef = a.take<char>((size_t)(1 + 2 * ns) * n * n * esz);
+  b.mw = a.take<char>((size_t)n * n * esz);
+  b.R64 = a.take<double2>(len);
+  b.T64 = a.take<double2>(len);
+  b.AP64 = a.take<double2>(len);
+  b.rinv64 = a.take<double2>((size_t)n * n);
+  b.partial = a.take<double2>((size_t)kParts * n * n);
+  b.npart = a.take<double>((size_t)kParts * kMaxN);
+  b.st = a.take<SolverState>(1);
+}
+
+// Phase-2 buffers live above the (dead) phase-1 buffers of the top-level solve.
+struct RefineBufs {
+  double2 *Bref, *E;
+};
+
+static size_t solve_bytes(const Geom &g, int n, int ns, bool mixed, bool own_X) {
+  Arena a(nullptr);
+  if (own_X) a.take<double2>((size_t)ns * g.Vh * 3 * n);
+  SolveBufs b;
+  layout_solve(a, g, n, ns, mixed, b);
+  // refinement: Bref, E, plus a single-shift solve
+  Arena r(nullptr);
+  if (own_X) r.take<double2>((size_t)ns * g.Vh * 3 * n);
+  r.take<double2>((size_t)g.Vh * 3 * n);
+  r.take<double2>((size_t)g.Vh * 3 * n);
+  SolveBufs b1;
+  layout_solve(r, g, n, 1, mixed, b1);
+  return std::max(a.off, r.off) + 256;
+}
+
+struct SolveParams {
+  double tol;
+  int max_iter;
+  bool mixed;
+  int fixed_iters;  // > 0: exactly this many iterations, no freezing, no checks
+};
+
+struct SolveStats {
+  int iters = 0, dirac = 0, reliable = 0;
+};
+
+// Column norms squared of an FP64 block (host result, n entries).
+static rhmc_status_t colnorms(rhmc_ctx *c, const double2 *A, int n, double *out, double *npart, cudaStream_t s) {
+  const long rows = c->g.Vh * 3;
+  RHMC_TRY(colnorm2<double>(A, rows, n, npart, kParts, s));
+  RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts * kMaxN));
+  RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, npart, sizeof(double) * kParts * n, cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int j = 0; j < n; ++j) {
+    double t = 0;
+    for (int p = 0; p < kParts; ++p) t += c->h_pin[p * n + j];
+    out[j] = t;
+  }
+  return RHMC_OK;
+}
+
+struct StateView {
+  double res[kMaxS][kMaxN];
+  int active[kMaxS];
+  int breakdown;
+};
+
+static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cudaStream_t s) {
+  RHMC_TRY(ensure_pinned(c, sizeof(StateView) + 64));
+  StateView *h = reinterpret_cast<StateView *>(c->h_pin);
+  RHMC_CUDA_TRY(cudaMemcpyAsync(h->res, st->res, sizeof(v.res), cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaMemcpyAsync(h->active, st->active, sizeof(v.active), cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaMemcpyAsync(&h->breakdown, &st->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(&v, h, sizeof(StateView));
+  return RHMC_OK;
+}
+
+// One SBCGrQ iteration (device work only).
+template <typename T, typename TX>
+static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc, int n, int ns, double sigma0, int k,
+                                      double tol_shift, int freeze, cudaStream_t s) {
+  const long rows = c->g.Vh * 3;
+  const long len = rows * n;
+  C<T> *P = (C<T> *)b.P, *Q = (C<T> *)b.Q, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
+  RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
+  RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kParts, s));
+  RHMC_TRY(nxn_alpha<T>(b.partial, kParts, n, b.st, k, (C<T> *)b.mw, s));
+  RHMC_TRY(block_axpy<T, T>(AP, Q, (const C<T> *)b.mw, W, rows, n, s));
+  RHMC_TRY(gram<T>(W, W, rows, n, b.partial, kParts, s));
+  RHMC_TRY(nxn_rho<T>(b.partial, kParts, n, b.st, k, (C<T> *)b.coef, s));
+  RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, s));
+  RHMC_TRY(update_all<T, TX>(W, Q, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, ns, rows, n, len, s));
+  return RHMC_OK;
+}
+
+// Core solve of (A + sigma_s) X^(s) = B, shifts ascending, X FP64 [ns][len].
+// Returns OK when the recursive residuals reached the target (phase 1 only).
+template <typename T>
+static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, const double *shifts, double2 *X,
+                                  const SolveParams &prm, const SolveBufs &b, SolveStats &stats, cudaStream_t s) {
+  const bool mixed = std::is_same<T, float>::value;
+  const long rows = c->g.Vh * 3;
+  const long len = rows * n;
+  const double sigma0 = shifts[0];
+  RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * ns, s));
+  // line 2: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
+  RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kParts, s));
+  RHMC_TRY(nxn_qr_init<double>(b.partial, kParts, n, ns, b.st, b.rinv64, s));
+  RHMC_TRY(block_axpy<double, T>(B, nullptr, b.rinv64, (C<T> *)b.Q, rows, n, s));
+  for (int q = 0; q < ns; ++q)
+    RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Q, sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
+  if (mixed) RHMC_CUDA_TRY(cudaMemsetAsync(b.Xinc, 0, sizeof(float2) * len * ns, s));
+  StateView v;
+  RHMC_TRY(read_state(c, b.st, v, s));
+  if (v.breakdown) {
+    set_error("breakdown: right-hand-side block is rank deficient");
+    return RHMC_ERR_BREAKDOWN;
+  }
+  const double target = prm.tol;
+  double res_at_reliable = 1.0;
+  int k = 0;
+  const int kmax = prm.fixed_iters > 0 ? prm.fixed_iters : prm.max_iter;
+  while (k < kmax) {
+    const int chunk = prm.fixed_iters > 0 ? kmax : std::min(kCheckEvery, kmax - k);
+    for (int q = 0; q < chunk; ++q) {
+      ++k;
+      if (mixed)
+        RHMC_TRY((sbcgrq_iteration<float, float>(c, b, (float *)b.Xinc, n, ns, sigma0, k, target,
+                                                  prm.fixed_iters > 0 ? 0 : 1, s)));
+      else
+        RHMC_TRY((sbcgrq_iteration<double, double>(c, b, (double *)X, n, ns, sigma0, k, target,
+                                                    prm.fixed_iters > 0 ? 0 : 1, s)));
+      stats.dirac++;
+    }
+    RHMC_TRY(read_state(c, b.st, v, s));
+    if (v.breakdown) {
+      set_error("breakdown in coefficient step %d at iteration %d", v.breakdown, k);
+      stats.iters = k;
+      return RHMC_ERR_BREAKDOWN;
+    }
+    if (prm.fixed_iters > 0) break;
+    double base = 0.0;
+    for (int j = 0; j < n; ++j) base = std::max(base, v.res[0][j]);
+    if (!std::isfinite(base)) {
+      set_error("non-finite residual at iteration %d", k);
+      stats.iters = k;
+      return RHMC_ERR_BREAKDOWN;
+    }
+    bool shifts_done = true;
+    for (int q = 1; q < ns; ++q) shifts_done = shifts_done && !v.active[q];
+    const bool converged = base < target && shifts_done;
+    if (mixed && (base < kReliableDelta * res_at_reliable || converged)) {
+      // reliable update: flush FP32 increments, FP64 true base residual, re-QR
+      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      RHMC_TRY(apply_A<double>(c, X, b.AP64, b.T64, n, sigma0, s));
+      RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
+      RHMC_TRY(gram<double>(b.R64, b.R64, rows, n, b.partial, kParts, s));
+      RHMC_TRY(nxn_reliable(b.partial, kParts, n, b.st, k, b.rinv64, s));
+      RHMC_TRY(block_axpy<double, float>(b.R64, nullptr, b.rinv64, (float2 *)b.Q, rows, n, s));
+      stats.dirac++;
+      stats.reliable++;
+      RHMC_TRY(read_state(c, b.st, v, s));
+      if (v.breakdown) {
+        // the true residual is numerically zero: every column has converged
+        stats.iters = k;
+        return RHMC_OK;
+      }
+      base = 0.0;
+      for (int j = 0; j < n; ++j) base = std::max(base, v.res[0][j]);
+      res_at_reliable = base;
+      if (base < target && shifts_done) {
+        stats.iters = k;
+        return RHMC_OK;
+      }
+      continue;
+    }
+    if (converged) {
+      stats.iters = k;
+      return RHMC_OK;
+    }
+  }
+  if (mixed)
+    for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+  stats.iters = k;
+  if (prm.fixed_iters > 0) return RHMC_OK;
+  set_error("not converged after %d iterations", k);
+  return RHMC_ERR_NOT_CONVERGED;
+}
+
+// Full solve with FP64 true residuals and per-shift defect correction.
+static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, const double *shifts, double2 *X,
+                               const SolveParams &prm, void *ws, rhmc_info_t *info, cudaStream_t s) {
+  const long rows = c->g.Vh * 3;
+  const long len = rows * n;
+  Arena a(ws);
+  SolveBufs b;
+  layout_solve(a, c->g, n, ns, prm.mixed, b);
+  SolveStats st;
+  SolveParams p1 = prm;
+  if (prm.fixed_iters <= 0) p1.tol = 0.5 * prm.tol;
+  rhmc_status_t rc = prm.mixed ? solve_phase1<float>(c, B, n, ns, shifts, X, p1, b, st, s)
+                               : solve_phase1<double>(c, B, n, ns, shifts, X, p1, b, st, s);
+  if (rc != RHMC_OK && rc != RHMC_ERR_NOT_CONVERGED) return rc;
+  const rhmc_status_t rc1 = rc;
+  // phase 2: FP64 true residual per shift, defect correction where needed
+  Arena ra(ws);
+  RefineBufs rb;
+  rb.Bref = ra.take<double2>(len);
+  rb.E = ra.take<double2>(len);
+  SolveBufs b1;
+  layout_solve(ra, c->g, n, 1, prm.mixed, b1);
+  // b1 overlaps b: phase-1 buffers are dead from here on.  The residual
+  // evaluation uses b1's FP64 helpers.
+  double bn[kMaxN];
+  RHMC_TRY(colnorms(c, B, n, bn, b1.npart, s));
+  for (int j = 0; j < n; ++j) bn[j] = std::sqrt(bn[j]);
+  int refinements = 0, refine_iters = 0;
+  double worst = 0.0;
+  std::vector<double> resid((size_t)ns * n, 0.0);
+  for (int q = 0; q < ns; ++q) {
+    double2 *Xq = X + q * len;
+    for (int round = 0;; ++round) {
+      RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], s));
+      RHMC_TRY(sub(B, b1.AP64, rb.Bref, len, s));
+      st.dirac++;
+      double rn[kMaxN];
+      RHMC_TRY(colnorms(c, rb.Bref, n, rn, b1.npart, s));
+      double mx = 0.0, ratio_min = 1e300;
+      for (int j = 0; j < n; ++j) {
+        const double r = std::sqrt(rn[j]) / bn[j];
+        resid[(size_t)q * n + j] = r;
+        mx = std::max(mx, r);
+        if (r > 0) ratio_min = std::min(ratio_min, prm.tol / r);
+      }
+      if (mx <= prm.tol || prm.fixed_iters > 0 || round >= kMaxRefine) {
+        worst = std::max(worst, mx);
+        break;
+      }
+      // defect correction: (A + sigma_q) E = R, X_q += E
+      SolveParams pr = prm;
+      pr.tol = std::min(0.1, 0.5 * ratio_min);
+      pr.fixed_iters = 0;
+      SolveStats st1;
+      rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s)
+                                   : solve_phase1<double>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s);
+      if (rr != RHMC_OK && rr != RHMC_ERR_NOT_CONVERGED && rr != RHMC_ERR_BREAKDOWN) return rr;
+      refinements++;
+      refine_iters += st1.iters;
+      st.dirac += st1.dirac;
+      RHMC_TRY(add_inplace(Xq, rb.E, len, s));  // X_q += E
+    }
+  }
+  if (info) {
+    info->iters = st.iters;
+    info->dirac_calls = st.dirac;
+    info->reliable_updates = st.reliable;
+    info->refinements = refinements;
+    info->refine_iters = refine_iters;
+    info->true_rel_resid_max = worst;
+    if (info->per_shift_resid) std::memcpy(info->per_shift_resid, resid.data(), sizeof(double) * resid.size());
+  }
+  if (prm.fixed_iters > 0) return RHMC_OK;
+  if (worst > prm.tol) {
+    set_error("true residual %.3e above tol %.3e after refinement (phase 1: %d)", worst, prm.tol, (int)rc1);
+    return RHMC_ERR_NOT_CONVERGED;
+  }
+  return RHMC_OK;
+}
+
+// ------------------------------------------------------------ per-vector SCG baseline
+static size_t scg_bytes(const Geom &g, int ns) {
+  Arena a(nullptr);
+  const size_t len = (size_t)g.Vh * 3;
+  a.take<double2>(len);           // b
+  a.take<double2>(len);           // r
+  a.take<double2>(len);           // Ap
+  a.take<double2>(len);           // tmp (odd)
+  a.take<double2>(len * ns);      // p
+  a.take<double2>(len * ns);      // x
+  a.take<double>(kParts);
+  a.take<double>(kMaxS);
+  a.take<ScgScalars>(1);
+  return a.off + 256;
+}
+
+}  // namespace rhmc
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *rhmc_last_error(void) { return rhmc::g_err; }
+
+long long rhmc_kernel_launches(void) { return rhmc::g_launches.load(); }
+
+rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int device) {
+  if (!out || !lat) {
+    set_error("rhmc_create: null argument");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  for (int mu = 0; mu < 4; ++mu)
+    if (lat->dims[mu] < 2 || lat->dims[mu] % 2) {
+      set_error("rhmc_create: extent %d of direction %d must be even and >= 2", lat->dims[mu], mu);
+      return RHMC_ERR_INVALID_ARG;
+    }
+  if (!(lat->mass >= 0.0)) {
+    set_error("rhmc_create: mass must be >= 0");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    set_error("rhmc_create: no CUDA device %d", device);
+    return RHMC_ERR_CUDA;
+  }
+  DeviceGuard dg(device);
+  rhmc_ctx *c = new rhmc_ctx();
+  c->device = device;
+  for (int mu = 0; mu < 4; ++mu) c->g.L[mu] = lat->dims[mu];
+  c->g.Lxh = lat->dims[0] / 2;
+  c->g.V = (long)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
+  c->g.Vh = c->g.V / 2;
+  c->mass = lat->mass;
+  c->bc_t = lat->bc_t == 1 ? 1 : -1;
+  for (int p = 0; p < 2; ++p) {
+    if (cudaMalloc(&c->l64[p], sizeof(double2) * 72 * c->g.Vh) != cudaSuccess ||
+        cudaMalloc(&c->l32[p], sizeof(float2) * 72 * c->g.Vh) != cudaSuccess) {
+      set_error("rhmc_create: out of device memory for links");
+      rhmc_destroy(c);
+      return RHMC_ERR_CUDA;
+    }
+  }
+  // the staged-link hop for FP64 at n = 4 needs 72 KB of shared memory
+  *out = c;
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
+  if (!c) return RHMC_OK;
+  DeviceGuard dg(c->device);
+  for (int p = 0; p < 2; ++p) {
+    if (c->l64[p]) cudaFree(c->l64[p]);
+    if (c->l32[p]) cudaFree(c->l32[p]);
+  }
+  if (c->pool) cudaFree(c->pool);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  delete c;
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *c, const void *U, rhmc_stream_t sv) {
+  if (!c || !U) {
+    set_error("rhmc_set_gauge: null argument");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  RHMC_TRY(stage_links(c->g, (const double2 *)U, c->bc_t, c->l64, c->l32, s));
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  c->have_gauge = true;
+  return RHMC_OK;
+}
+
+size_t rhmc_workspace_bytes(const rhmc_ctx_t *c, int n, int ns, rhmc_precision_t p) {
+  if (!c || n < 1 || n > RHMC_MAX_NRHS || ns < 1 || ns > RHMC_MAX_SHIFTS) return 0;
+  const bool mixed = p == RHMC_MIXED_FP32;
+  // solve with an internal X (unsorted shifts or force) + force's Y fields
+  const size_t len = (size_t)c->g.Vh * 3 * n;
+  size_t solve = solve_bytes(c->g, n, ns, mixed, true);
+  size_t force = sizeof(double2) * len * ns * 2 + sizeof(double) * (kMaxS + kParts) + 4096;
+  return std::max(solve, force) + sizeof(double2) * len * ns + 4096;
+}
+
+static rhmc_status_t check_common(rhmc_ctx_t *c, const void *a, const void *b, int n) {
+  if (!c || !a || !b) {
+    set_error("null argument");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  if (n < 1 || n > RHMC_MAX_NRHS) {
+    set_error("n_rhs = %d out of range [1, %d]", n, RHMC_MAX_NRHS);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  if (!c->have_gauge) {
+    set_error("gauge field not set");
+    return RHMC_ERR_NO_GAUGE;
+  }
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *c, const void *X, void *Y, int n, double sigma, rhmc_precision_t p,
+                                    rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, X, Y, n));
+  if (X == Y) {
+    set_error("X and Y may not alias");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  const long len = c->g.Vh * 3 * n;
+  if (p == RHMC_FP64) {
+    RHMC_TRY(ensure_pool(c, sizeof(double2) * len + 256));
+    return apply_A<double>(c, (const double2 *)X, (double2 *)Y, (double2 *)c->pool, n, sigma, s);
+  }
+  RHMC_TRY(ensure_pool(c, 3 * (sizeof(float2) * len + 256)));
+  Arena a(c->pool);
+  float2 *x32 = a.take<float2>(len), *y32 = a.take<float2>(len), *t32 = a.take<float2>(len);
+  RHMC_TRY((convert<double, float>((const double2 *)X, x32, len, s)));
+  RHMC_TRY(apply_A<float>(c, x32, y32, t32, n, sigma, s));
+  RHMC_TRY((convert<float, double>(y32, (double2 *)Y, len, s)));
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_hop(rhmc_ctx_t *c, const void *X, void *Y, int n, int out_par, rhmc_precision_t p,
+                       rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, X, Y, n));
+  if (X == Y || (out_par != 0 && out_par != 1)) {
+    set_error("rhmc_hop: aliasing or bad parity");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  const long len = c->g.Vh * 3 * n;
+  if (p == RHMC_FP64) return hop<double>(c->g, out_par, c->l64[out_par], (const double2 *)X, (double2 *)Y, nullptr, 0, n, 1, 0, s);
+  RHMC_TRY(ensure_pool(c, 2 * (sizeof(float2) * len + 256)));
+  Arena a(c->pool);
+  float2 *x32 = a.take<float2>(len), *y32 = a.take<float2>(len);
+  RHMC_TRY((convert<double, float>((const double2 *)X, x32, len, s)));
+  RHMC_TRY(hop<float>(c->g, out_par, c->l32[out_par], x32, y32, nullptr, 0, n, 1, 0, s));
+  RHMC_TRY((convert<float, double>(y32, (double2 *)Y, len, s)));
+  return RHMC_OK;
+}
+
+static rhmc_status_t check_shifts(int ns, const double *shifts, double tol) {
+  if (ns < 1 || ns > RHMC_MAX_SHIFTS || !shifts) {
+    set_error("n_shifts = %d out of range [1, %d] or null shifts", ns, RHMC_MAX_SHIFTS);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  for (int q = 0; q < ns; ++q)
+    if (!(shifts[q] >= 0.0) || !std::isfinite(shifts[q])) {
+      set_error("shift %d = %g must be finite and >= 0", q, shifts[q]);
+      return RHMC_ERR_INVALID_ARG;
+    }
+  if (!(tol > 0.0) || !(tol < 1.0)) {
+    set_error("tol = %g must be in (0, 1)", tol);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  return RHMC_OK;
+}
+
+static int default_max_iter(const rhmc_ctx *c, double sigma0, double tol) {
+  const double lo = 4.0 * c->mass * c->mass + sigma0;
+  const double kappa = (lo > 0) ? (64.0 + lo) / lo : 1e12;
+  const double it = 10.0 * std::sqrt(kappa) * std::log(1.0 / tol) + 100.0;
+  return (int)std::min(it, 1e6);
+}
+
+// Solve into caller X (any shift order) using workspace ws.
+static rhmc_status_t block_solve_entry(rhmc_ctx_t *c, const double2 *B, int n, int ns, const double *shifts,
+                                       double2 *X, double tol, int max_iter, bool mixed, int fixed_iters, void *ws,
+                                       rhmc_info_t *info, cudaStream_t s) {
+  const long len = c->g.Vh * 3 * n;
+  std::vector<int> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return shifts[a] < shifts[b]; });
+  bool sorted = true;
+  for (int q = 0; q < ns; ++q) sorted = sorted && order[q] == q;
+  std::vector<double> sh(ns);
+  for (int q = 0; q < ns; ++q) sh[q] = shifts[order[q]];
+  SolveParams prm{tol, max_iter > 0 ? max_iter : default_max_iter(c, sh[0], tol), mixed, fixed_iters};
+  std::vector<double> resid((size_t)ns * n);
+  rhmc_info_t local{};
+  local.per_shift_resid = resid.data();
+  rhmc_status_t rc;
+  if (sorted) {
+    rc = solve_all(c, B, n, ns, sh.data(), X, prm, ws, &local, s);
+  } else {
+    Arena a(ws);
+    double2 *Xs = a.take<double2>((size_t)ns * len);
+    rc = solve_all(c, B, n, ns, sh.data(), Xs, prm, (char *)ws + a.off, &local, s);
+    if (rc == RHMC_OK || rc == RHMC_ERR_NOT_CONVERGED)
+      for (int q = 0; q < ns; ++q)
+        RHMC_CUDA_TRY(cudaMemcpyAsync(X + (size_t)order[q] * len, Xs + (size_t)q * len, sizeof(double2) * len,
+                                      cudaMemcpyDeviceToDevice, s));
+  }
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    double *user = info->per_shift_resid;
+    *info = local;
+    info->per_shift_resid = user;
+    if (user)
+      for (int q = 0; q < ns; ++q)
+        for (int j = 0; j < n; ++j) user[(size_t)order[q] * n + j] = resid[(size_t)q * n + j];
+  }
+  return rc;
+}
+
+rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *c, const void *B, int n, int ns, const double *shifts, void *X,
+                                       double tol, int max_iter, rhmc_precision_t p, void *ws, rhmc_info_t *info,
+                                       rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, B, X, n));
+  RHMC_TRY(check_shifts(ns, shifts, tol));
+  if (p != RHMC_FP64 && p != RHMC_MIXED_FP32) {
+    set_error("unknown precision %d", (int)p);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  if (!ws) {
+    RHMC_TRY(ensure_pool(c, rhmc_workspace_bytes(c, n, ns, p)));
+    ws = c->pool;
+  }
+  return block_solve_entry(c, (const double2 *)B, n, ns, shifts, (double2 *)X, tol, max_iter, p == RHMC_MIXED_FP32,
+                           0, ws, info, s);
+}
+
+rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n, int ns, const double *shifts,
+                                           void *Xv, double tol, int max_iter, void *ws, rhmc_info_t *info,
+                                           rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, Bv, Xv, n));
+  RHMC_TRY(check_shifts(ns, shifts, tol));
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  const size_t need = scg_bytes(c->g, ns);
+  if (!ws) {
+    RHMC_TRY(ensure_pool(c, need));
+    ws = c->pool;
+  }
+  std::vector<int> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return shifts[a] < shifts[b]; });
+  std::vector<double> sh(ns);
+  for (int q = 0; q < ns; ++q) sh[q] = shifts[order[q]];
+  const long len1 = c->g.Vh * 3;
+  const long lenb = len1 * n;
+  Arena a(ws);
+  double2 *b = a.take<double2>(len1), *r = a.take<double2>(len1), *Ap = a.take<double2>(len1),
+          *tmp = a.take<double2>(len1), *p = a.take<double2>(len1 * ns), *x = a.take<double2>(len1 * ns);
+  double *parts = a.take<double>(kParts), *sig = a.take<double>(kMaxS);
+  ScgScalars *sc = a.take<ScgScalars>(1);
+  RHMC_CUDA_TRY(cudaMemcpyAsync(sig, sh.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  const int kmax = max_iter > 0 ? max_iter : default_max_iter(c, sh[0], tol);
+  const double a0 = 4.0 * c->mass * c->mass + sh[0];
+  int total_iters = 0, dirac = 0;
+  bool all_ok = true;
+  RHMC_TRY(ensure_pinned(c, sizeof(ScgScalars)));
+  for (int j = 0; j < n; ++j) {
+    RHMC_TRY(column((const double2 *)Bv, b, len1, n, j, 1, s));
+    RHMC_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double2) * len1, cudaMemcpyDeviceToDevice, s));
+    for (int q = 0; q < ns; ++q)
+      RHMC_CUDA_TRY(cudaMemcpyAsync(p + q * len1, b, sizeof(double2) * len1, cudaMemcpyDeviceToDevice, s));
+    RHMC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * len1 * ns, s));
+    RHMC_TRY(redot(r, r, len1, parts, kParts, s));
+    RHMC_TRY(scg_init(sc, parts, kParts, ns, sig, s));
+    int k = 0;
+    bool done = false;
+    while (k < kmax && !done) {
+      const int chunk = std::min(kCheckEvery, kmax - k);
+      for (int q = 0; q < chunk; ++q) {
+        ++k;
+        RHMC_TRY(hop<double>(c->g, 1, c->l64[1], p, tmp, nullptr, 0.0, 1, 1, 0, s));
+        RHMC_TRY(hop<double>(c->g, 0, c->l64[0], tmp, Ap, p, a0, 1, 1, 0, s));
+        RHMC_TRY(redot(p, Ap, len1, parts, kParts, s));
+        RHMC_TRY(scg_alpha(sc, parts, kParts, ns, s));
+        RHMC_TRY(scg_update1(sc, r, Ap, x, p, ns, len1, parts, kParts, s));
+        RHMC_TRY(scg_beta(sc, parts, kParts, ns, tol, s));
+        RHMC_TRY(scg_update2(sc, r, p, ns, len1, s));
+        dirac++;
+      }
+      ScgScalars *h = reinterpret_cast<ScgScalars *>(c->h_pin);
+      RHMC_CUDA_TRY(cudaMemcpyAsync(h, sc, sizeof(ScgScalars), cudaMemcpyDeviceToHost, s));
+      RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+      if (h->breakdown) {
+        set_error("scg breakdown (p^dagger A p <= 0)");
+        return RHMC_ERR_BREAKDOWN;
+      }
+      bool act = false;
+      for (int q = 1; q < ns; ++q) act = act || h->active[q];
+      done = h->rel < tol && !act;
+    }
+    all_ok = all_ok && done;
+    total_iters += k;
+    for (int q = 0; q < ns; ++q) RHMC_TRY(column(x + q * len1, (double2 *)Xv + (size_t)order[q] * lenb, len1, n, j, 0, s));
+  }
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = total_iters;
+    info->dirac_calls = dirac;
+    info->reliable_updates = 0;
+    info->refinements = 0;
+    info->refine_iters = 0;
+    info->true_rel_resid_max = -1.0;
+  }
+  if (!all_ok) {
+    set_error("per-vector multishift CG not converged");
+    return RHMC_ERR_NOT_CONVERGED;
+  }
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, const double *alpha,
+                         const double *beta, int ns, double tol, int max_iter, rhmc_precision_t p, const void *X_in,
+                         void *G, double *S_out, void *ws, rhmc_info_t *info, rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, Phi, G, n));
+  if (!alpha || !beta) {
+    set_error("rhmc_force: null alpha/beta");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  RHMC_TRY(check_shifts(ns, beta, X_in ? 0.5 : tol));
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  if (!ws) {
+    RHMC_TRY(ensure_pool(c, rhmc_workspace_bytes(c, n, ns, p)));
+    ws = c->pool;
+  }
+  const long len = c->g.Vh * 3 * n;
+  Arena a(ws);
+  double2 *X = (double2 *)X_in;
+  if (!X) X = a.take<double2>((size_t)ns * len);
+  void *rest = (char *)ws + a.off;
+  if (!X_in) {
+    const rhmc_status_t rc = block_solve_entry(c, (const double2 *)Phi, n, ns, beta, X, tol, max_iter,
+                                               p == RHMC_MIXED_FP32, 0, rest, info, s);
+    if (rc != RHMC_OK) return rc;
+  } else if (info) {
+    std::memset(info, 0, sizeof(*info) - sizeof(double *));
+  }
+  // Y^(s) = D_oe X^(s), all shifts in one batched hop (links loaded once per tile)
+  Arena fa(rest);
+  double2 *Y = fa.take<double2>((size_t)ns * len);
+  double *alpha_d = fa.take<double>(kMaxS);
+  double *parts = fa.take<double>(kParts);
+  RHMC_CUDA_TRY(cudaMemcpyAsync(alpha_d, alpha, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  RHMC_TRY(hop<double>(c->g, 1, c->l64[1], X, Y, nullptr, 0.0, n, ns, len, s));
+  RHMC_TRY(force_links(c->g, X, Y, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+  if (S_out) {
+    RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts));
+    double S = 0.0;
+    RHMC_TRY(redot((const double2 *)Phi, (const double2 *)Phi, len, parts, kParts, s));
+    RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
+    RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int q = 0; q < kParts; ++q) S += alpha0 * c->h_pin[q];
+    for (int q = 0; q < ns; ++q) {
+      RHMC_TRY(redot((const double2 *)Phi, X + (size_t)q * len, len, parts, kParts, s));
+      RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
+      RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+      double t = 0.0;
+      for (int k = 0; k < kParts; ++k) t += c->h_pin[k];
+      S += alpha[q] * t;
+    }
+    *S_out = S;
+  }
+  return RHMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/rhmc.h"
+
+namespace rhmc {
+
+// ------------------------------------------------------------ complex types
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+template <typename T> using C = typename cplx<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) {
+  C<T> z;
+  z.x = re;
+  z.y = im;
+  return z;
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> czero() { return mk<T>(T(0), T(0)); }
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cmac(C<T> &acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename T> __device__ __forceinline__ void cmac_cj(C<T> &acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+template <typename T> __device__ __forceinline__ void cmac_bcj(C<T> &acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.y, b.x, acc.y);
+  acc.y = fma(-a.x, b.y, acc.y);
+}
+
+// ------------------------------------------------------------ lattice geometry
+struct Geom {
+  int L[4];
+  int Lxh;   // Lx / 2
+  long V, Vh;
+};
+
+// Coordinates of the site with parity `par` and parity rank h.  Because Lx is
+// even, lex = 2h or 2h+1; the parity fixes which.
+__device__ __forceinline__ void site_coords(const Geom &g, int par, long h, int x[4]) {
+  long r = h / g.Lxh;  // (y, z, t) row index
+  const int xh = (int)(h - r * g.Lxh);
+  x[1] = (int)(r % g.L[1]);
+  r /= g.L[1];
+  x[2] = (int)(r % g.L[2]);
+  x[3] = (int)(r / g.L[2]);
+  const int rowpar = (x[1] + x[2] + x[3]) & 1;
+  x[0] = 2 * xh + (rowpar ^ par);
+}
+
+__device__ __forceinline__ long lex_of(const Geom &g, const int x[4]) {
+  return x[0] + (long)g.L[0] * (x[1] + (long)g.L[1] * (x[2] + (long)g.L[2] * x[3]));
+}
+
+// Parity rank of the neighbour of x in direction mu (dir = +1 / -1).
+__device__ __forceinline__ long nb_rank(const Geom &g, const int x[4], int mu, int dir) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  int v = y[mu] + dir;
+  if (v < 0) v += g.L[mu];
+  if (v >= g.L[mu]) v -= g.L[mu];
+  y[mu] = v;
+  return lex_of(g, y) >> 1;
+}
+
+// ------------------------------------------------------------ status handling
+void set_error(const char *fmt, ...);
+void count_launch();
+
+#define RHMC_CUDA_TRY(call)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      ::rhmc::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));   \
+      return RHMC_ERR_CUDA;                                                                    \
+    }                                                                                          \
+  } while (0)
+
+#define RHMC_LAUNCH_CHECK()                                                                    \
+  do {                                                                                         \
+    ::rhmc::count_launch();                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess) {                                                                   \
+      ::rhmc::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return RHMC_ERR_CUDA;                                                                    \
+    }                                                                                          \
+  } while (0)
+
+}  // namespace rhmc

@@ -1,0 +1,92 @@
+// Pseudofermion force, Eq. (force) with the rational approximation of Eq. (RA):
+//
+//   G_mu(x) = dS/dRe U_mu(x) + i dS/dIm U_mu(x)
+//           = 2 eps(x) eta_mu(x) b_mu(x) sum_s alpha_s sum_i W_si(x) W_si(x+mu)^dagger,
+//
+// with W = X^(s) on even sites and W = Y^(s) = D_oe X^(s) on odd sites (the
+// derivative of S = sum_s alpha_s phi^dagger (A + beta_s)^-1 phi through
+// A = 4m^2 - D_eo D_oe and D_oe = -D_eo^dagger).  Per link this is a
+// (3 x R)(R x 3) contraction over R = n * n_shifts columns.  FP64 throughout.
+//
+// One group of 16 lanes per link: lane i accumulates the columns i, i+16, ...
+// of every shift (coalesced loads across the lanes), the 9 complex partial
+// sums are then reduced across the group with shuffles.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rhmc {
+
+__global__ void __launch_bounds__(256) k_force(Geom g, const double2 *__restrict__ X, const double2 *__restrict__ Y,
+                                               int n, int ns, long fstride, const double *__restrict__ alpha,
+                                               int bc_t, double2 *__restrict__ G) {
+  const long pair = (long)blockIdx.x * 16 + threadIdx.x / 16;
+  const int lane = threadIdx.x & 15;
+  const bool valid = pair < 4 * g.V;
+  const long lex = valid ? (pair >> 2) : 0;
+  const int mu = (int)(pair & 3);
+  int x[4];
+  {
+    long r = lex;
+    x[0] = (int)(r % g.L[0]);
+    r /= g.L[0];
+    x[1] = (int)(r % g.L[1]);
+    r /= g.L[1];
+    x[2] = (int)(r % g.L[2]);
+    x[3] = (int)(r / g.L[2]);
+  }
+  const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const long hx = lex >> 1;
+  const long hy = nb_rank(g, x, mu, +1);
+  const double2 *Wx = par ? Y : X;
+  const double2 *Wy = par ? X : Y;
+  double2 acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = make_double2(0.0, 0.0);
+  if (valid) {
+    for (int s = 0; s < ns; ++s) {
+      const double a = alpha[s];
+      const double2 *px = Wx + s * fstride + hx * 3 * n;
+      const double2 *py = Wy + s * fstride + hy * 3 * n;
+      for (int i = lane; i < n; i += 16) {
+        double2 u[3], v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          u[c] = px[c * n + i];
+          const double2 w = py[c * n + i];
+          v[c] = make_double2(a * w.x, a * w.y);
+        }
+#pragma unroll
+        for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 3; ++cb) cmac_bcj<double>(acc[ca * 3 + cb], u[ca], v[cb]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+      acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+    }
+  if (valid && lane == 0) {
+    int sum = 0;
+    for (int nu = 0; nu < mu; ++nu) sum += x[nu];
+    double pre = 2.0 * (par ? -1.0 : 1.0) * ((sum & 1) ? -1.0 : 1.0);
+    if (mu == 3 && bc_t == -1 && x[3] == g.L[3] - 1) pre = -pre;
+    double2 *o = G + pair * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) o[q] = make_double2(pre * acc[q].x, pre * acc[q].y);
+  }
+}
+
+rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
+                          const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s) {
+  const long pairs = 4 * g.V;
+  const long grid = (pairs + 15) / 16;
+  k_force<<<(unsigned)grid, 256, 0, s>>>(g, X, Y, n, nshift, fstride, alpha_dev, bc_t, G);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
+}  // namespace rhmc

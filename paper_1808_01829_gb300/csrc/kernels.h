@@ -1,0 +1,75 @@
+// Internal launch wrappers (host functions enqueueing kernels on a stream).
+#pragma once
+
+#include "common.cuh"
+
+namespace rhmc {
+
+constexpr int kMaxN = RHMC_MAX_NRHS;
+constexpr int kMaxS = RHMC_MAX_SHIFTS;
+
+// Device-resident state of the SBCGrQ coefficient recursion (FP64).  Matrices
+// are n x n row-major in the first n*n entries.  Slots [k & 1] hold iteration
+// k's alpha, Gram1 (= alpha^-1), rho and delta.
+struct SolverState {
+  double2 alpha[2][kMaxN * kMaxN];
+  double2 G1[2][kMaxN * kMaxN];
+  double2 rho[2][kMaxN * kMaxN];
+  double2 delta[2][kMaxN * kMaxN];
+  double2 beta_s[kMaxS][kMaxN * kMaxN];
+  double2 alpha_s[kMaxS][kMaxN * kMaxN];
+  double sigma[kMaxS];        // shifts, ascending
+  double d0[kMaxN];           // ||B e_j||
+  double res[kMaxS][kMaxN];   // recursive relative residual per shift and column (s = 0: base)
+  int active[kMaxS];          // shift still being updated
+  int upd[kMaxS];             // shift updated in the current iteration
+  int breakdown;              // nonzero: which coefficient step failed
+};
+
+// dslash.cu
+rhmc_status_t stage_links(const Geom &g, const double2 *U, int bc_t, double2 *l64[2], float2 *l32[2],
+                          cudaStream_t s);
+template <typename T>
+rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
+                  int n, int nbatch, long bstride, cudaStream_t s);
+
+// blas.cu
+template <typename T>
+rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *partial, int nparts, cudaStream_t s);
+template <typename TA, typename TY>
+rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY> *Y, long rows, int n,
+                         cudaStream_t s);
+template <typename T, typename TX>
+rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
+                         long rows, int n, long fstride, cudaStream_t s);
+rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s);
+template <typename TI, typename TO>
+rhmc_status_t convert(const C<TI> *in, C<TO> *out, long len, cudaStream_t s);
+rhmc_status_t sub(const double2 *a, const double2 *b, double2 *out, long len, cudaStream_t s);
+rhmc_status_t add_inplace(double2 *a, const double2 *b, long len, cudaStream_t s);
+template <typename T>
+rhmc_status_t colnorm2(const C<T> *A, long rows, int n, double *partial, int nparts, cudaStream_t s);
+rhmc_status_t redot(const double2 *A, const double2 *B, long len, double *partial, int nparts, cudaStream_t s);
+
+// small.cu
+template <typename T>
+rhmc_status_t nxn_qr_init(const double2 *partial, int nparts, int n, int nshift, SolverState *st, C<T> *rinv,
+                          cudaStream_t s);
+template <typename T>
+rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *mw, cudaStream_t s);
+template <typename T>
+rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef, cudaStream_t s);
+template <typename T>
+rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
+                         cudaStream_t s);
+rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, double2 *rinv,
+                           cudaStream_t s);
+
+// force.cu
+rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
+                          const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
+
+// scg.cu (per-vector FP64 multishift CG baseline)
+struct ScgState;
+
+}  // namespace rhmc

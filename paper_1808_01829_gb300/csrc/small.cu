@@ -1,0 +1,435 @@
+// n x n coefficient algebra of SBCGrQ (Algorithm 1), FP64, on the device.
+//
+// A CTA of 256 threads works on n x n complex matrices (n <= 16) held in
+// shared memory, thread t owning element (t / n, t % n).  The state of the
+// recursion lives in a SolverState in device memory; quantities of iteration
+// k are written to slot k & 1 and those of k-1 read from slot (k-1) & 1, so
+// consecutive launches never overwrite what the next one still reads.
+//
+//   qr_init   {Q_0, delta_0} = qr(B) by Cholesky of B^dagger B   (line 2)
+//   alpha     alpha_k = (P^dagger (A + sigma_0) P)^-1            (line 4)
+//   rho       rho_k from the Cholesky of W^dagger W (thin QR),     (lines 5-8)
+//             base coefficients alpha_k delta_{k-1}, rho_k^dagger, delta_k
+//   shifts    beta^(s)_k, alpha^(s)_k and the coefficients of      (lines 9-12)
+//             lines 11-12, one CTA per shift; shifted residual
+//             delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (Sec. III), freezing
+//   reliable  delta_k replaced by the R factor of the true residual
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rhmc {
+
+namespace {
+
+struct Cta {
+  int n, t, i, j;
+  bool own;
+  __device__ Cta(int n_) : n(n_), t(threadIdx.x), i(threadIdx.x / n_), j(threadIdx.x % n_), own(threadIdx.x < n_ * n_) {}
+};
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmulz(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 conjz(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cdivz(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// C = op(A) op(B); ca / cb: use the adjoint of A / B.  C may not alias A or B.
+__device__ void mm(const Cta &c, double2 *Cm, const double2 *A, const double2 *B, bool ca = false, bool cb = false) {
+  if (c.own) {
+    double2 acc = make_double2(0, 0);
+    for (int k = 0; k < c.n; ++k) {
+      const double2 a = ca ? conjz(A[k * c.n + c.i]) : A[c.i * c.n + k];
+      const double2 b = cb ? conjz(B[c.j * c.n + k]) : B[k * c.n + c.j];
+      acc = cadd(acc, cmulz(a, b));
+    }
+    Cm[c.t] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ void copy(const Cta &c, double2 *D, const double2 *S) {
+  if (c.own) D[c.t] = S[c.t];
+  __syncthreads();
+}
+
+__device__ void set_eye(const Cta &c, double2 *D) {
+  if (c.own) D[c.t] = make_double2(c.i == c.j ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+}
+
+// Sum the per-CTA partials of a Gram matrix into G.
+__device__ void reduce_partials(const Cta &c, double2 *G, const double2 *partial, int nparts) {
+  if (c.own) {
+    double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+    const int nn = c.n * c.n;
+    int p = 0;
+    for (; p + 1 < nparts; p += 2) {
+      s0 = cadd(s0, partial[(long)p * nn + c.t]);
+      s1 = cadd(s1, partial[(long)(p + 1) * nn + c.t]);
+    }
+    if (p < nparts) s0 = cadd(s0, partial[(long)p * nn + c.t]);
+    G[c.t] = cadd(s0, s1);
+  }
+  __syncthreads();
+}
+
+// In-place Cholesky A = L L^dagger (lower, positive real diagonal).  The Gram
+// matrix is symmetrised first.  Returns false (for all threads) if A is not
+// numerically positive definite.
+__device__ bool cholesky(const Cta &c, double2 *A, int *flag) {
+  const int n = c.n;
+  double2 h = make_double2(0, 0);
+  if (c.own) h = (c.i == c.j) ? make_double2(A[c.t].x, 0.0)
+                              : make_double2(0.5 * (A[c.t].x + A[c.j * n + c.i].x),
+                                             0.5 * (A[c.t].y - A[c.j * n + c.i].y));
+  __syncthreads();
+  if (c.own) A[c.t] = h;
+  if (c.t == 0) *flag = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (c.t == 0) {
+      const double d = A[k * n + k].x;
+      if (!(d > 0.0) || !isfinite(d)) *flag = 1;
+      A[k * n + k] = make_double2(sqrt(fmax(d, 0.0)), 0.0);
+    }
+    __syncthreads();
+    if (*flag) return false;
+    if (c.t > k && c.t < n) {
+      const double dk = A[k * n + k].x;
+      A[c.t * n + k] = make_double2(A[c.t * n + k].x / dk, A[c.t * n + k].y / dk);
+    }
+    __syncthreads();
+    if (c.own && c.i > k && c.j > k && c.j <= c.i)
+      A[c.t] = csub(A[c.t], cmulz(A[c.i * n + k], conjz(A[c.j * n + k])));
+    __syncthreads();
+  }
+  if (c.own && c.j > c.i) A[c.t] = make_double2(0, 0);
+  __syncthreads();
+  return true;
+}
+
+// Inverse of an upper-triangular R (R^-1 upper).  Thread j < n owns column j.
+__device__ void inv_upper(const Cta &c, double2 *Ri, const double2 *R) {
+  const int n = c.n;
+  if (c.own) Ri[c.t] = make_double2(0, 0);
+  __syncthreads();
+  if (c.t < n) {
+    const int j = c.t;
+    for (int i = j; i >= 0; --i) {
+      double2 s = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      for (int k = i + 1; k <= j; ++k) s = csub(s, cmulz(R[i * n + k], Ri[k * n + j]));
+      Ri[i * n + j] = cdivz(s, R[i * n + i]);
+    }
+  }
+  __syncthreads();
+}
+
+// General inverse by Gauss-Jordan with partial pivoting.  A is destroyed.
+__device__ bool inv_general(const Cta &c, double2 *Ai, double2 *A, int *piv, int *flag) {
+  const int n = c.n;
+  set_eye(c, Ai);
+  for (int k = 0; k < n; ++k) {
+    if (c.t == 0) {
+      int p = k;
+      double best = A[k * n + k].x * A[k * n + k].x + A[k * n + k].y * A[k * n + k].y;
+      for (int r = k + 1; r < n; ++r) {
+        const double v = A[r * n + k].x * A[r * n + k].x + A[r * n + k].y * A[r * n + k].y;
+        if (v > best) {
+          best = v;
+          p = r;
+        }
+      }
+      *piv = p;
+      if (!(best > 0.0) || !isfinite(best)) *flag = 1;
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const int p = *piv;
+    if (p != k && c.t < 2 * n) {
+      const int col = c.t % n;
+      double2 *M = (c.t < n) ? A : Ai;
+      const double2 tmp = M[k * n + col];
+      M[k * n + col] = M[p * n + col];
+      M[p * n + col] = tmp;
+    }
+    __syncthreads();
+    const double2 d = A[k * n + k];
+    __syncthreads();
+    if (c.t < 2 * n) {
+      const int col = c.t % n;
+      double2 *M = (c.t < n) ? A : Ai;
+      M[k * n + col] = cdivz(M[k * n + col], d);
+    }
+    __syncthreads();
+    // eliminate column k from the other rows; factors read before any write
+    double2 fa = make_double2(0, 0), va = make_double2(0, 0), vi = make_double2(0, 0);
+    if (c.own && c.i != k) {
+      fa = A[c.i * n + k];
+      va = A[k * n + c.j];
+      vi = Ai[k * n + c.j];
+    }
+    __syncthreads();
+    if (c.own && c.i != k) {
+      A[c.t] = csub(A[c.t], cmulz(fa, va));
+      Ai[c.t] = csub(Ai[c.t], cmulz(fa, vi));
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+__device__ double colnorm(const Cta &c, const double2 *A, int j) {
+  double s = 0.0;
+  for (int i = 0; i < c.n; ++i) s += A[i * c.n + j].x * A[i * c.n + j].x + A[i * c.n + j].y * A[i * c.n + j].y;
+  return sqrt(s);
+}
+
+template <typename T>
+__device__ void store_coef(const Cta &c, C<T> *dst, const double2 *M, double scale = 1.0) {
+  if (c.own) dst[c.t] = mk<T>((T)(scale * M[c.t].x), (T)(scale * M[c.t].y));
+}
+
+#define NN 256  // shared matrix capacity (n <= 16)
+
+}  // namespace
+
+// ------------------------------------------------------------ kernels
+
+// line 2: {Q_0, delta_0} = qr(B) via Cholesky of the Gram B^dagger B; init state.
+template <typename T>
+__global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int nparts, int n, int nshift,
+                                                 SolverState *st, C<T> *rinv_out) {
+  __shared__ double2 G[NN], Ri[NN];
+  __shared__ int flag;
+  Cta c(n);
+  reduce_partials(c, G, partial, nparts);
+  if (!cholesky(c, G, &flag)) {
+    if (c.t == 0) st->breakdown = 1;
+    return;
+  }
+  // delta_0 = L^dagger
+  if (c.own) Ri[c.t] = conjz(G[c.j * n + c.i]);
+  __syncthreads();
+  copy(c, G, Ri);  // G = delta_0 (upper)
+  inv_upper(c, Ri, G);
+  store_coef<T>(c, rinv_out, Ri);
+  if (c.own) {
+    st->delta[0][c.t] = G[c.t];
+    st->rho[0][c.t] = G[c.t];
+    const double2 e = make_double2(c.i == c.j ? 1.0 : 0.0, 0.0);
+    st->alpha[0][c.t] = e;
+    st->G1[0][c.t] = e;
+    for (int s = 0; s < nshift; ++s) {
+      st->beta_s[s][c.t] = e;
+      st->alpha_s[s][c.t] = e;
+    }
+  }
+  if (c.t < n) st->d0[c.t] = colnorm(c, G, c.t);
+  if (c.t < nshift) {
+    st->active[c.t] = 1;
+    st->upd[c.t] = 0;
+    for (int j = 0; j < n; ++j) st->res[c.t][j] = 1.0;
+  }
+  if (c.t == 0) st->breakdown = 0;
+}
+
+// line 4: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P; also -alpha_k for line 5.
+template <typename T>
+__global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k,
+                                                   C<T> *mw_out) {
+  __shared__ double2 G[NN], L[NN], Li[NN], A[NN];
+  __shared__ int flag;
+  Cta c(n);
+  const int cur = k & 1;
+  reduce_partials(c, G, partial, nparts);
+  if (c.own) {
+    // Hermitian part (the Gram of P with an Hermitian operator)
+    const double2 a = G[c.t], b = G[c.j * n + c.i];
+    L[c.t] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  __syncthreads();
+  copy(c, G, L);
+  if (c.own) st->G1[cur][c.t] = G[c.t];
+  if (!cholesky(c, L, &flag)) {
+    if (c.t == 0) st->breakdown = 2;
+    return;
+  }
+  // L^-1 via the upper inverse of L^dagger:  (L^dagger)^-1 = (L^-1)^dagger
+  if (c.own) A[c.t] = conjz(L[c.j * n + c.i]);
+  __syncthreads();
+  inv_upper(c, Li, A);     // Li = (L^dagger)^-1 = L^-dagger
+  mm(c, A, Li, Li, false, true);  // alpha = L^-dagger L^-1
+  if (c.own) st->alpha[cur][c.t] = A[c.t];
+  store_coef<T>(c, mw_out, A, -1.0);
+}
+
+// lines 5-8: rho_k from the Cholesky of W^dagger W; base coefficients; delta_k.
+template <typename T>
+__global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k,
+                                                 C<T> *coef) {
+  __shared__ double2 G[NN], R[NN], Ri[NN], M[NN];
+  __shared__ int flag;
+  Cta c(n);
+  const int cur = k & 1, prev = (k - 1) & 1;
+  const int nn = n * n;
+  reduce_partials(c, G, partial, nparts);
+  if (!cholesky(c, G, &flag)) {
+    if (c.t == 0) st->breakdown = 3;
+    return;
+  }
+  if (c.own) R[c.t] = conjz(G[c.j * n + c.i]);  // rho_k = L^dagger (upper)
+  __syncthreads();
+  inv_upper(c, Ri, R);
+  store_coef<T>(c, coef, Ri);
+  if (c.own) st->rho[cur][c.t] = R[c.t];
+  // M1 = alpha_k delta_{k-1}   (line 6)
+  mm(c, M, st->alpha[cur], st->delta[prev]);
+  store_coef<T>(c, coef + nn, M);
+  // M2 = rho_k^dagger          (line 7)
+  if (c.own) M[c.t] = conjz(R[c.j * n + c.i]);
+  __syncthreads();
+  store_coef<T>(c, coef + 2 * nn, M);
+  // delta_k = rho_k delta_{k-1} (line 8)
+  mm(c, M, R, st->delta[prev]);
+  if (c.own) st->delta[cur][c.t] = M[c.t];
+  if (c.t < n) st->res[0][c.t] = colnorm(c, M, c.t) / st->d0[c.t];
+  if (c.t == 0) st->upd[0] = 1;
+}
+
+// lines 9-12 for shift s = blockIdx.x + 1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef,
+                                                    double tol_shift, int freeze) {
+  __shared__ double2 Cp[NN], A1[NN], A2[NN], B[NN], Bi[NN];
+  __shared__ int flag, piv;
+  Cta c(n);
+  const int s = blockIdx.x + 1;
+  if (s >= nshift) return;
+  const int cur = k & 1, prev = (k - 1) & 1;
+  const int nn = n * n;
+  if (!st->active[s]) {
+    if (c.t == 0) st->upd[s] = 0;
+    return;
+  }
+  if (c.t == 0) flag = 0;
+  const double dsig = st->sigma[s] - st->sigma[0];
+  // coupling C = alpha_k rho_{k-1} alpha_{k-1}^-1, with alpha_{k-1}^-1 = Gram1_{k-1}
+  mm(c, A1, st->alpha[cur], st->rho[prev]);
+  mm(c, Cp, A1, st->G1[prev]);
+  // T = 1 + dsig alpha_k + C (1 - beta_{k-1}) rho_{k-1}^dagger      (line 9)
+  if (c.own) {
+    const double2 b = st->beta_s[s][c.t];
+    A1[c.t] = make_double2((c.i == c.j ? 1.0 : 0.0) - b.x, -b.y);
+  }
+  __syncthreads();
+  mm(c, A2, Cp, A1);
+  mm(c, A1, A2, st->rho[prev], false, true);
+  if (c.own) {
+    const double2 a = st->alpha[cur][c.t];
+    B[c.t] = make_double2((c.i == c.j ? 1.0 : 0.0) + dsig * a.x + A1[c.t].x, dsig * a.y + A1[c.t].y);
+  }
+  __syncthreads();
+  if (!inv_general(c, Bi, B, &piv, &flag)) {
+    if (c.t == 0) st->breakdown = 4;
+    return;
+  }
+  // alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                        (line 10)
+  mm(c, A1, Bi, Cp);
+  mm(c, A2, A1, st->alpha_s[s]);
+  // M1 = alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12)
+  store_coef<T>(c, coef + (1 + 2 * s) * nn, A2);
+  mm(c, A1, Bi, st->rho[cur], false, true);
+  store_coef<T>(c, coef + (2 + 2 * s) * nn, A1);
+  if (c.own) {
+    st->beta_s[s][c.t] = Bi[c.t];
+    st->alpha_s[s][c.t] = A2[c.t];
+  }
+  // shifted residual delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k = rho_k Gram1_k alpha^(s)_k
+  mm(c, A1, st->rho[cur], st->G1[cur]);
+  mm(c, B, A1, A2);
+  if (c.t == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double r = colnorm(c, B, j) / st->d0[j];
+      st->res[s][j] = r;
+      mx = fmax(mx, r);
+    }
+    st->upd[s] = 1;
+    if (freeze && mx < tol_shift) st->active[s] = 0;
+  }
+}
+
+// Reliable update: delta_k <- R factor of the true residual (Gram partials of
+// R^dagger R); writes (delta')^-1 for Q = R (delta')^-1.
+__global__ void __launch_bounds__(256) k_nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st,
+                                                      int k, double2 *rinv_out) {
+  __shared__ double2 G[NN], R[NN], Ri[NN];
+  __shared__ int flag;
+  Cta c(n);
+  const int cur = k & 1;
+  reduce_partials(c, G, partial, nparts);
+  if (!cholesky(c, G, &flag)) {
+    if (c.t == 0) st->breakdown = 5;
+    return;
+  }
+  if (c.own) R[c.t] = conjz(G[c.j * n + c.i]);
+  __syncthreads();
+  inv_upper(c, Ri, R);
+  if (c.own) {
+    st->delta[cur][c.t] = R[c.t];
+    rinv_out[c.t] = Ri[c.t];
+  }
+  if (c.t < n) st->res[0][c.t] = colnorm(c, R, c.t) / st->d0[c.t];
+}
+
+// ------------------------------------------------------------ launchers
+template <typename T>
+rhmc_status_t nxn_qr_init(const double2 *partial, int nparts, int n, int nshift, SolverState *st, C<T> *rinv,
+                          cudaStream_t s) {
+  k_qr_init<T><<<1, 256, 0, s>>>(partial, nparts, n, nshift, st, rinv);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+template <typename T>
+rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *mw, cudaStream_t s) {
+  k_nxn_alpha<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, mw);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+template <typename T>
+rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef,
+                      cudaStream_t s) {
+  k_nxn_rho<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, coef);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+template <typename T>
+rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
+                         cudaStream_t s) {
+  if (nshift > 1) {
+    k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze);
+    RHMC_LAUNCH_CHECK();
+  }
+  return RHMC_OK;
+}
+rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, double2 *rinv,
+                           cudaStream_t s) {
+  k_nxn_reliable<<<1, 256, 0, s>>>(partial, nparts, n, st, k, rinv);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
+#define RHMC_INST_NXN(T)                                                                                     \
+  template rhmc_status_t nxn_qr_init<T>(const double2 *, int, int, int, SolverState *, C<T> *, cudaStream_t); \
+  template rhmc_status_t nxn_alpha<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);   \
+  template rhmc_status_t nxn_rho<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);     \
+  template rhmc_status_t nxn_shifts<T>(int, int, SolverState *, int, C<T> *, double, int, cudaStream_t);
+RHMC_INST_NXN(float)
+RHMC_INST_NXN(double)
+
+}  // namespace rhmc

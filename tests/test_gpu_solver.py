@@ -1,0 +1,172 @@
+"""GPU parity of SBCGrQ (Algorithm 1), the per-vector SCG baseline and the
+force (Eqs. (RA), (force)) against the FP64 oracle.
+
+Criteria: every (shift, column) FP64 true residual <= tol (computed here with
+the oracle's operator), and ||X_gpu - X_orc|| <= tol ||B|| / (4m^2 + sigma_s)
++ 1e-10 ||X_orc|| per column (the solution error a residual tol allows,
+lambda_min >= 4m^2), with the oracle solved to 1e-13.  Force: the oracle's
+force from the GPU's own X matches to 1e-12 (kernel-level parity); the full
+GPU force matches the oracle's within the solution-error bound."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import colrel, make_ctx, need_gpu, to_gpu
+from paper_1808_01829_gb300 import synthetic as syn
+from paper_1808_01829_gb300.remez import rational_approx
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_solution(dims, mass, U, B, shifts, Xg, tol, Xo):
+    bn = np.linalg.norm(B.reshape(-1, B.shape[-1]), axis=0)
+    for s, sig in enumerate(shifts):
+        R = B - oracle.apply_A(dims, mass, U, Xg[s], sigma=sig)
+        rn = np.linalg.norm(R.reshape(-1, B.shape[-1]), axis=0) / bn
+        assert np.all(rn <= tol), (s, sig, rn)
+        err = np.linalg.norm((Xg[s] - Xo[s]).reshape(-1, B.shape[-1]), axis=0)
+        xn = np.linalg.norm(Xo[s].reshape(-1, B.shape[-1]), axis=0)
+        bound = tol * bn / (4 * mass ** 2 + sig) + 1e-10 * xn
+        assert np.all(err <= bound), (s, sig, err / bound)
+
+
+CONFIGS = [
+    # dims, mass, n, (r, a, b, N), eps, tol, precision
+    ((4, 4, 4, 4), 0.1, 2, (-1.0 / 8, 1e-3, 64.0, 8), 0.3, 1e-10, "fp64"),
+    ((4, 4, 4, 4), 0.1, 2, (-1.0 / 8, 1e-3, 64.0, 8), 0.3, 1e-8, "mixed"),
+    ((8, 8, 8, 8), 0.05, 4, (-1.0 / 16, 2e-3, 64.0, 12), 0.5, 1e-10, "fp64"),
+    ((8, 8, 8, 8), 0.05, 4, (-1.0 / 16, 2e-3, 64.0, 12), 0.5, 1e-8, "mixed"),
+    ((4, 6, 4, 8), 0.03, 5, (-1.0 / 20, 1e-3, 64.0, 6), 0.5, 1e-9, "mixed"),
+]
+
+
+@pytest.mark.parametrize("dims,mass,n,rp,eps,tol,prec", CONFIGS)
+def test_block_multishift_matches_oracle(dims, mass, n, rp, eps, tol, prec):
+    need_gpu()
+    ra = rational_approx(*rp)
+    U = syn.random_links(dims, eps, 1200)
+    B = syn.gaussian_pseudofermions(dims, n, 2200)
+    ctx = make_ctx(dims, mass, U)
+    Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, tol, precision=prec)
+    Xg = Xg.cpu().numpy()
+    assert info.true_rel_resid_max <= tol
+    Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13, max_iter=20000)
+    assert rc == 0
+    _check_solution(dims, mass, U, B, ra.beta, Xg, tol, Xo)
+    ctx.close()
+
+
+def test_unsorted_shifts_and_per_shift_info():
+    need_gpu()
+    dims, mass, n = (4, 4, 4, 4), 0.1, 3
+    U = syn.random_links(dims, 0.5, 1201)
+    B = syn.gaussian_pseudofermions(dims, n, 2201)
+    shifts = [0.5, 0.001, 4.0, 0.05]
+    ctx = make_ctx(dims, mass, U)
+    Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-10, precision="fp64")
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, sorted(shifts), tol=1e-13)
+    order = np.argsort(shifts)
+    Xo_caller = np.empty_like(Xo)
+    Xo_caller[order] = Xo
+    _check_solution(dims, mass, U, B, shifts, Xg.cpu().numpy(), 1e-10, Xo_caller)
+    assert len(info.per_shift_resid) == 4
+    assert max(max(r) for r in info.per_shift_resid) <= 1e-10
+    ctx.close()
+
+
+def test_n1_equals_scalar_cg_iterates():
+    """SBCGrQ with one right-hand side reduces to multishift CG (Sec. III)."""
+    need_gpu()
+    dims, mass = (8, 8, 8, 8), 0.05
+    U = syn.random_links(dims, 0.5, 1202)
+    B = syn.gaussian_pseudofermions(dims, 1, 2202)
+    shifts = [0.002, 0.05, 1.0]
+    ctx = make_ctx(dims, mass, U)
+    Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-10, precision="fp64")
+    xs, ks, _ = oracle.scg(dims, mass, U, B[..., 0], shifts, tol=0.5e-10)
+    for s in range(3):
+        assert colrel(Xg.cpu().numpy()[s], xs[s][..., None]) <= 1e-9
+    assert abs(info.iters - ks) <= kcheck_slack()
+    ctx.close()
+
+
+def kcheck_slack():
+    return 8  # host checks every 8 iterations
+
+
+def test_pervector_scg_baseline_matches_oracle():
+    need_gpu()
+    dims, mass, n = (8, 8, 8, 8), 0.05, 4
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1203)
+    B = syn.gaussian_pseudofermions(dims, n, 2203)
+    ctx = make_ctx(dims, mass, U)
+    Xg, info = ctx.multishift_cg_pervector(to_gpu(B), ra.beta, 1e-10)
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
+    _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-10 * 1.5, Xo)
+    # block solver needs fewer iterations than the per-vector one summed over vectors
+    _, binfo = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-10, precision="fp64")
+    assert binfo.iters < info.iters
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_force_matches_oracle(prec, tol):
+    need_gpu()
+    dims, mass, n = (8, 8, 8, 8), 0.05, 4
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1204)
+    Phi = syn.gaussian_pseudofermions(dims, n, 2204)
+    ctx = make_ctx(dims, mass, U)
+    G, S, info = ctx.force(to_gpu(Phi), ra.alpha0, ra.alpha, ra.beta, tol, precision=prec)
+    G = G.cpu().numpy()
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, Phi, ra.beta, tol=1e-13)
+    Go = oracle.force(dims, U, Xo, ra.alpha)
+    So = oracle.action(ra.alpha0, ra.alpha, Phi, Xo)
+    # bound from the solution error of each shift
+    bn = np.linalg.norm(Phi)
+    bound = 2 * max(tol * bn / ((4 * mass ** 2 + b) * np.linalg.norm(Xo[s])) for s, b in enumerate(ra.beta)) + 1e-10
+    assert np.linalg.norm(G - Go) / np.linalg.norm(Go) <= bound
+    assert abs(S - So) / abs(So) <= bound
+    ctx.close()
+
+
+def test_force_kernel_parity_from_given_solutions():
+    """G from supplied X (no solve): FP64 force kernel against the oracle's force of the same X."""
+    need_gpu()
+    dims = (6, 4, 4, 8)
+    U = syn.random_links(dims, 0.5, 1205)
+    ns, n = 3, 5
+    X = np.stack([syn.gaussian_pseudofermions(dims, n, 2205 + s) for s in range(ns)])
+    alpha = [0.3, 1.1, 0.07]
+    ctx = make_ctx(dims, 0.1, U)
+    G, _, _ = ctx.force(to_gpu(X[0]), 0.5, alpha, [0.1, 0.2, 0.3], 1e-8, X=to_gpu(X))
+    Go = oracle.force(dims, U, X, alpha)
+    assert np.linalg.norm(G.cpu().numpy() - Go) <= 1e-12 * np.linalg.norm(Go)
+    ctx.close()
+
+
+def test_breakdown_on_rank_deficient_block():
+    need_gpu()
+    from paper_1808_01829_gb300._lib import RhmcError
+
+    dims = (4, 4, 4, 4)
+    U = syn.random_links(dims, 0.5, 1206)
+    B = syn.gaussian_pseudofermions(dims, 2, 2206)
+    B[..., 1] = B[..., 0]
+    ctx = make_ctx(dims, 0.1, U)
+    with pytest.raises(RhmcError, match="BREAKDOWN"):
+        ctx.block_multishift_cg(to_gpu(B), [0.01, 0.1], 1e-10, precision="fp64")
+    ctx.close()
+
+
+def test_not_converged_reported():
+    need_gpu()
+    dims = (8, 8, 8, 8)
+    U = syn.random_links(dims, 0.5, 1207)
+    B = syn.gaussian_pseudofermions(dims, 2, 2207)
+    ctx = make_ctx(dims, 0.01, U)
+    X, info = ctx.block_multishift_cg(to_gpu(B), [1e-4, 0.1], 1e-10, max_iter=5, precision="fp64",
+                                      allow_not_converged=True)
+    assert info.iters <= 8 and info.true_rel_resid_max > 1e-10
+    ctx.close()
