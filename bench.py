@@ -144,12 +144,10 @@ def cpu_sample(cfg, U, Phi, ra, budget_s=20.0):
     oracle.build()
     threads = oracle.max_threads()
     t0 = time.perf_counter()
-    k = 1
-    oracle.sbcgrq(cfg["dims"], cfg["mass"], U, Phi, ra.beta, fixed_iters=k)
+    X = oracle.sbcgrq(cfg["dims"], cfg["mass"], U, Phi, ra.beta, fixed_iters=1)[0]
     t_iter = time.perf_counter() - t0
     t_force = 0.0
     if t_iter < budget_s:
-        X = oracle.sbcgrq(cfg["dims"], cfg["mass"], U, Phi, ra.beta, fixed_iters=1)[0]
         t0 = time.perf_counter()
         oracle.force(cfg["dims"], U, X, ra.alpha)
         t_force = time.perf_counter() - t0
@@ -228,6 +226,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    lib = ctx.lib
+    l0 = lib.rhmc_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -236,6 +236,7 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    launches = int(lib.rhmc_kernel_launches() - l0)
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -261,10 +262,15 @@ def run_gpu(args):
             e2e.append(a.elapsed_time(b))
     e2e_ms = statistics.median(e2e)
 
-    # ---- roofline: FP32 multi-RHS hop at this workload, events on the launching stream
+    # ---- per-kernel times: one more step with the library's event profiler
     from paper_1808_01829_gb300 import roofline
 
-    roof = roofline.measure_hop(ctx, n, dev)
+    stats = roofline.profile(step)
+    kt = roofline.table(stats)
+    hbm_kernels = [r["kernel"] for r in kt if r["GB/s"]]
+    dominant = hbm_kernels[0] if hbm_kernels else None
+    roof = roofline.entry(stats, dominant) if dominant else None
+    roof_dslash = roofline.entry(stats, "hop_fp32") if "hop_fp32" in stats else None
 
     # ---- comparison: per-vector FP64 multishift CG + force (Fig. 9 analogue)
     base = None
@@ -298,8 +304,10 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (U 191 MB, fields 64-127 MB each)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": len_b, "d2h_bytes_per_step": G.numel() * 16},
-            "gpu_launches": launches_per_step(last, ns),
+            "gpu_launches": launches,
             "roofline": roof,
+            "roofline_dslash": roof_dslash,
+            "kernel_table": kt,
             "clocks": clk,
             "solver": {"iters": last.iters, "dirac_calls": last.dirac_calls, "reliable_updates": last.reliable_updates,
                        "refinements": last.refinements, "refine_iters": last.refine_iters,
@@ -311,15 +319,6 @@ def run_gpu(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def launches_per_step(info, ns):
-    """Kernel launches of one force evaluation (counted from the driver's sequence)."""
-    per_iter = 8  # 2 hops, 2 grams, alpha, axpy, rho, shifts, update (shifts kernel counted once)
-    per_iter += 1
-    reliable = info.reliable_updates * (ns + 6)
-    phase2 = info.dirac_calls - info.iters - info.reliable_updates
-    return int(info.iters * per_iter + 4 + reliable + max(phase2, 0) * 4 + info.refine_iters * per_iter + 2 + 1 + 2)
 
 
 if __name__ == "__main__":

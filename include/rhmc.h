@@ -164,6 +164,22 @@ const char *rhmc_last_error(void);
  * contexts and threads); differences around a call count its launches. */
 long long rhmc_kernel_launches(void);
 
+/* Per-kernel timing for measurement runs.  rhmc_profile_enable(1) clears the
+ * record and starts recording, for every kernel launch of the library, a pair
+ * of CUDA events on the launching stream plus the launch's algorithmic bytes
+ * (each input read once, each output written once); (0) stops recording.
+ * While enabled the fused update kernel reads its shift flags back to the host
+ * first (a synchronisation), so use it outside timed regions.
+ * rhmc_profile_read(category, ...) synchronises on the recorded events and
+ * returns the number of launches, their summed duration (ms) and summed bytes
+ * of one category (RHMC_PROF_*). */
+enum {
+  RHMC_PROF_HOP_FP32 = 0, RHMC_PROF_HOP_FP64, RHMC_PROF_GRAM_FP32, RHMC_PROF_GRAM_FP64, RHMC_PROF_BLOCK_AXPY,
+  RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER, RHMC_PROF_NCAT
+};
+rhmc_status_t rhmc_profile_enable(int on);
+rhmc_status_t rhmc_profile_read(int category, long long *launches, double *ms, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,10 @@ STATUS = {
 }
 
 
+PROF_CATEGORIES = ["hop_fp32", "hop_fp64", "gram_fp32", "gram_fp64", "block_axpy", "update_fp32", "update_fp64",
+                   "nxn", "force", "other"]
+
+
 class RhmcError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
@@ -78,6 +82,10 @@ def load():
         lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
         lib.rhmc_last_error.restype = ctypes.c_char_p
         lib.rhmc_kernel_launches.restype = ctypes.c_longlong
+        lib.rhmc_profile_enable.argtypes = [I]
+        lib.rhmc_profile_enable.restype = I
+        lib.rhmc_profile_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), PD, PD]
+        lib.rhmc_profile_read.restype = I
         for name in ("rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_apply_mdagm_mrhs", "rhmc_hop",
                      "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force"):
             getattr(lib, name).restype = I
@@ -97,4 +105,5 @@ def exported_symbols():
     return [
         "rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_workspace_bytes", "rhmc_apply_mdagm_mrhs",
         "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
+        "rhmc_profile_enable", "rhmc_profile_read",
     ]

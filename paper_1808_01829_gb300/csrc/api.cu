@@ -39,6 +39,41 @@ static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// ------------------------------------------------------------ profiler
+struct ProfRec {
+  int cat;
+  cudaEvent_t a, b;
+  double bytes;
+};
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+static size_t g_pool_next = 0;
+
+static cudaEvent_t pool_event() {
+  if (g_pool_next == g_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_next++];
+}
+
+bool prof_on() { return g_prof; }
+
+void prof_begin(int cat, cudaStream_t s) {
+  if (!g_prof) return;
+  ProfRec r{cat, pool_event(), pool_event(), 0.0};
+  cudaEventRecord(r.a, s);
+  g_recs.push_back(r);
+}
+
+void prof_end(cudaStream_t s, double bytes) {
+  if (!g_prof || g_recs.empty()) return;
+  cudaEventRecord(g_recs.back().b, s);
+  g_recs.back().bytes = bytes;
+}
+
 void set_error(const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -456,6 +491,33 @@ extern "C" {
 const char *rhmc_last_error(void) { return rhmc::g_err; }
 
 long long rhmc_kernel_launches(void) { return rhmc::g_launches.load(); }
+
+rhmc_status_t rhmc_profile_enable(int on) {
+  rhmc::g_recs.clear();
+  rhmc::g_pool_next = 0;
+  rhmc::g_prof = on != 0;
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_profile_read(int cat, long long *launches, double *ms, double *bytes) {
+  if (cat < 0 || cat >= rhmc::PROF_NCAT || !launches || !ms || !bytes) {
+    set_error("rhmc_profile_read: bad argument");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  *launches = 0;
+  *ms = 0.0;
+  *bytes = 0.0;
+  for (auto &r : rhmc::g_recs) {
+    if (r.cat != cat) continue;
+    RHMC_CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    RHMC_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    *launches += 1;
+    *ms += t;
+    *bytes += r.bytes;
+  }
+  return RHMC_OK;
+}
 
 rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int device) {
   if (!out || !lat) {

@@ -270,9 +270,11 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
 
 template <typename T>
 rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *partial, int nparts, cudaStream_t s) {
+  prof_begin(sizeof(T) == 4 ? PROF_GRAM32 : PROF_GRAM64, s);
 #define L_GRAM(NN) k_gram<T, NN><<<nparts, 256, 0, s>>>(A, B, rows, partial)
   RHMC_DISPATCH_N(n, L_GRAM)
 #undef L_GRAM
+  prof_end(s, (double)rows * n * sizeof(C<T>) * (A == B ? 1 : 2));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
@@ -284,9 +286,11 @@ rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY>
                          cudaStream_t s) {
   const int bs = 128;
   const long grid = (rows + bs - 1) / bs;
+  prof_begin(PROF_AXPY, s);
 #define L_AXPY(NN) k_block_axpy<TA, TY, NN><<<grid, bs, 0, s>>>(A, Cin, M, Y, rows)
   RHMC_DISPATCH_N(n, L_AXPY)
 #undef L_AXPY
+  prof_end(s, (double)rows * n * (sizeof(C<TA>) + sizeof(C<TY>) * (Cin ? 2 : 1)));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
@@ -305,8 +309,17 @@ rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *
 #define L_UPD(NN)                                                                                     \
   k_update_all<T, TX, NN><<<grid, bs, 0, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd, nshift, rows, \
                                               fstride)
+  int nupd = nshift;
+  if (prof_on()) {  // profiling only: count the shifts this launch updates (host sync)
+    int h[kMaxS];
+    cudaMemcpy(h, upd, sizeof(int) * nshift, cudaMemcpyDeviceToHost);
+    nupd = 0;
+    for (int q = 0; q < nshift; ++q) nupd += h[q] != 0;
+  }
+  prof_begin(sizeof(T) == 4 ? PROF_UPDATE32 : PROF_UPDATE64, s);
   RHMC_DISPATCH_N(n, L_UPD)
 #undef L_UPD
+  prof_end(s, (double)rows * n * (2.0 * sizeof(C<T>) + nupd * 2.0 * (sizeof(C<T>) + sizeof(C<TX>))));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }

@@ -84,6 +84,17 @@ __device__ __forceinline__ long nb_rank(const Geom &g, const int x[4], int mu, i
 void set_error(const char *fmt, ...);
 void count_launch();
 
+// Optional per-kernel timing (rhmc_profile_enable): events recorded on the
+// launching stream around each launch of a category, with the launch's
+// algorithmic bytes.  No-ops when profiling is off.
+enum ProfCat {
+  PROF_HOP32 = 0, PROF_HOP64, PROF_GRAM32, PROF_GRAM64, PROF_AXPY, PROF_UPDATE32, PROF_UPDATE64,
+  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_NCAT
+};
+bool prof_on();
+void prof_begin(int cat, cudaStream_t s);
+void prof_end(cudaStream_t s, double bytes);
+
 #define RHMC_CUDA_TRY(call)                                                                    \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \

@@ -145,6 +145,7 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
     cudaFuncSetAttribute(k_hop<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr_done = true;
   }
+  prof_begin(sizeof(T) == 4 ? PROF_HOP32 : PROF_HOP64, s);
   if (self) {
     if (stage)
       k_hop<T, true, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
@@ -156,6 +157,8 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
     else
       k_hop<T, false, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
   }
+  // algorithmic bytes: every link once, every input field once, the output once (+ self)
+  prof_end(s, (double)g.Vh * sizeof(C<T>) * (72.0 + nbatch * 3.0 * n * (self ? 3 : 2)));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }

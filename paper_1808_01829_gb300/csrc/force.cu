@@ -84,7 +84,10 @@ rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int
                           const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s) {
   const long pairs = 4 * g.V;
   const long grid = (pairs + 15) / 16;
+  prof_begin(PROF_FORCE, s);
   k_force<<<(unsigned)grid, 256, 0, s>>>(g, X, Y, n, nshift, fstride, alpha_dev, bc_t, G);
+  // algorithmic bytes: X and Y of every shift once, G written once
+  prof_end(s, 2.0 * nshift * g.Vh * 3.0 * n * sizeof(double2) + 4.0 * g.V * 9 * sizeof(double2));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }

@@ -391,20 +391,26 @@ __global__ void __launch_bounds__(256) k_nxn_reliable(const double2 *partial, in
 template <typename T>
 rhmc_status_t nxn_qr_init(const double2 *partial, int nparts, int n, int nshift, SolverState *st, C<T> *rinv,
                           cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
   k_qr_init<T><<<1, 256, 0, s>>>(partial, nparts, n, nshift, st, rinv);
+  prof_end(s, 0.0);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
 template <typename T>
 rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *mw, cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
   k_nxn_alpha<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, mw);
+  prof_end(s, 0.0);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
 template <typename T>
 rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef,
                       cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
   k_nxn_rho<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, coef);
+  prof_end(s, 0.0);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
@@ -412,14 +418,18 @@ template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
                          cudaStream_t s) {
   if (nshift > 1) {
+    prof_begin(PROF_NXN, s);
     k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze);
+    prof_end(s, 0.0);
     RHMC_LAUNCH_CHECK();
   }
   return RHMC_OK;
 }
 rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, double2 *rinv,
                            cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
   k_nxn_reliable<<<1, 256, 0, s>>>(partial, nparts, n, st, k, rinv);
+  prof_end(s, 0.0);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
