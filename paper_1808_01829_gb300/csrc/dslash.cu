@@ -63,100 +63,204 @@ rhmc_status_t stage_links(const Geom &g, const double2 *U, int bc_t, double2 *l6
 }
 
 // ------------------------------------------------------------ hop
-// out[b] = (self ? a * self[b] : 0) - (self ? 1 : -1) * D in[b]   on parity `par`
-// i.e. out = D in            when self == nullptr,
-//      out = a self - D in   otherwise (the fused 4m^2 + sigma axpy of A).
-// One thread per (site, right-hand side); `tile` sites per CTA; the batch
-// loop reuses the staged links for `nbatch` independent fields.
-template <typename T, bool SELF, bool STAGE>
-__global__ void __launch_bounds__(256) k_hop(Geom g, int par, const C<T> *__restrict__ links,
+// out[b] = D in[b]                 (self == nullptr)
+// out[b] = a self[b] - D in[b]     (the fused 4m^2 + sigma axpy of A)
+// on parity `par`, for nbatch independent fields b (stride bstride) that
+// share the staged links.
+//
+// Thread layout: R right-hand sides per thread (register blocking), n / R
+// threads per site, `tile` sites per CTA.  The CTA stages the 72-complex link
+// records of its sites into shared memory once; in FP32 each link element is
+// stored expanded as (re, re, -im, im) so that a complex multiply-add is two
+// packed fma.rn.f32x2 operations on (re, im) and (im, re).
+namespace {
+
+__device__ __forceinline__ void fma2(float2 &acc, float2 a, float2 b) {
+  unsigned long long r, x, y;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(acc.x), "f"(acc.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(r) : "l"(x), "l"(y));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(acc.x), "=f"(acc.y) : "l"(r));
+}
+
+// acc += L * v for an expanded FP32 link element e = (re, re, -im, im)
+__device__ __forceinline__ void lmac(float2 &acc, const float4 &e, const float2 &v) {
+  fma2(acc, make_float2(e.x, e.y), v);
+  fma2(acc, make_float2(e.z, e.w), make_float2(v.y, v.x));
+}
+__device__ __forceinline__ void lmac(double2 &acc, const double2 &e, const double2 &v) { cmac<double>(acc, e, v); }
+
+template <typename T> struct LinkSlot;
+template <> struct LinkSlot<float> { using t = float4; };
+template <> struct LinkSlot<double> { using t = double2; };
+
+__device__ __forceinline__ void expand(float4 &dst, float2 z) { dst = make_float4(z.x, z.x, -z.y, z.y); }
+__device__ __forceinline__ void expand(double2 &dst, double2 z) { dst = z; }
+
+// Vector load / store of R consecutive complex numbers.
+template <typename T, int R> struct Vec;
+template <> struct Vec<float, 4> {
+  __device__ static void ld(const float2 *p, float2 *v) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p)), b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w); v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+  }
+  __device__ static void st(float2 *p, const float2 *v) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  }
+};
+template <> struct Vec<float, 2> {
+  __device__ static void ld(const float2 *p, float2 *v) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  }
+  __device__ static void st(float2 *p, const float2 *v) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  }
+};
+template <typename T> struct Vec1 {
+  __device__ static void ld(const C<T> *p, C<T> *v) { v[0] = p[0]; }
+  __device__ static void st(C<T> *p, const C<T> *v) { p[0] = v[0]; }
+};
+template <> struct Vec<float, 1> : Vec1<float> {};
+template <> struct Vec<double, 1> : Vec1<double> {};
+template <int R> struct VecD {
+  __device__ static void ld(const double2 *p, double2 *v) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = __ldg(p + r);
+  }
+  __device__ static void st(double2 *p, const double2 *v) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r] = v[r];
+  }
+};
+template <> struct Vec<double, 2> : VecD<2> {};
+template <> struct Vec<double, 4> : VecD<4> {};
+
+}  // namespace
+
+template <typename T, int R, bool SELF, bool STAGE>
+__global__ void __launch_bounds__(128) k_hop(Geom g, int par, const C<T> *__restrict__ links,
                                              const C<T> *__restrict__ in, C<T> *__restrict__ out,
                                              const C<T> *__restrict__ self, T a, int n, int tile, int nbatch,
                                              long bstride) {
+  using LS = typename LinkSlot<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T> *sl = reinterpret_cast<C<T> *>(smem_raw);
-  const long h0 = (long)blockIdx.x * tile;
-  const int nsites = (int)min((long)tile, g.Vh - h0);
+  LS *sl = reinterpret_cast<LS *>(smem_raw);
+  const int tps = n / R;
+  const int h0 = blockIdx.x * tile;
+  const int nsites = min(tile, (int)g.Vh - h0);
   if (STAGE) {
-    // 16-byte vector copy of nsites * 72 complex
-    const int nvec = nsites * 72 * (int)sizeof(C<T>) / 16;
-    const int4 *src = reinterpret_cast<const int4 *>(links + h0 * 72);
-    int4 *dst = reinterpret_cast<int4 *>(sl);
-    for (int k = threadIdx.x; k < nvec; k += blockDim.x) dst[k] = __ldg(src + k);
+    const C<T> *src = links + (long)h0 * 72;
+    for (int k = threadIdx.x; k < nsites * 72; k += blockDim.x) expand(sl[k], __ldg(src + k));
     __syncthreads();
   }
-  const int ls = threadIdx.x / n;
-  const int j = threadIdx.x - ls * n;
-  if (ls >= nsites) return;
-  const long h = h0 + ls;
-  int x[4];
-  site_coords(g, par, h, x);
-  long nb[8];
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu) {
-    nb[mu] = nb_rank(g, x, mu, +1) * 3 * n + j;
-    nb[4 + mu] = nb_rank(g, x, mu, -1) * 3 * n + j;
+  // neighbour ranks of every site of the tile, shared by the site's threads
+  int *snb = reinterpret_cast<int *>(smem_raw + (STAGE ? (size_t)tile * 72 * sizeof(LS) : 0));
+  for (int k = threadIdx.x; k < nsites * 8; k += blockDim.x) {
+    const int site = k >> 3, d = k & 7;
+    int x[4];
+    site_coords(g, par, h0 + site, x);
+    const int mu = d & 3, st = d < 4 ? 1 : -1;
+    // neighbour coordinates without dynamic indexing of x[]
+    int y0 = x[0], y1 = x[1], y2 = x[2], y3 = x[3];
+    if (mu == 0) y0 = (y0 + st + g.L[0]) % g.L[0];
+    else if (mu == 1) y1 = (y1 + st + g.L[1]) % g.L[1];
+    else if (mu == 2) y2 = (y2 + st + g.L[2]) % g.L[2];
+    else y3 = (y3 + st + g.L[3]) % g.L[3];
+    const int lex = y0 + g.L[0] * (y1 + g.L[1] * (y2 + g.L[2] * y3));
+    snb[k] = (lex >> 1) * 3 * n;
   }
-  const C<T> *L = STAGE ? sl + ls * 72 : links + h * 72;
+  __syncthreads();
+  const int ls = threadIdx.x / tps;
+  const int j0 = (threadIdx.x - ls * tps) * R;
+  if (ls >= nsites) return;
+  const int h = h0 + ls;
+  const int o = h * 3 * n + j0;
   for (int b = 0; b < nbatch; ++b) {
     const C<T> *inb = in + b * bstride;
-    C<T> acc0 = czero<T>(), acc1 = czero<T>(), acc2 = czero<T>();
+    C<T> acc[3][R];
 #pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[c][r] = czero<T>();
+#pragma unroll 1
     for (int d = 0; d < 8; ++d) {
-      const C<T> v0 = inb[nb[d]], v1 = inb[nb[d] + n], v2 = inb[nb[d] + 2 * n];
-      const C<T> *l = L + d * 9;
-      cmac<T>(acc0, l[0], v0);
-      cmac<T>(acc0, l[1], v1);
-      cmac<T>(acc0, l[2], v2);
-      cmac<T>(acc1, l[3], v0);
-      cmac<T>(acc1, l[4], v1);
-      cmac<T>(acc1, l[5], v2);
-      cmac<T>(acc2, l[6], v0);
-      cmac<T>(acc2, l[7], v1);
-      cmac<T>(acc2, l[8], v2);
+      C<T> v[3][R];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Vec<T, R>::ld(inb + snb[ls * 8 + d] + j0 + c * n, v[c]);
+#pragma unroll
+      for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < 3; ++cb) {
+          LS e;
+          if (STAGE)
+            e = sl[ls * 72 + d * 9 + ca * 3 + cb];
+          else
+            expand(e, __ldg(links + (long)h * 72 + d * 9 + ca * 3 + cb));
+#pragma unroll
+          for (int r = 0; r < R; ++r) lmac(acc[ca][r], e, v[cb][r]);
+        }
     }
-    const long o = b * bstride + h * 3 * n + j;
+    C<T> *ob = out + b * bstride + o;
     if (SELF) {
-      const C<T> s0 = self[o], s1 = self[o + n], s2 = self[o + 2 * n];
-      out[o] = mk<T>(a * s0.x - acc0.x, a * s0.y - acc0.y);
-      out[o + n] = mk<T>(a * s1.x - acc1.x, a * s1.y - acc1.y);
-      out[o + 2 * n] = mk<T>(a * s2.x - acc2.x, a * s2.y - acc2.y);
-    } else {
-      out[o] = acc0;
-      out[o + n] = acc1;
-      out[o + 2 * n] = acc2;
+      const C<T> *sb = self + b * bstride + o;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C<T> sv[R];
+        Vec<T, R>::ld(sb + c * n, sv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[c][r] = mk<T>(a * sv[r].x - acc[c][r].x, a * sv[r].y - acc[c][r].y);
+      }
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Vec<T, R>::st(ob + c * n, acc[c]);
+  }
+}
+
+template <typename T, int R>
+static void launch_hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self,
+                       double a, int n, int nbatch, long bstride, cudaStream_t s) {
+  using LS = typename LinkSlot<T>::t;
+  const int tps = n / R;
+  const bool stage = tps >= 2;  // links are reused only when several threads share a site
+  const int tile = max(1, 128 / tps);
+  const int threads = ((tile * tps + 31) / 32) * 32;
+  const size_t smem = (stage ? (size_t)tile * 72 * sizeof(LS) : 0) + (size_t)tile * 8 * sizeof(int);
+  const unsigned grid = (unsigned)((g.Vh + tile - 1) / tile);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_hop<T, R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_hop<T, R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_hop<T, R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_hop<T, R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr_done = true;
+  }
+  if (self) {
+    if (stage)
+      k_hop<T, R, true, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
+    else
+      k_hop<T, R, true, false><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
+  } else {
+    if (stage)
+      k_hop<T, R, false, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
+    else
+      k_hop<T, R, false, false><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
   }
 }
 
 template <typename T>
 rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
                   int n, int nbatch, long bstride, cudaStream_t s) {
-  if (n < 1 || n > 256) return RHMC_ERR_INVALID_ARG;
-  const bool stage = n >= 4;
-  int tile = 256 / n;
-  if (!stage) tile = (n == 1) ? 128 : 64;
-  const int threads = ((tile * n + 31) / 32) * 32;
-  const size_t smem = stage ? (size_t)tile * 72 * sizeof(C<T>) : 0;
-  const long grid = (g.Vh + tile - 1) / tile;
-  static bool attr_done = false;  // FP64 at n = 4 stages 72 KB of links
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_hop<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_hop<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_done = true;
-  }
+  if (n < 1 || n > RHMC_MAX_NRHS || g.Vh * 3L * n > 0x7fffffffL) return RHMC_ERR_INVALID_ARG;
   prof_begin(sizeof(T) == 4 ? PROF_HOP32 : PROF_HOP64, s);
-  if (self) {
-    if (stage)
-      k_hop<T, true, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
-    else
-      k_hop<T, true, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
-  } else {
-    if (stage)
-      k_hop<T, false, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
-    else
-      k_hop<T, false, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
-  }
+  if (n % 4 == 0)
+    launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
+  else if (n % 2 == 0)
+    launch_hop<T, 2>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
+  else
+    launch_hop<T, 1>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   // algorithmic bytes: every link once, every input field once, the output once (+ self)
   prof_end(s, (double)g.Vh * sizeof(C<T>) * (72.0 + nbatch * 3.0 * n * (self ? 3 : 2)));
   RHMC_LAUNCH_CHECK();
