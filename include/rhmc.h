@@ -178,6 +178,15 @@ enum {
   RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER, RHMC_PROF_NCAT
 };
 rhmc_status_t rhmc_profile_enable(int on);
+
+/* Launch-parameter tuning, process-wide (used by the autotuner).  Keys:
+ *   RHMC_TUNE_HOP_RHS_PER_THREAD  right-hand sides per thread in the hop
+ *                                 kernel: 1, 2 or 4 (must divide n_rhs)
+ *   RHMC_TUNE_UPDATE_THREADS      threads per CTA of the fused shift update
+ * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
+enum { RHMC_TUNE_HOP_RHS_PER_THREAD = 0, RHMC_TUNE_UPDATE_THREADS = 1 };
+rhmc_status_t rhmc_tune_set(int key, int value);
+int rhmc_tune_get(int key);
 rhmc_status_t rhmc_profile_read(int category, long long *launches, double *ms, double *bytes);
 
 #ifdef __cplusplus

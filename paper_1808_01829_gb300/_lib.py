@@ -82,6 +82,10 @@ def load():
         lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
         lib.rhmc_last_error.restype = ctypes.c_char_p
         lib.rhmc_kernel_launches.restype = ctypes.c_longlong
+        lib.rhmc_tune_set.argtypes = [I, I]
+        lib.rhmc_tune_set.restype = I
+        lib.rhmc_tune_get.argtypes = [I]
+        lib.rhmc_tune_get.restype = I
         lib.rhmc_profile_enable.argtypes = [I]
         lib.rhmc_profile_enable.restype = I
         lib.rhmc_profile_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), PD, PD]
@@ -105,5 +109,5 @@ def exported_symbols():
     return [
         "rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_workspace_bytes", "rhmc_apply_mdagm_mrhs",
         "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
-        "rhmc_profile_enable", "rhmc_profile_read",
+        "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
     ]

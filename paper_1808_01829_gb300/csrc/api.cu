@@ -61,6 +61,9 @@ static cudaEvent_t pool_event() {
 
 bool prof_on() { return g_prof; }
 
+static int g_tune[TUNE_NKEYS] = {0};
+int tune_get(int key) { return (key >= 0 && key < TUNE_NKEYS) ? g_tune[key] : 0; }
+
 void prof_begin(int cat, cudaStream_t s) {
   if (!g_prof) return;
   ProfRec r{cat, pool_event(), pool_event(), 0.0};
@@ -491,6 +494,17 @@ extern "C" {
 const char *rhmc_last_error(void) { return rhmc::g_err; }
 
 long long rhmc_kernel_launches(void) { return rhmc::g_launches.load(); }
+
+rhmc_status_t rhmc_tune_set(int key, int value) {
+  if (key < 0 || key >= rhmc::TUNE_NKEYS || value < 0) {
+    set_error("rhmc_tune_set: bad key %d or value %d", key, value);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  rhmc::g_tune[key] = value;
+  return RHMC_OK;
+}
+
+int rhmc_tune_get(int key) { return rhmc::tune_get(key); }
 
 rhmc_status_t rhmc_profile_enable(int on) {
   rhmc::g_recs.clear();

@@ -92,6 +92,10 @@ enum ProfCat {
   PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_NCAT
 };
 bool prof_on();
+
+// Tunable launch parameters (rhmc_tune_set); 0 = built-in choice.
+enum TuneKey { TUNE_HOP_RHS_PER_THREAD = 0, TUNE_UPDATE_THREADS, TUNE_NKEYS };
+int tune_get(int key);
 void prof_begin(int cat, cudaStream_t s);
 void prof_end(cudaStream_t s, double bytes);
 

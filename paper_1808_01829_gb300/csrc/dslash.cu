@@ -70,33 +70,19 @@ rhmc_status_t stage_links(const Geom &g, const double2 *U, int bc_t, double2 *l6
 //
 // Thread layout: R right-hand sides per thread (register blocking), n / R
 // threads per site, `tile` sites per CTA.  The CTA stages the 72-complex link
-// records of its sites into shared memory once; in FP32 each link element is
-// stored expanded as (re, re, -im, im) so that a complex multiply-add is two
-// packed fma.rn.f32x2 operations on (re, im) and (im, re).
+// records of its sites into shared memory once, together with the 8 neighbour
+// offsets of each site.  The loop over the 8 directions keeps the next
+// direction's neighbour block in flight while the current one is multiplied.
 namespace {
 
-__device__ __forceinline__ void fma2(float2 &acc, float2 a, float2 b) {
-  unsigned long long r, x, y;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(acc.x), "f"(acc.y));
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(r) : "l"(x), "l"(y));
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(acc.x), "=f"(acc.y) : "l"(r));
+
+template <typename T> __device__ __forceinline__ void lmac(C<T> &acc, const C<T> &e, const C<T> &v) {
+  cmac<T>(acc, e, v);
 }
 
-// acc += L * v for an expanded FP32 link element e = (re, re, -im, im)
-__device__ __forceinline__ void lmac(float2 &acc, const float4 &e, const float2 &v) {
-  fma2(acc, make_float2(e.x, e.y), v);
-  fma2(acc, make_float2(e.z, e.w), make_float2(v.y, v.x));
-}
-__device__ __forceinline__ void lmac(double2 &acc, const double2 &e, const double2 &v) { cmac<double>(acc, e, v); }
+template <typename T> struct LinkSlot { using t = C<T>; };
 
-template <typename T> struct LinkSlot;
-template <> struct LinkSlot<float> { using t = float4; };
-template <> struct LinkSlot<double> { using t = double2; };
-
-__device__ __forceinline__ void expand(float4 &dst, float2 z) { dst = make_float4(z.x, z.x, -z.y, z.y); }
-__device__ __forceinline__ void expand(double2 &dst, double2 z) { dst = z; }
+template <typename T> __device__ __forceinline__ void expand(C<T> &dst, C<T> z) { dst = z; }
 
 // Vector load / store of R consecutive complex numbers.
 template <typename T, int R> struct Vec;
@@ -153,7 +139,7 @@ __global__ void __launch_bounds__(128) k_hop(Geom g, int par, const C<T> *__rest
   const int nsites = min(tile, (int)g.Vh - h0);
   if (STAGE) {
     const C<T> *src = links + (long)h0 * 72;
-    for (int k = threadIdx.x; k < nsites * 72; k += blockDim.x) expand(sl[k], __ldg(src + k));
+    for (int k = threadIdx.x; k < nsites * 72; k += blockDim.x) expand<T>(sl[k], __ldg(src + k));
     __syncthreads();
   }
   // neighbour ranks of every site of the tile, shared by the site's threads
@@ -185,11 +171,15 @@ __global__ void __launch_bounds__(128) k_hop(Geom g, int par, const C<T> *__rest
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[c][r] = czero<T>();
+    C<T> v[3][R], vn[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Vec<T, R>::ld(inb + snb[ls * 8] + j0 + c * n, v[c]);
 #pragma unroll 1
     for (int d = 0; d < 8; ++d) {
-      C<T> v[3][R];
+      // prefetch the next direction's neighbour block while this one is used
+      const int dn = d < 7 ? d + 1 : d;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Vec<T, R>::ld(inb + snb[ls * 8 + d] + j0 + c * n, v[c]);
+      for (int c = 0; c < 3; ++c) Vec<T, R>::ld(inb + snb[ls * 8 + dn] + j0 + c * n, vn[c]);
 #pragma unroll
       for (int ca = 0; ca < 3; ++ca)
 #pragma unroll
@@ -198,10 +188,14 @@ __global__ void __launch_bounds__(128) k_hop(Geom g, int par, const C<T> *__rest
           if (STAGE)
             e = sl[ls * 72 + d * 9 + ca * 3 + cb];
           else
-            expand(e, __ldg(links + (long)h * 72 + d * 9 + ca * 3 + cb));
+            expand<T>(e, __ldg(links + (long)h * 72 + d * 9 + ca * 3 + cb));
 #pragma unroll
-          for (int r = 0; r < R; ++r) lmac(acc[ca][r], e, v[cb][r]);
+          for (int r = 0; r < R; ++r) lmac<T>(acc[ca][r], e, v[cb][r]);
         }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[c][r] = vn[c][r];
     }
     C<T> *ob = out + b * bstride + o;
     if (SELF) {
@@ -255,9 +249,11 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
                   int n, int nbatch, long bstride, cudaStream_t s) {
   if (n < 1 || n > RHMC_MAX_NRHS || g.Vh * 3L * n > 0x7fffffffL) return RHMC_ERR_INVALID_ARG;
   prof_begin(sizeof(T) == 4 ? PROF_HOP32 : PROF_HOP64, s);
-  if (n % 4 == 0)
+  int R = tune_get(TUNE_HOP_RHS_PER_THREAD);
+  if (R <= 0 || n % R != 0) R = (n % 4 == 0) ? 4 : (n % 2 == 0 ? 2 : 1);
+  if (R == 4)
     launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
-  else if (n % 2 == 0)
+  else if (R == 2)
     launch_hop<T, 2>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   else
     launch_hop<T, 1>(g, par, links, in, out, self, a, n, nbatch, bstride, s);

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     with open(os.path.join(ROOT, "include", "rhmc.h")) as f:
         src = f.read()
-    return sorted(set(re.findall(r"^\s*(?:rhmc_status_t|size_t|const char \*|long long)\s*(rhmc_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:rhmc_status_t|size_t|const char \*|long long|int)\s*(rhmc_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")
