@@ -311,6 +311,7 @@ def run_gpu(args):
             "clocks": clk,
             "solver": {"iters": last.iters, "dirac_calls": last.dirac_calls, "reliable_updates": last.reliable_updates,
                        "refinements": last.refinements, "refine_iters": last.refine_iters,
+                       "phase1_rel_resid_max": last.phase1_rel_resid_max,
                        "true_rel_resid_max": last.true_rel_resid_max},
             "baseline_fp64_scg": base,
             "cpu_baseline": cpu,

@@ -86,6 +86,7 @@ typedef struct {
   int refinements;           /* per-shift defect-correction solves */
   int refine_iters;          /* iterations spent in them */
   double true_rel_resid_max; /* max_{s,j} ||B e_j - (A+sigma_s) X^(s) e_j|| / ||B e_j||, FP64 */
+  double phase1_rel_resid_max; /* the same before any defect correction */
   double *per_shift_resid;   /* optional caller array [n_shifts*n_rhs] (shift-major), or NULL */
 } rhmc_info_t;
 

@@ -51,6 +51,7 @@ class Info(ctypes.Structure):
         ("refinements", ctypes.c_int),
         ("refine_iters", ctypes.c_int),
         ("true_rel_resid_max", ctypes.c_double),
+        ("phase1_rel_resid_max", ctypes.c_double),
         ("per_shift_resid", ctypes.POINTER(ctypes.c_double)),
     ]
 

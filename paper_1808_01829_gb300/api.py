@@ -31,6 +31,7 @@ class SolveInfo:
     refinements: int
     refine_iters: int
     true_rel_resid_max: float
+    phase1_rel_resid_max: float
     per_shift_resid: list
 
 
@@ -124,7 +125,8 @@ class RhmcContext:
 
     def _info(self, info: _lib.Info, buf, ns, n):
         return SolveInfo(info.iters, info.dirac_calls, info.reliable_updates, info.refinements, info.refine_iters,
-                         info.true_rel_resid_max, [list(buf[q * n:(q + 1) * n]) for q in range(ns)])
+                         info.true_rel_resid_max, info.phase1_rel_resid_max,
+                         [list(buf[q * n:(q + 1) * n]) for q in range(ns)])
 
     # -- rhmc_block_multishift_cg
     def block_multishift_cg(self, B: torch.Tensor, shifts: Sequence[float], tol: float, max_iter: int = 0,
@@ -155,7 +157,7 @@ class RhmcContext:
         rc = self.lib.rhmc_multishift_cg_pervector(self._h, _ptr(B), n, ns, _doubles(shifts), _ptr(X), float(tol),
                                                    int(max_iter), None, ctypes.byref(info), _stream(B))
         _lib.check(rc, "rhmc_multishift_cg_pervector")
-        return X, SolveInfo(info.iters, info.dirac_calls, 0, 0, 0, -1.0, [])
+        return X, SolveInfo(info.iters, info.dirac_calls, 0, 0, 0, -1.0, -1.0, [])
 
     # -- rhmc_force
     def force(self, Phi: torch.Tensor, alpha0: float, alpha: Sequence[float], beta: Sequence[float], tol: float,

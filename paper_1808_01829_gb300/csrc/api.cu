@@ -90,7 +90,8 @@ void set_error(const char *fmt, ...) {
     if (st_ != RHMC_OK) return st_;     \
   } while (0)
 
-constexpr int kParts = 304;           // Gram partial sums (2 CTAs per SM)
+constexpr int kParts = 304;           // partial sums of the simple reductions (2 CTAs per SM)
+constexpr int kGramParts = 38;        // Gram partials: one per cluster of 8 CTAs (304 CTAs)
 constexpr double kReliableDelta = 0.1;
 constexpr int kCheckEvery = 8;        // iterations between host checks
 constexpr int kMaxRefine = 4;
@@ -209,7 +210,7 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   b.T64 = a.take<double2>(len);
   b.AP64 = a.take<double2>(len);
   b.rinv64 = a.take<double2>((size_t)n * n);
-  b.partial = a.take<double2>((size_t)kParts * n * n);
+  b.partial = a.take<double2>((size_t)kGramParts * n * n);
   b.npart = a.take<double>((size_t)kParts * kMaxN);
   b.st = a.take<SolverState>(1);
 }
@@ -285,11 +286,11 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   const long len = rows * n;
   C<T> *P = (C<T> *)b.P, *Q = (C<T> *)b.Q, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
-  RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kParts, s));
-  RHMC_TRY(nxn_alpha<T>(b.partial, kParts, n, b.st, k, (C<T> *)b.mw, s));
+  RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kGramParts, s));
+  RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
   RHMC_TRY(block_axpy<T, T>(AP, Q, (const C<T> *)b.mw, W, rows, n, s));
-  RHMC_TRY(gram<T>(W, W, rows, n, b.partial, kParts, s));
-  RHMC_TRY(nxn_rho<T>(b.partial, kParts, n, b.st, k, (C<T> *)b.coef, s));
+  RHMC_TRY(gram<T>(W, W, rows, n, b.partial, kGramParts, s));
+  RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, s));
   RHMC_TRY(update_all<T, TX>(W, Q, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, ns, rows, n, len, s));
   return RHMC_OK;
@@ -307,8 +308,8 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * ns, s));
   // line 2: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
-  RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kParts, s));
-  RHMC_TRY(nxn_qr_init<double>(b.partial, kParts, n, ns, b.st, b.rinv64, s));
+  RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kGramParts, s));
+  RHMC_TRY(nxn_qr_init<double>(b.partial, kGramParts, n, ns, b.st, b.rinv64, s));
   RHMC_TRY(block_axpy<double, T>(B, nullptr, b.rinv64, (C<T> *)b.Q, rows, n, s));
   for (int q = 0; q < ns; ++q)
     RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Q, sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
@@ -357,8 +358,8 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(apply_A<double>(c, X, b.AP64, b.T64, n, sigma0, s));
       RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
-      RHMC_TRY(gram<double>(b.R64, b.R64, rows, n, b.partial, kParts, s));
-      RHMC_TRY(nxn_reliable(b.partial, kParts, n, b.st, k, b.rinv64, s));
+      RHMC_TRY(gram<double>(b.R64, b.R64, rows, n, b.partial, kGramParts, s));
+      RHMC_TRY(nxn_reliable(b.partial, kGramParts, n, b.st, k, b.rinv64, s));
       RHMC_TRY(block_axpy<double, float>(b.R64, nullptr, b.rinv64, (float2 *)b.Q, rows, n, s));
       stats.dirac++;
       stats.reliable++;
@@ -418,7 +419,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   RHMC_TRY(colnorms(c, B, n, bn, b1.npart, s));
   for (int j = 0; j < n; ++j) bn[j] = std::sqrt(bn[j]);
   int refinements = 0, refine_iters = 0;
-  double worst = 0.0;
+  double worst = 0.0, worst1 = 0.0;
   std::vector<double> resid((size_t)ns * n, 0.0);
   for (int q = 0; q < ns; ++q) {
     double2 *Xq = X + q * len;
@@ -435,6 +436,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
         mx = std::max(mx, r);
         if (r > 0) ratio_min = std::min(ratio_min, prm.tol / r);
       }
+      if (round == 0) worst1 = std::max(worst1, mx);
       if (mx <= prm.tol || prm.fixed_iters > 0 || round >= kMaxRefine) {
         worst = std::max(worst, mx);
         break;
@@ -460,6 +462,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
     info->refinements = refinements;
     info->refine_iters = refine_iters;
     info->true_rel_resid_max = worst;
+    info->phase1_rel_resid_max = worst1;
     if (info->per_shift_resid) std::memcpy(info->per_shift_resid, resid.data(), sizeof(double) * resid.size());
   }
   if (prm.fixed_iters > 0) return RHMC_OK;
@@ -829,6 +832,7 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n,
     info->refinements = 0;
     info->refine_iters = 0;
     info->true_rel_resid_max = -1.0;
+    info->phase1_rel_resid_max = -1.0;
   }
   if (!all_ok) {
     set_error("per-vector multishift CG not converged");

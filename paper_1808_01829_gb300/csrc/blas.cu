@@ -10,74 +10,131 @@
 //               (lines 6-7 for s = 0 with M1 = alpha_k delta_{k-1}, M2 = rho_k^dagger;
 //                lines 11-12 with M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger)
 //   flush       X64 += X32, X32 = 0 (mixed precision reliable-update flush)
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace rhmc {
 
 // ------------------------------------------------------------ Gram partials
-// Thread layout: (ib, jb) 2x2 blocks of the n x n result, `rg` row groups.
-// Rows are staged through shared memory in tiles of TR rows.
-template <typename T, int N>
+// G = A^dagger B.  Thread layout: BS x BS blocks of the n x n result (register
+// blocking), the remaining threads split the rows into row groups.  Row tiles
+// of A and B are double-buffered in shared memory with cp.async.  Each CTA
+// reduces its row groups in FP64; the CTAs of a cluster of kGramCluster then
+// sum their partials through distributed shared memory in a fixed order, so
+// one FP64 partial per cluster reaches global memory (deterministic).
+constexpr int kGramCluster = 8;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;"); }
+
+template <typename T, int N, int BS, int TR>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
                                               double2 *__restrict__ partial) {
-  constexpr int NB = (N + 1) / 2;
+  constexpr int NB = N / BS;
   constexpr int NBLK = NB * NB;
   constexpr int RG = 256 / NBLK;
-  constexpr int TR = 64;
-  __shared__ C<T> sa[TR][N + 1], sb[TR][N + 1];
-  __shared__ double2 red[256];
+  constexpr int TE = TR * N;                       // complex per tile and operand
+  constexpr int V16 = (int)(TE * sizeof(C<T>) / 16);  // 16-byte chunks per tile and operand
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T> *sa = reinterpret_cast<C<T> *>(smem_raw);   // [2][TR][N]
+  C<T> *sb = sa + 2 * TE;                           // [2][TR][N]
+  double2 *red = reinterpret_cast<double2 *>(sb + 2 * TE);  // [N*N]
   const int t = threadIdx.x;
   const int blk = t % NBLK, grp = t / NBLK;
-  const int i0 = 2 * (blk / NB), j0 = 2 * (blk % NB);
-  C<T> acc[2][2];
+  const int i0 = BS * (blk / NB), j0 = BS * (blk % NB);
+  C<T> acc[BS][BS];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < BS; ++u)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) acc[u][v] = czero<T>();
-  const long per = (rows + gridDim.x - 1) / gridDim.x;
-  const long r0 = (long)blockIdx.x * per;
-  const long r1 = min(rows, r0 + per);
-  for (long rt = r0; rt < r1; rt += TR) {
-    const int nr = (int)min((long)TR, r1 - rt);
-    __syncthreads();
-    for (int k = t; k < nr * N; k += 256) {
-      const int r = k / N, c = k - r * N;
-      sa[r][c] = A[(rt + r) * N + c];
-      sb[r][c] = B[(rt + r) * N + c];
+    for (int v = 0; v < BS; ++v) acc[u][v] = czero<T>();
+  // this CTA's row range, whole tiles except possibly the last
+  const long ntiles_all = (rows + TR - 1) / TR;
+  const long per = (ntiles_all + gridDim.x - 1) / gridDim.x;
+  const long t0 = (long)blockIdx.x * per, t1 = min(ntiles_all, t0 + per);
+  auto load_tile = [&](long tile, int buf) {
+    const long r0 = tile * TR;
+    const int nr = (int)min((long)TR, rows - r0);
+    const int nv = (int)(nr * N * sizeof(C<T>) / 16);
+    const char *ga = reinterpret_cast<const char *>(A + r0 * N);
+    const char *gb = reinterpret_cast<const char *>(B + r0 * N);
+    char *da = reinterpret_cast<char *>(sa + buf * TE), *db = reinterpret_cast<char *>(sb + buf * TE);
+    for (int k = t; k < nv; k += 256) {
+      cp_async16(da + 16 * k, ga + 16 * k);
+      cp_async16(db + 16 * k, gb + 16 * k);
     }
+    // zero the ragged tail (only the last tile)
+    for (int k = nv + t; k < V16; k += 256) {
+      reinterpret_cast<int4 *>(da)[k] = make_int4(0, 0, 0, 0);
+      reinterpret_cast<int4 *>(db)[k] = make_int4(0, 0, 0, 0);
+    }
+  };
+  if (t0 < t1) load_tile(t0, 0);
+  cp_async_commit();
+  for (long tile = t0; tile < t1; ++tile) {
+    const int buf = (int)((tile - t0) & 1);
+    if (tile + 1 < t1) load_tile(tile + 1, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait_all_but_one();
     __syncthreads();
     if (grp < RG) {
-      for (int r = grp; r < nr; r += RG) {
-        const C<T> a0 = sa[r][i0], b0 = sb[r][j0];
-        const C<T> a1 = (i0 + 1 < N) ? sa[r][i0 + 1] : czero<T>();
-        const C<T> b1 = (j0 + 1 < N) ? sb[r][j0 + 1] : czero<T>();
-        cmac_cj<T>(acc[0][0], a0, b0);
-        cmac_cj<T>(acc[0][1], a0, b1);
-        cmac_cj<T>(acc[1][0], a1, b0);
-        cmac_cj<T>(acc[1][1], a1, b1);
+      const C<T> *ta = sa + buf * TE, *tb = sb + buf * TE;
+#pragma unroll 4
+      for (int r = grp; r < TR; r += RG) {
+        C<T> a[BS], b[BS];
+#pragma unroll
+        for (int u = 0; u < BS; ++u) {
+          a[u] = ta[r * N + i0 + u];
+          b[u] = tb[r * N + j0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < BS; ++u)
+#pragma unroll
+          for (int v = 0; v < BS; ++v) cmac_cj<T>(acc[u][v], a[u], b[v]);
       }
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+  // reduce the row groups in FP64 into red[N*N]
+  for (int k = t; k < N * N; k += 256) red[k] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int g = 0; g < RG; ++g) {
+    if (grp == g) {
+#pragma unroll
+      for (int u = 0; u < BS; ++u)
+#pragma unroll
+        for (int v = 0; v < BS; ++v) {
+          double2 &d = red[(i0 + u) * N + j0 + v];
+          d.x += (double)acc[u][v].x;
+          d.y += (double)acc[u][v].y;
+        }
+    }
+    __syncthreads();
+  }
+  // cluster reduction through distributed shared memory, fixed order
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  cl.sync();
+  if (cl.block_rank() == 0) {
+    for (int k = t; k < N * N; k += 256) {
+      double2 sum = red[k];
+      for (unsigned q = 1; q < cl.num_blocks(); ++q) {
+        const double2 *rem = cl.map_shared_rank(red, q);
+        sum.x += rem[k].x;
+        sum.y += rem[k].y;
+      }
+      partial[(long)(blockIdx.x / cl.num_blocks()) * N * N + k] = sum;
     }
   }
-  // reduce over row groups in FP64
-  double2 *out = partial + (long)blockIdx.x * N * N;
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      __syncthreads();
-      red[t] = make_double2((double)acc[u][v].x, (double)acc[u][v].y);
-      __syncthreads();
-      if (t < NBLK) {
-        double2 s = red[t];
-        for (int q = 1; q < RG; ++q) {
-          s.x += red[t + q * NBLK].x;
-          s.y += red[t + q * NBLK].y;
-        }
-        const int i = i0 + u, j = j0 + v;
-        if (i < N && j < N) out[i * N + j] = s;
-      }
-    }
+  cl.sync();
 }
 
 // ------------------------------------------------------------ Y = C + A M
@@ -112,61 +169,85 @@ __global__ void __launch_bounds__(256) k_block_axpy(const C<TA> *__restrict__ Ai
 // coef layout (type C<T>): [0, N*N) rho^-1; then for s: M1^(s) at (1+2s)*N*N,
 // M2^(s) at (2+2s)*N*N.  upd[s] != 0 selects the shifts updated this iteration.
 // X^(s) is of type TX (FP64 in the FP64 solver, FP32 partial sums in the mixed
-// one).  The coefficient pair of one shift at a time sits in shared memory.
-template <typename T, typename TX, int N>
-__global__ void __launch_bounds__(128) k_update_all(const C<T> *__restrict__ W, C<T> *__restrict__ Q,
+// one).
+//
+// Layout: CG output columns per thread, N / CG threads per row (consecutive
+// lanes of one warp), persistent grid-stride loop over rows.  All coefficient
+// matrices stay in shared memory for the whole launch.  A thread keeps the
+// full P^(s) row in registers; the lanes of a row finish reading it
+// (__syncwarp) before any of them overwrites its columns.
+template <typename T, typename TX, int N, int CG>
+__global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, C<T> *__restrict__ Q,
                                                     C<T> *__restrict__ P, TX *__restrict__ Xv,
                                                     const C<T> *__restrict__ coef, const int *__restrict__ upd,
                                                     int nshift, long rows, long fstride) {
-  __shared__ C<T> sr[N * N], s1[N * N], s2[N * N];
-  for (int k = threadIdx.x; k < N * N; k += blockDim.x) sr[k] = coef[k];
+  constexpr int TPR = N / CG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T> *sc = reinterpret_cast<C<T> *>(smem_raw);
+  __shared__ int supd[kMaxS];
+  const int ncoef = (1 + 2 * nshift) * N * N;
+  for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = coef[k];
+  for (int k = threadIdx.x; k < nshift; k += blockDim.x) supd[k] = upd[k];
   __syncthreads();
-  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = r < rows;
   using CX = C<TX>;
   CX *X = reinterpret_cast<CX *>(Xv);
-  // Q row = W row rho^-1  (rho^-1 is upper triangular)
-  C<T> q[N];
-  if (live) {
-    C<T> w[N];
+  const int lane_in_row = threadIdx.x % TPR;
+  const int j0 = lane_in_row * CG;
+  const long rows_per_cta = blockDim.x / TPR;
+  for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
+    const long r = rbase + threadIdx.x / TPR;
+    const bool live = r < rows;
+    // Q row slice = W row rho^-1  (rho^-1 is upper triangular)
+    C<T> q[CG];
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = W[r * N + k];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      C<T> acc = czero<T>();
-#pragma unroll
-      for (int k = 0; k <= j; ++k) cmac<T>(acc, w[k], sr[k * N + j]);
-      q[j] = acc;
-      Q[r * N + j] = acc;
-    }
-  }
-  for (int s = 0; s < nshift; ++s) {
-    if (!upd[s]) continue;  // uniform across the CTA
-    __syncthreads();
-    for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
-      s1[k] = coef[(1 + 2 * s) * N * N + k];
-      s2[k] = coef[(2 + 2 * s) * N * N + k];
-    }
-    __syncthreads();
-    if (!live) continue;
-    C<T> p[N];
-    C<T> *Ps = P + s * fstride + r * N;
-    CX *Xs = X + s * fstride + r * N;
-#pragma unroll
-    for (int k = 0; k < N; ++k) p[k] = Ps[k];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      C<T> a1 = czero<T>(), a2 = czero<T>();
+    for (int c = 0; c < CG; ++c) q[c] = czero<T>();
+    if (live) {
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        cmac<T>(a1, p[k], s1[k * N + j]);
-        cmac<T>(a2, p[k], s2[k * N + j]);
+        const C<T> w = W[r * N + k];
+#pragma unroll
+        for (int c = 0; c < CG; ++c)
+          if (k <= j0 + c) cmac<T>(q[c], w, sc[k * N + j0 + c]);
       }
-      CX x = Xs[j];
-      x.x += a1.x;
-      x.y += a1.y;
-      Xs[j] = x;
-      Ps[j] = mk<T>(q[j].x + a2.x, q[j].y + a2.y);
+#pragma unroll
+      for (int c = 0; c < CG; ++c) Q[r * N + j0 + c] = q[c];
+    }
+    for (int s = 0; s < nshift; ++s) {
+      if (!supd[s]) continue;
+      const C<T> *m1 = sc + (1 + 2 * s) * N * N;
+      const C<T> *m2 = m1 + N * N;
+      C<T> *Ps = P + s * fstride;
+      C<T> p[N];
+      if (live) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) p[k] = Ps[r * N + k];
+      }
+      __syncwarp();
+      if (live) {
+        C<T> a1[CG], a2[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+          a1[c] = czero<T>();
+          a2[c] = czero<T>();
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+          for (int c = 0; c < CG; ++c) {
+            cmac<T>(a1[c], p[k], m1[k * N + j0 + c]);
+            cmac<T>(a2[c], p[k], m2[k * N + j0 + c]);
+          }
+        CX *Xs = X + s * fstride + r * N + j0;
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+          CX x = Xs[c];
+          x.x += a1[c].x;
+          x.y += a1[c].y;
+          Xs[c] = x;
+          Ps[r * N + j0 + c] = mk<T>(q[c].x + a2[c].x, q[c].y + a2[c].y);
+        }
+      }
+      __syncwarp();
     }
   }
 }
@@ -268,12 +349,44 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
     default: return RHMC_ERR_INVALID_ARG; \
   }
 
+template <typename T, int N>
+static cudaError_t launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *partial, int nparts,
+                               cudaStream_t s) {
+  constexpr int BS = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
+  constexpr int TR = sizeof(T) == 4 ? 128 : 64;
+  const size_t smem = 4 * (size_t)TR * N * sizeof(C<T>) + (size_t)N * N * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram<T, N, BS, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nparts * kGramCluster);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kGramCluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gram<T, N, BS, TR>, A, B, rows, partial);
+}
+
+// nparts: number of FP64 partial n x n sums written (one per cluster of CTAs).
 template <typename T>
 rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *partial, int nparts, cudaStream_t s) {
   prof_begin(sizeof(T) == 4 ? PROF_GRAM32 : PROF_GRAM64, s);
-#define L_GRAM(NN) k_gram<T, NN><<<nparts, 256, 0, s>>>(A, B, rows, partial)
+  cudaError_t e = cudaSuccess;
+#define L_GRAM(NN) e = launch_gram<T, NN>(A, B, rows, partial, nparts, s)
   RHMC_DISPATCH_N(n, L_GRAM)
 #undef L_GRAM
+  if (e != cudaSuccess) {
+    set_error("gram launch: %s", cudaGetErrorString(e));
+    return RHMC_ERR_CUDA;
+  }
   prof_end(s, (double)rows * n * sizeof(C<T>) * (A == B ? 1 : 2));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
@@ -301,14 +414,32 @@ template rhmc_status_t block_axpy<double, double>(const double2 *, const double2
 template rhmc_status_t block_axpy<double, float>(const double2 *, const float2 *, const double2 *, float2 *, long,
                                                  int, cudaStream_t);
 
+template <typename T, typename TX, int N>
+static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
+                          long rows, long fstride, cudaStream_t s) {
+  constexpr int CG = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
+  const size_t smem = (size_t)(1 + 2 * nshift) * N * N * sizeof(C<T>);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_update_all<T, TX, N, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  int threads = tune_get(TUNE_UPDATE_THREADS);
+  if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
+  const long rows_per_cta = threads / (N / CG);
+  long grid = (rows + rows_per_cta - 1) / rows_per_cta;
+  grid = std::min(grid, (long)(8 * 152));
+  k_update_all<T, TX, N, CG><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd,
+                                                                   nshift, rows, fstride);
+}
+
 template <typename T, typename TX>
 rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
                          long rows, int n, long fstride, cudaStream_t s) {
-  const int bs = 128;
-  const long grid = (rows + bs - 1) / bs;
-#define L_UPD(NN)                                                                                     \
-  k_update_all<T, TX, NN><<<grid, bs, 0, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd, nshift, rows, \
-                                              fstride)
+  if ((size_t)(1 + 2 * nshift) * n * n * sizeof(C<T>) > 220 * 1024) {
+    set_error("update_all: %d shifts at n = %d exceed the shared-memory coefficient store", nshift, n);
+    return RHMC_ERR_INVALID_ARG;
+  }
   int nupd = nshift;
   if (prof_on()) {  // profiling only: count the shifts this launch updates (host sync)
     int h[kMaxS];
@@ -317,6 +448,7 @@ rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *
     for (int q = 0; q < nshift; ++q) nupd += h[q] != 0;
   }
   prof_begin(sizeof(T) == 4 ? PROF_UPDATE32 : PROF_UPDATE64, s);
+#define L_UPD(NN) launch_update<T, TX, NN>(W, Q, P, X, coef, upd, nshift, rows, fstride, s)
   RHMC_DISPATCH_N(n, L_UPD)
 #undef L_UPD
   prof_end(s, (double)rows * n * (2.0 * sizeof(C<T>) + nupd * 2.0 * (sizeof(C<T>) + sizeof(C<TX>))));

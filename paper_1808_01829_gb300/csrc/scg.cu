@@ -13,15 +13,25 @@
 
 namespace rhmc {
 
+// Sum of nparts partials by the whole CTA (256 threads); valid in every thread.
 static __device__ double reduce_parts(const double *p, int nparts) {
+  __shared__ double red[256];
   double s = 0.0;
-  for (int q = 0; q < nparts; ++q) s += p[q];
-  return s;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) s += p[q];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
 }
 
 __global__ void k_scg_init(ScgScalars *sc, const double *parts, int nparts, int ns, const double *sigma) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double rr = reduce_parts(parts, nparts);
+  if (threadIdx.x != 0) return;
   sc->rr = rr;
   sc->bb = rr;
   sc->alpha_prev = 1.0;
@@ -38,8 +48,8 @@ __global__ void k_scg_init(ScgScalars *sc, const double *parts, int nparts, int 
 
 // alpha_k and the shifted alphas
 __global__ void k_scg_alpha(ScgScalars *sc, const double *parts, int nparts, int ns) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double pAp = reduce_parts(parts, nparts);
+  if (threadIdx.x != 0) return;
   if (!(pAp > 0.0)) sc->breakdown = 1;
   const double a = sc->rr / pAp;
   sc->alpha = a;
@@ -95,8 +105,8 @@ __global__ void __launch_bounds__(256) k_scg_update1(const ScgScalars *__restric
 
 // beta_k, shifted betas, freezing, roll the recurrence
 __global__ void k_scg_beta(ScgScalars *sc, const double *parts, int nparts, int ns, double tol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double rr_new = reduce_parts(parts, nparts);
+  if (threadIdx.x != 0) return;
   const double b = rr_new / sc->rr;
   sc->beta = b;
   sc->beta_s[0] = b;
@@ -146,12 +156,12 @@ __global__ void k_column(const double2 *__restrict__ in, double2 *__restrict__ o
 
 rhmc_status_t scg_init(ScgScalars *sc, const double *parts, int nparts, int ns, const double *sigma_dev,
                        cudaStream_t s) {
-  k_scg_init<<<1, 32, 0, s>>>(sc, parts, nparts, ns, sigma_dev);
+  k_scg_init<<<1, 256, 0, s>>>(sc, parts, nparts, ns, sigma_dev);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
 rhmc_status_t scg_alpha(ScgScalars *sc, const double *parts, int nparts, int ns, cudaStream_t s) {
-  k_scg_alpha<<<1, 32, 0, s>>>(sc, parts, nparts, ns);
+  k_scg_alpha<<<1, 256, 0, s>>>(sc, parts, nparts, ns);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
@@ -162,7 +172,7 @@ rhmc_status_t scg_update1(const ScgScalars *sc, double2 *r, const double2 *Ap, d
   return RHMC_OK;
 }
 rhmc_status_t scg_beta(ScgScalars *sc, const double *parts, int nparts, int ns, double tol, cudaStream_t s) {
-  k_scg_beta<<<1, 32, 0, s>>>(sc, parts, nparts, ns, tol);
+  k_scg_beta<<<1, 256, 0, s>>>(sc, parts, nparts, ns, tol);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }

@@ -62,18 +62,23 @@ __device__ void set_eye(const Cta &c, double2 *D) {
   __syncthreads();
 }
 
-// Sum the per-CTA partials of a Gram matrix into G.
+// Sum the per-cluster partials of a Gram matrix into G (8 loads in flight per thread).
 __device__ void reduce_partials(const Cta &c, double2 *G, const double2 *partial, int nparts) {
   if (c.own) {
-    double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
     const int nn = c.n * c.n;
+    double2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_double2(0, 0);
     int p = 0;
-    for (; p + 1 < nparts; p += 2) {
-      s0 = cadd(s0, partial[(long)p * nn + c.t]);
-      s1 = cadd(s1, partial[(long)(p + 1) * nn + c.t]);
+    for (; p + 8 <= nparts; p += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = cadd(acc[q], partial[(long)(p + q) * nn + c.t]);
     }
-    if (p < nparts) s0 = cadd(s0, partial[(long)p * nn + c.t]);
-    G[c.t] = cadd(s0, s1);
+    for (; p < nparts; ++p) acc[0] = cadd(acc[0], partial[(long)p * nn + c.t]);
+    double2 sum = acc[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) sum = cadd(sum, acc[q]);
+    G[c.t] = sum;
   }
   __syncthreads();
 }
