@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(256) k_block_axpy(const C<TA> *__restrict__ Ai
 // one).
 //
 // Layout: CG output columns per thread, N / CG threads per row (consecutive
-// lanes of one warp), persistent grid-stride loop over rows.  All coefficient
+// lanes of one warp; a row never straddles two warps), persistent grid-stride
+// loop over rows.  All coefficient
 // matrices stay in shared memory for the whole launch.  A thread keeps the
 // full P^(s) row in registers; the lanes of a row finish reading it
 // (__syncwarp) before any of them overwrites its columns.
@@ -191,12 +192,15 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   __syncthreads();
   using CX = C<TX>;
   CX *X = reinterpret_cast<CX *>(Xv);
-  const int lane_in_row = threadIdx.x % TPR;
-  const int j0 = lane_in_row * CG;
-  const long rows_per_cta = blockDim.x / TPR;
+  // rows never straddle a warp: 32 / TPR rows per warp, remaining lanes idle
+  constexpr int RPW = 32 / TPR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / TPR;
+  const int j0 = (lane - slot * TPR) * CG;
+  const long rows_per_cta = (long)(blockDim.x >> 5) * RPW;
   for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
-    const long r = rbase + threadIdx.x / TPR;
-    const bool live = r < rows;
+    const long r = rbase + (long)warp * RPW + slot;
+    const bool live = slot < RPW && r < rows;
     // Q row slice = W row rho^-1  (rho^-1 is upper triangular)
     C<T> q[CG];
 #pragma unroll
@@ -426,7 +430,7 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
   }
   int threads = tune_get(TUNE_UPDATE_THREADS);
   if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
-  const long rows_per_cta = threads / (N / CG);
+  const long rows_per_cta = (long)(threads / 32) * (32 / (N / CG));
   long grid = (rows + rows_per_cta - 1) / rows_per_cta;
   grid = std::min(grid, (long)(8 * 152));
   k_update_all<T, TX, N, CG><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd,

@@ -37,6 +37,11 @@ CONFIGS = [
     ((8, 8, 8, 8), 0.05, 4, (-1.0 / 16, 2e-3, 64.0, 12), 0.5, 1e-10, "fp64"),
     ((8, 8, 8, 8), 0.05, 4, (-1.0 / 16, 2e-3, 64.0, 12), 0.5, 1e-8, "mixed"),
     ((4, 6, 4, 8), 0.03, 5, (-1.0 / 20, 1e-3, 64.0, 6), 0.5, 1e-9, "mixed"),
+    # widths whose rows do not tile a warp evenly (3, 6, 12 lanes per row group)
+    ((4, 4, 4, 4), 0.1, 3, (-1.0 / 12, 1e-3, 64.0, 5), 0.5, 1e-9, "mixed"),
+    ((4, 4, 4, 6), 0.1, 6, (-1.0 / 24, 1e-3, 64.0, 5), 0.5, 1e-10, "fp64"),
+    ((4, 4, 4, 4), 0.05, 12, (-1.0 / 48, 2e-3, 64.0, 12), 0.5, 1e-8, "mixed"),
+    ((6, 4, 4, 4), 0.05, 16, (-1.0 / 64, 2e-3, 64.0, 12), 0.5, 1e-8, "mixed"),
 ]
 
 
