@@ -184,8 +184,20 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_HOP_RHS_PER_THREAD  right-hand sides per thread in the hop
  *                                 kernel: 1, 2 or 4 (must divide n_rhs)
  *   RHMC_TUNE_UPDATE_THREADS      threads per CTA of the fused shift update
+ *   RHMC_TUNE_FLUSH_EVERY         mixed precision: add the FP32 solution increments
+ *                                 into the FP64 solutions every k iterations as
+ *                                 well as at reliable updates (0: only there)
+ *   RHMC_TUNE_RELIABLE_DELTA_MILLI  mixed precision: reliable update when the
+ *                                 base residual fell by value/1000 (0: 0.1)
+ *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 8)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
-enum { RHMC_TUNE_HOP_RHS_PER_THREAD = 0, RHMC_TUNE_UPDATE_THREADS = 1 };
+enum {
+  RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
+  RHMC_TUNE_UPDATE_THREADS = 1,
+  RHMC_TUNE_FLUSH_EVERY = 2,
+  RHMC_TUNE_RELIABLE_DELTA_MILLI = 3,
+  RHMC_TUNE_CHECK_EVERY = 4
+};
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);
 rhmc_status_t rhmc_profile_read(int category, long long *launches, double *ms, double *bytes);

@@ -322,10 +322,14 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   }
   const double target = prm.tol;
   double res_at_reliable = 1.0;
-  int k = 0;
+  const int check_every = tune_get(TUNE_CHECK_EVERY) > 0 ? tune_get(TUNE_CHECK_EVERY) : kCheckEvery;
+  const int flush_every = tune_get(TUNE_FLUSH_EVERY);
+  const double rel_delta = tune_get(TUNE_RELIABLE_DELTA_MILLI) > 0 ? 1e-3 * tune_get(TUNE_RELIABLE_DELTA_MILLI)
+                                                                     : kReliableDelta;
+  int k = 0, last_flush = 0;
   const int kmax = prm.fixed_iters > 0 ? prm.fixed_iters : prm.max_iter;
   while (k < kmax) {
-    const int chunk = prm.fixed_iters > 0 ? kmax : std::min(kCheckEvery, kmax - k);
+    const int chunk = prm.fixed_iters > 0 ? kmax : std::min(check_every, kmax - k);
     for (int q = 0; q < chunk; ++q) {
       ++k;
       if (mixed)
@@ -353,7 +357,11 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     bool shifts_done = true;
     for (int q = 1; q < ns; ++q) shifts_done = shifts_done && !v.active[q];
     const bool converged = base < target && shifts_done;
-    if (mixed && (base < kReliableDelta * res_at_reliable || converged)) {
+    if (mixed && flush_every > 0 && k - last_flush >= flush_every) {
+      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      last_flush = k;
+    }
+    if (mixed && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(apply_A<double>(c, X, b.AP64, b.T64, n, sigma0, s));

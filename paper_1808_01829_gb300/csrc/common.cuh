@@ -94,7 +94,14 @@ enum ProfCat {
 bool prof_on();
 
 // Tunable launch parameters (rhmc_tune_set); 0 = built-in choice.
-enum TuneKey { TUNE_HOP_RHS_PER_THREAD = 0, TUNE_UPDATE_THREADS, TUNE_NKEYS };
+enum TuneKey {
+  TUNE_HOP_RHS_PER_THREAD = 0,
+  TUNE_UPDATE_THREADS,
+  TUNE_FLUSH_EVERY,          // mixed: also flush FP32 increments every k iterations (0: at reliable updates only)
+  TUNE_RELIABLE_DELTA_MILLI, // mixed: reliable update when the base residual fell by this / 1000 (0: 100)
+  TUNE_CHECK_EVERY,          // iterations between host convergence checks (0: 8)
+  TUNE_NKEYS
+};
 int tune_get(int key);
 void prof_begin(int cat, cudaStream_t s);
 void prof_end(cudaStream_t s, double bytes);
