@@ -125,6 +125,9 @@ struct rhmc_ctx {
   size_t pool_bytes = 0;
   double *h_pin = nullptr;  // pinned host staging (readbacks)
   size_t h_pin_bytes = 0;
+  cudaStream_t side = nullptr;     // shifted coefficient steps and updates
+  cudaEvent_t ev_base[3] = {};     // base update of iteration k done (slot k % 3)
+  cudaEvent_t ev_side[3] = {};     // shifted updates of iteration k done
 };
 
 namespace rhmc {
@@ -185,7 +188,7 @@ static rhmc_status_t apply_A(const rhmc_ctx *c, const C<T> *X, C<T> *Y, C<T> *tm
 // ------------------------------------------------------------ solver workspace
 struct SolveBufs {
   // precision-specific fields (T = float or double)
-  void *P, *Q, *W, *AP, *Todd, *Xinc;  // Xinc: FP32 increments (mixed only)
+  void *P, *Qb[2], *W, *AP, *Todd, *Xinc;  // Qb: Q_k in Qb[k & 1]; Xinc: FP32 increments (mixed only)
   void *coef, *mw;
   // FP64 helpers
   double2 *R64, *T64, *AP64, *rinv64;
@@ -199,7 +202,8 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
   auto field = [&](size_t count) { return (void *)a.take<char>(count * len * esz); };
   b.P = field(ns);
-  b.Q = field(1);
+  b.Qb[0] = field(1);
+  b.Qb[1] = field(1);
   b.W = field(1);
   b.AP = field(1);
   b.Todd = field(1);
@@ -278,21 +282,44 @@ static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cuda
   return RHMC_OK;
 }
 
-// One SBCGrQ iteration (device work only).
+// One SBCGrQ iteration (device work only).  The base recursion runs on the
+// caller's stream s; with more than one shift the shifted coefficient step and
+// the shifted updates of iteration k run on the context's side stream, where
+// they overlap iteration k+1 of the base.  Ordering:
+//   side(k)   waits for the base update of k (Q_k, rho_k, alpha_k in place);
+//   base(k)   waits for side(k-2) before it overwrites the state slot k % 3 and
+//             the buffer Q_k = Qb[k & 1] that side(k-2) was reading.
 template <typename T, typename TX>
 static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc, int n, int ns, double sigma0, int k,
                                       double tol_shift, int freeze, cudaStream_t s) {
   const long rows = c->g.Vh * 3;
   const long len = rows * n;
-  C<T> *P = (C<T> *)b.P, *Q = (C<T> *)b.Q, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
+  C<T> *P = (C<T> *)b.P, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
+  C<T> *Qprev = (C<T> *)b.Qb[(k - 1) & 1], *Qcur = (C<T> *)b.Qb[k & 1];
+  const bool split = ns > 1;
+  if (split && k >= 3) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[(k - 2) % 3], 0));
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
   RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kGramParts, s));
   RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
-  RHMC_TRY(block_axpy<T, T>(AP, Q, (const C<T> *)b.mw, W, rows, n, s));
+  RHMC_TRY(block_axpy<T, T>(AP, Qprev, (const C<T> *)b.mw, W, rows, n, s));
   RHMC_TRY(gram<T>(W, W, rows, n, b.partial, kGramParts, s));
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
-  RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, s));
-  RHMC_TRY(update_all<T, TX>(W, Q, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, ns, rows, n, len, s));
+  // base: Q_k = W rho_k^-1, X^(0), P^(0)
+  RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 0, 1, 1, rows, n, len, s));
+  if (split) {
+    RHMC_CUDA_TRY(cudaEventRecord(c->ev_base[k % 3], s));
+    RHMC_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_base[k % 3], 0));
+    RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, c->side));
+    RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
+                               c->side));
+    RHMC_CUDA_TRY(cudaEventRecord(c->ev_side[k % 3], c->side));
+  }
+  return RHMC_OK;
+}
+
+// Make stream s wait for everything enqueued so far on the side stream.
+static rhmc_status_t join_side(rhmc_ctx *c, int k, int ns, cudaStream_t s) {
+  if (ns > 1 && k >= 1) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[k % 3], 0));
   return RHMC_OK;
 }
 
@@ -308,11 +335,19 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * ns, s));
   // line 2: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
-  RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kGramParts, s));
-  RHMC_TRY(nxn_qr_init<double>(b.partial, kGramParts, n, ns, b.st, b.rinv64, s));
-  RHMC_TRY(block_axpy<double, T>(B, nullptr, b.rinv64, (C<T> *)b.Q, rows, n, s));
+  if (mixed) {
+    // the FP32 basis only needs FP32 orthonormality: QR of the rounded block
+    RHMC_TRY((convert<double, float>(B, (float2 *)b.W, len, s)));
+    RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.partial, kGramParts, s));
+    RHMC_TRY(nxn_qr_init<float>(b.partial, kGramParts, n, ns, b.st, (float2 *)b.mw, s));
+    RHMC_TRY((block_axpy<float, float>((float2 *)b.W, nullptr, (float2 *)b.mw, (float2 *)b.Qb[0], rows, n, s)));
+  } else {
+    RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kGramParts, s));
+    RHMC_TRY(nxn_qr_init<double>(b.partial, kGramParts, n, ns, b.st, b.rinv64, s));
+    RHMC_TRY(block_axpy<double, T>(B, nullptr, b.rinv64, (C<T> *)b.Qb[0], rows, n, s));
+  }
   for (int q = 0; q < ns; ++q)
-    RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Q, sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
+    RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Qb[0], sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
   if (mixed) RHMC_CUDA_TRY(cudaMemsetAsync(b.Xinc, 0, sizeof(float2) * len * ns, s));
   StateView v;
   RHMC_TRY(read_state(c, b.st, v, s));
@@ -340,6 +375,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
                                                     prm.fixed_iters > 0 ? 0 : 1, s)));
       stats.dirac++;
     }
+    RHMC_TRY(join_side(c, k, ns, s));
     RHMC_TRY(read_state(c, b.st, v, s));
     if (v.breakdown) {
       set_error("breakdown in coefficient step %d at iteration %d", v.breakdown, k);
@@ -366,9 +402,11 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(apply_A<double>(c, X, b.AP64, b.T64, n, sigma0, s));
       RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
-      RHMC_TRY(gram<double>(b.R64, b.R64, rows, n, b.partial, kGramParts, s));
-      RHMC_TRY(nxn_reliable(b.partial, kGramParts, n, b.st, k, b.rinv64, s));
-      RHMC_TRY(block_axpy<double, float>(b.R64, nullptr, b.rinv64, (float2 *)b.Q, rows, n, s));
+      // thin QR of the FP32-rounded true residual (Q is an FP32 basis)
+      RHMC_TRY((convert<double, float>(b.R64, (float2 *)b.W, len, s)));
+      RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.partial, kGramParts, s));
+      RHMC_TRY(nxn_reliable<float>(b.partial, kGramParts, n, b.st, k, (float2 *)b.mw, s));
+      RHMC_TRY((block_axpy<float, float>((float2 *)b.W, nullptr, (float2 *)b.mw, (float2 *)b.Qb[k & 1], rows, n, s)));
       stats.dirac++;
       stats.reliable++;
       RHMC_TRY(read_state(c, b.st, v, s));
@@ -581,7 +619,18 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
       return RHMC_ERR_CUDA;
     }
   }
-  // the staged-link hop for FP64 at n = 4 needs 72 KB of shared memory
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("rhmc_create: cannot create the side stream");
+    rhmc_destroy(c);
+    return RHMC_ERR_CUDA;
+  }
+  for (int q = 0; q < 3; ++q)
+    if (cudaEventCreateWithFlags(&c->ev_base[q], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_side[q], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("rhmc_create: cannot create events");
+      rhmc_destroy(c);
+      return RHMC_ERR_CUDA;
+    }
   *out = c;
   return RHMC_OK;
 }
@@ -593,8 +642,14 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
     if (c->l64[p]) cudaFree(c->l64[p]);
     if (c->l32[p]) cudaFree(c->l32[p]);
   }
+  if (c->side) cudaStreamSynchronize(c->side);
   if (c->pool) cudaFree(c->pool);
   if (c->h_pin) cudaFreeHost(c->h_pin);
+  for (int q = 0; q < 3; ++q) {
+    if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
+    if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);
+  }
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
   return RHMC_OK;
 }

@@ -181,14 +181,15 @@ template <typename T, typename TX, int N, int CG>
 __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, C<T> *__restrict__ Q,
                                                     C<T> *__restrict__ P, TX *__restrict__ Xv,
                                                     const C<T> *__restrict__ coef, const int *__restrict__ upd,
-                                                    int nshift, long rows, long fstride) {
+                                                    int s_begin, int s_end, int compute_q, long rows, long fstride) {
   constexpr int TPR = N / CG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T> *sc = reinterpret_cast<C<T> *>(smem_raw);
+  C<T> *sc = reinterpret_cast<C<T> *>(smem_raw);  // rho^-1 (if compute_q), then the pairs of [s_begin, s_end)
   __shared__ int supd[kMaxS];
-  const int ncoef = (1 + 2 * nshift) * N * N;
-  for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = coef[k];
-  for (int k = threadIdx.x; k < nshift; k += blockDim.x) supd[k] = upd[k];
+  const int c0 = compute_q ? 0 : (1 + 2 * s_begin) * N * N;  // first coefficient staged
+  const int ncoef = (1 + 2 * s_end) * N * N - c0;
+  for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = coef[c0 + k];
+  for (int k = threadIdx.x; k < s_end; k += blockDim.x) supd[k] = upd[k];
   __syncthreads();
   using CX = C<TX>;
   CX *X = reinterpret_cast<CX *>(Xv);
@@ -201,24 +202,29 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
     const long r = rbase + (long)warp * RPW + slot;
     const bool live = slot < RPW && r < rows;
-    // Q row slice = W row rho^-1  (rho^-1 is upper triangular)
+    // Q row slice = W row rho^-1  (rho^-1 is upper triangular), or read it
     C<T> q[CG];
 #pragma unroll
     for (int c = 0; c < CG; ++c) q[c] = czero<T>();
     if (live) {
+      if (compute_q) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const C<T> w = W[r * N + k];
+        for (int k = 0; k < N; ++k) {
+          const C<T> w = W[r * N + k];
 #pragma unroll
-        for (int c = 0; c < CG; ++c)
-          if (k <= j0 + c) cmac<T>(q[c], w, sc[k * N + j0 + c]);
+          for (int c = 0; c < CG; ++c)
+            if (k <= j0 + c) cmac<T>(q[c], w, sc[k * N + j0 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CG; ++c) Q[r * N + j0 + c] = q[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < CG; ++c) q[c] = Q[r * N + j0 + c];
       }
-#pragma unroll
-      for (int c = 0; c < CG; ++c) Q[r * N + j0 + c] = q[c];
     }
-    for (int s = 0; s < nshift; ++s) {
+    for (int s = s_begin; s < s_end; ++s) {
       if (!supd[s]) continue;
-      const C<T> *m1 = sc + (1 + 2 * s) * N * N;
+      const C<T> *m1 = sc + (1 + 2 * s) * N * N - c0;
       const C<T> *m2 = m1 + N * N;
       C<T> *Ps = P + s * fstride;
       C<T> p[N];
@@ -419,10 +425,10 @@ template rhmc_status_t block_axpy<double, float>(const double2 *, const float2 *
                                                  int, cudaStream_t);
 
 template <typename T, typename TX, int N>
-static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
-                          long rows, long fstride, cudaStream_t s) {
+static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
+                          int s_end, int compute_q, long rows, long fstride, cudaStream_t s) {
   constexpr int CG = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
-  const size_t smem = (size_t)(1 + 2 * nshift) * N * N * sizeof(C<T>);
+  const size_t smem = (size_t)((1 + 2 * s_end) - (compute_q ? 0 : 1 + 2 * s_begin)) * N * N * sizeof(C<T>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_all<T, TX, N, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -434,35 +440,36 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
   long grid = (rows + rows_per_cta - 1) / rows_per_cta;
   grid = std::min(grid, (long)(8 * 152));
   k_update_all<T, TX, N, CG><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd,
-                                                                   nshift, rows, fstride);
+                                                                   s_begin, s_end, compute_q, rows, fstride);
 }
 
 template <typename T, typename TX>
-rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
-                         long rows, int n, long fstride, cudaStream_t s) {
-  if ((size_t)(1 + 2 * nshift) * n * n * sizeof(C<T>) > 220 * 1024) {
-    set_error("update_all: %d shifts at n = %d exceed the shared-memory coefficient store", nshift, n);
+rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
+                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s) {
+  if ((size_t)(1 + 2 * s_end) * n * n * sizeof(C<T>) > 220 * 1024) {
+    set_error("update_all: %d shifts at n = %d exceed the shared-memory coefficient store", s_end, n);
     return RHMC_ERR_INVALID_ARG;
   }
-  int nupd = nshift;
+  int nupd = s_end - s_begin;
   if (prof_on()) {  // profiling only: count the shifts this launch updates (host sync)
     int h[kMaxS];
-    cudaMemcpy(h, upd, sizeof(int) * nshift, cudaMemcpyDeviceToHost);
+    cudaStreamSynchronize(s);
+    cudaMemcpy(h, upd, sizeof(int) * s_end, cudaMemcpyDeviceToHost);
     nupd = 0;
-    for (int q = 0; q < nshift; ++q) nupd += h[q] != 0;
+    for (int q = s_begin; q < s_end; ++q) nupd += h[q] != 0;
   }
   prof_begin(sizeof(T) == 4 ? PROF_UPDATE32 : PROF_UPDATE64, s);
-#define L_UPD(NN) launch_update<T, TX, NN>(W, Q, P, X, coef, upd, nshift, rows, fstride, s)
+#define L_UPD(NN) launch_update<T, TX, NN>(W, Q, P, X, coef, upd, s_begin, s_end, compute_q, rows, fstride, s)
   RHMC_DISPATCH_N(n, L_UPD)
 #undef L_UPD
-  prof_end(s, (double)rows * n * (2.0 * sizeof(C<T>) + nupd * 2.0 * (sizeof(C<T>) + sizeof(C<TX>))));
+  prof_end(s, (double)rows * n * ((compute_q ? 2.0 : 1.0) * sizeof(C<T>) + nupd * 2.0 * (sizeof(C<T>) + sizeof(C<TX>))));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
 template rhmc_status_t update_all<float, float>(const float2 *, float2 *, float2 *, float2 *, const float2 *,
-                                                const int *, int, long, int, long, cudaStream_t);
+                                                const int *, int, int, int, long, int, long, cudaStream_t);
 template rhmc_status_t update_all<double, double>(const double2 *, double2 *, double2 *, double2 *, const double2 *,
-                                                  const int *, int, long, int, long, cudaStream_t);
+                                                  const int *, int, int, int, long, int, long, cudaStream_t);
 
 rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s) {
   const int bs = 256;

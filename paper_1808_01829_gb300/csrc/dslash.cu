@@ -250,7 +250,8 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
   if (n < 1 || n > RHMC_MAX_NRHS || g.Vh * 3L * n > 0x7fffffffL) return RHMC_ERR_INVALID_ARG;
   prof_begin(sizeof(T) == 4 ? PROF_HOP32 : PROF_HOP64, s);
   int R = tune_get(TUNE_HOP_RHS_PER_THREAD);
-  if (R <= 0 || n % R != 0) R = (n % 4 == 0) ? 4 : (n % 2 == 0 ? 2 : 1);
+  // measured at 24^4 (FP32): 2 per thread best for n >= 12, 1 otherwise; FP64 is ALU bound
+  if (R <= 0 || n % R != 0) R = (sizeof(T) == 4 && n >= 12 && n % 2 == 0) ? 2 : 1;
   if (R == 4)
     launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   else if (R == 2)

@@ -9,13 +9,16 @@ constexpr int kMaxN = RHMC_MAX_NRHS;
 constexpr int kMaxS = RHMC_MAX_SHIFTS;
 
 // Device-resident state of the SBCGrQ coefficient recursion (FP64).  Matrices
-// are n x n row-major in the first n*n entries.  Slots [k & 1] hold iteration
-// k's alpha, Gram1 (= alpha^-1), rho and delta.
+// are n x n row-major in the first n*n entries.  Slot k % kSlots holds
+// iteration k's alpha, Gram1 (= alpha^-1), rho and delta: the shifted
+// coefficient step of iteration k reads slots k and k-1 while the base step of
+// iteration k+1 already writes slot k+1 on another stream.
+constexpr int kSlots = 3;
 struct SolverState {
-  double2 alpha[2][kMaxN * kMaxN];
-  double2 G1[2][kMaxN * kMaxN];
-  double2 rho[2][kMaxN * kMaxN];
-  double2 delta[2][kMaxN * kMaxN];
+  double2 alpha[kSlots][kMaxN * kMaxN];
+  double2 G1[kSlots][kMaxN * kMaxN];
+  double2 rho[kSlots][kMaxN * kMaxN];
+  double2 delta[kSlots][kMaxN * kMaxN];
   double2 beta_s[kMaxS][kMaxN * kMaxN];
   double2 alpha_s[kMaxS][kMaxN * kMaxN];
   double sigma[kMaxS];        // shifts, ascending
@@ -39,9 +42,11 @@ rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *part
 template <typename TA, typename TY>
 rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY> *Y, long rows, int n,
                          cudaStream_t s);
+// Shifts [s_begin, s_end): X^(s) += P^(s) M1^(s), P^(s) = Q + P^(s) M2^(s).
+// compute_q: first form Q = W rho^-1 (and store it); otherwise read Q.
 template <typename T, typename TX>
-rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int nshift,
-                         long rows, int n, long fstride, cudaStream_t s);
+rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
+                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s);
 rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s);
 template <typename TI, typename TO>
 rhmc_status_t convert(const C<TI> *in, C<TO> *out, long len, cudaStream_t s);
@@ -62,7 +67,8 @@ rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st
 template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
                          cudaStream_t s);
-rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, double2 *rinv,
+template <typename T>
+rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *rinv,
                            cudaStream_t s);
 
 // force.cu

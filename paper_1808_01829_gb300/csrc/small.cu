@@ -3,8 +3,8 @@
 // A CTA of 256 threads works on n x n complex matrices (n <= 16) held in
 // shared memory, thread t owning element (t / n, t % n).  The state of the
 // recursion lives in a SolverState in device memory; quantities of iteration
-// k are written to slot k & 1 and those of k-1 read from slot (k-1) & 1, so
-// consecutive launches never overwrite what the next one still reads.
+// k are written to slot k % 3 and those of k-1 read from slot (k-1) % 3, so a
+// launch never overwrites what a launch still running on the other stream reads.
 //
 //   qr_init   {Q_0, delta_0} = qr(B) by Cholesky of B^dagger B   (line 2)
 //   alpha     alpha_k = (P^dagger (A + sigma_0) P)^-1            (line 4)
@@ -33,10 +33,41 @@ __device__ __forceinline__ double2 cmulz(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ double2 conjz(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 cdivz(double2 a, double2 b) {
-  const double d = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+// FP64 reciprocal and square root without the long IEEE sequences (FP64 is
+// latency-bound here): an FP32 estimate of the scaled mantissa refined by
+// Newton-Raphson in FP64, r <- r + r (1 - x r) for 1/x, and
+// y <- y (3 - x y^2) / 2 for 1/sqrt(x) followed by s <- s + y (x - s^2) / 2.
+// Two (three) steps take the 2^-23 estimate to full double precision.
+__device__ __forceinline__ double frcp(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  double r = ldexp((double)__frcp_rn((float)m), -e);
+  double err = fma(-x, r, 1.0);
+  r = fma(r, err, r);
+  err = fma(-x, r, 1.0);
+  return fma(r, err, r);
 }
+__device__ __forceinline__ double fsqrt(double x) {
+  if (!(x > 0.0)) return 0.0;
+  int e;
+  double m = frexp(x, &e);  // x = m 2^e, m in [0.5, 1)
+  if (e & 1) {
+    m *= 2.0;
+    e -= 1;
+  }
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-0.5 * m * y, y, 1.5);
+  y = y * fma(-0.5 * m * y, y, 1.5);
+  double sq = m * y;
+  sq = fma(0.5 * y, fma(-sq, sq, m), sq);
+  return ldexp(sq, e / 2);
+}
+// a / b = a conj(b) / |b|^2
+__device__ __forceinline__ double2 cdivz(double2 a, double2 b) {
+  const double r = frcp(b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double r) { return make_double2(a.x * r, a.y * r); }
 
 // C = op(A) op(B); ca / cb: use the adjoint of A / B.  C may not alias A or B.
 __device__ void mm(const Cta &c, double2 *Cm, const double2 *A, const double2 *B, bool ca = false, bool cb = false) {
@@ -96,18 +127,18 @@ __device__ bool cholesky(const Cta &c, double2 *A, int *flag) {
   if (c.own) A[c.t] = h;
   if (c.t == 0) *flag = 0;
   __syncthreads();
+  __shared__ double rpiv;
   for (int k = 0; k < n; ++k) {
     if (c.t == 0) {
       const double d = A[k * n + k].x;
       if (!(d > 0.0) || !isfinite(d)) *flag = 1;
-      A[k * n + k] = make_double2(sqrt(fmax(d, 0.0)), 0.0);
+      const double sd = fsqrt(fmax(d, 0.0));
+      A[k * n + k] = make_double2(sd, 0.0);
+      rpiv = frcp(sd);
     }
     __syncthreads();
     if (*flag) return false;
-    if (c.t > k && c.t < n) {
-      const double dk = A[k * n + k].x;
-      A[c.t * n + k] = make_double2(A[c.t * n + k].x / dk, A[c.t * n + k].y / dk);
-    }
+    if (c.t > k && c.t < n) A[c.t * n + k] = cscale(A[c.t * n + k], rpiv);
     __syncthreads();
     if (c.own && c.i > k && c.j > k && c.j <= c.i)
       A[c.t] = csub(A[c.t], cmulz(A[c.i * n + k], conjz(A[c.j * n + k])));
@@ -119,16 +150,19 @@ __device__ bool cholesky(const Cta &c, double2 *A, int *flag) {
 }
 
 // Inverse of an upper-triangular R (R^-1 upper).  Thread j < n owns column j.
+// The diagonal of R is real and positive (Cholesky factors).
 __device__ void inv_upper(const Cta &c, double2 *Ri, const double2 *R) {
   const int n = c.n;
+  __shared__ double rd[kMaxN];
   if (c.own) Ri[c.t] = make_double2(0, 0);
+  if (c.t < n) rd[c.t] = frcp(R[c.t * n + c.t].x);
   __syncthreads();
   if (c.t < n) {
     const int j = c.t;
     for (int i = j; i >= 0; --i) {
       double2 s = make_double2(i == j ? 1.0 : 0.0, 0.0);
       for (int k = i + 1; k <= j; ++k) s = csub(s, cmulz(R[i * n + k], Ri[k * n + j]));
-      Ri[i * n + j] = cdivz(s, R[i * n + i]);
+      Ri[i * n + j] = cscale(s, rd[i]);
     }
   }
   __syncthreads();
@@ -163,12 +197,17 @@ __device__ bool inv_general(const Cta &c, double2 *Ai, double2 *A, int *piv, int
       M[p * n + col] = tmp;
     }
     __syncthreads();
-    const double2 d = A[k * n + k];
+    __shared__ double2 dinv;
+    if (c.t == 0) {
+      const double2 d = A[k * n + k];
+      const double r = frcp(d.x * d.x + d.y * d.y);
+      dinv = make_double2(d.x * r, -d.y * r);
+    }
     __syncthreads();
     if (c.t < 2 * n) {
       const int col = c.t % n;
       double2 *M = (c.t < n) ? A : Ai;
-      M[k * n + col] = cdivz(M[k * n + col], d);
+      M[k * n + col] = cmulz(M[k * n + col], dinv);
     }
     __syncthreads();
     // eliminate column k from the other rows; factors read before any write
@@ -189,9 +228,12 @@ __device__ bool inv_general(const Cta &c, double2 *Ai, double2 *A, int *piv, int
 }
 
 __device__ double colnorm(const Cta &c, const double2 *A, int j) {
-  double s = 0.0;
-  for (int i = 0; i < c.n; ++i) s += A[i * c.n + j].x * A[i * c.n + j].x + A[i * c.n + j].y * A[i * c.n + j].y;
-  return sqrt(s);
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = 0; i < c.n; ++i) {
+    s0 = fma(A[i * c.n + j].x, A[i * c.n + j].x, s0);
+    s1 = fma(A[i * c.n + j].y, A[i * c.n + j].y, s1);
+  }
+  return fsqrt(s0 + s1);
 }
 
 template <typename T>
@@ -250,7 +292,7 @@ __global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int n
   __shared__ double2 G[NN], L[NN], Li[NN], A[NN];
   __shared__ int flag;
   Cta c(n);
-  const int cur = k & 1;
+  const int cur = k % kSlots;
   reduce_partials(c, G, partial, nparts);
   if (c.own) {
     // Hermitian part (the Gram of P with an Hermitian operator)
@@ -280,7 +322,7 @@ __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int npa
   __shared__ double2 G[NN], R[NN], Ri[NN], M[NN];
   __shared__ int flag;
   Cta c(n);
-  const int cur = k & 1, prev = (k - 1) & 1;
+  const int cur = k % kSlots, prev = (k - 1) % kSlots;
   const int nn = n * n;
   reduce_partials(c, G, partial, nparts);
   if (!cholesky(c, G, &flag)) {
@@ -315,7 +357,7 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   Cta c(n);
   const int s = blockIdx.x + 1;
   if (s >= nshift) return;
-  const int cur = k & 1, prev = (k - 1) & 1;
+  const int cur = k % kSlots, prev = (k - 1) % kSlots;
   const int nn = n * n;
   if (!st->active[s]) {
     if (c.t == 0) st->upd[s] = 0;
@@ -357,13 +399,16 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   // shifted residual delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k = rho_k Gram1_k alpha^(s)_k
   mm(c, A1, st->rho[cur], st->G1[cur]);
   mm(c, B, A1, A2);
+  __shared__ double colres[kMaxN];
+  if (c.t < n) {
+    const double r = colnorm(c, B, c.t) * frcp(st->d0[c.t]);
+    colres[c.t] = r;
+    st->res[s][c.t] = r;
+  }
+  __syncthreads();
   if (c.t == 0) {
     double mx = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double r = colnorm(c, B, j) / st->d0[j];
-      st->res[s][j] = r;
-      mx = fmax(mx, r);
-    }
+    for (int j = 0; j < n; ++j) mx = fmax(mx, colres[j]);
     st->upd[s] = 1;
     if (freeze && mx < tol_shift) st->active[s] = 0;
   }
@@ -371,12 +416,13 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
 
 // Reliable update: delta_k <- R factor of the true residual (Gram partials of
 // R^dagger R); writes (delta')^-1 for Q = R (delta')^-1.
+template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st,
-                                                      int k, double2 *rinv_out) {
+                                                      int k, C<T> *rinv_out) {
   __shared__ double2 G[NN], R[NN], Ri[NN];
   __shared__ int flag;
   Cta c(n);
-  const int cur = k & 1;
+  const int cur = k % kSlots;
   reduce_partials(c, G, partial, nparts);
   if (!cholesky(c, G, &flag)) {
     if (c.t == 0) st->breakdown = 5;
@@ -385,10 +431,8 @@ __global__ void __launch_bounds__(256) k_nxn_reliable(const double2 *partial, in
   if (c.own) R[c.t] = conjz(G[c.j * n + c.i]);
   __syncthreads();
   inv_upper(c, Ri, R);
-  if (c.own) {
-    st->delta[cur][c.t] = R[c.t];
-    rinv_out[c.t] = Ri[c.t];
-  }
+  if (c.own) st->delta[cur][c.t] = R[c.t];
+  store_coef<T>(c, rinv_out, Ri);
   if (c.t < n) st->res[0][c.t] = colnorm(c, R, c.t) / st->d0[c.t];
 }
 
@@ -430,10 +474,11 @@ rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, 
   }
   return RHMC_OK;
 }
-rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, double2 *rinv,
+template <typename T>
+rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *rinv,
                            cudaStream_t s) {
   prof_begin(PROF_NXN, s);
-  k_nxn_reliable<<<1, 256, 0, s>>>(partial, nparts, n, st, k, rinv);
+  k_nxn_reliable<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, rinv);
   prof_end(s, 0.0);
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
@@ -443,7 +488,8 @@ rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverStat
   template rhmc_status_t nxn_qr_init<T>(const double2 *, int, int, int, SolverState *, C<T> *, cudaStream_t); \
   template rhmc_status_t nxn_alpha<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);   \
   template rhmc_status_t nxn_rho<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);     \
-  template rhmc_status_t nxn_shifts<T>(int, int, SolverState *, int, C<T> *, double, int, cudaStream_t);
+  template rhmc_status_t nxn_shifts<T>(int, int, SolverState *, int, C<T> *, double, int, cudaStream_t);      \
+  template rhmc_status_t nxn_reliable<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);
 RHMC_INST_NXN(float)
 RHMC_INST_NXN(double)
 
