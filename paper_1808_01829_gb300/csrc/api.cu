@@ -244,6 +244,7 @@ struct SolveParams {
   int max_iter;
   bool mixed;
   int fixed_iters;  // > 0: exactly this many iterations, no freezing, no checks
+  bool verify_at_convergence = true;  // mixed: reliable update before declaring convergence
 };
 
 struct SolveStats {
@@ -397,6 +398,11 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       last_flush = k;
     }
+    if (mixed && converged && !prm.verify_at_convergence) {
+      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      stats.iters = k;
+      return RHMC_OK;
+    }
     if (mixed && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
@@ -491,6 +497,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
       SolveParams pr = prm;
       pr.tol = std::min(0.1, 0.5 * ratio_min);
       pr.fixed_iters = 0;
+      pr.verify_at_convergence = false;  // the FP64 true residual is checked right after
       SolveStats st1;
       rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s)
                                    : solve_phase1<double>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s);
