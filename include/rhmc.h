@@ -113,6 +113,22 @@ size_t rhmc_workspace_bytes(const rhmc_ctx_t *ctx, int n_rhs, int n_shifts, rhmc
 rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, double sigma,
                                     rhmc_precision_t p, rhmc_stream_t s);
 
+/* The same operator application as rhmc_apply_mdagm_mrhs with p = RHMC_FP64,
+ * for callers that must not allocate device memory (inside a stream capture,
+ * under a fixed memory budget, or under a framework that owns all
+ * allocation).  The paper has no counterpart; this is a deployment variant.
+ * It allocates nothing: the odd-parity intermediate lives in a file-scope
+ * device array of fixed size (32 MiB, i.e. V/2 * 3 * n_rhs * 16 bytes at most,
+ * e.g. a 16^4 lattice with 16 right-hand sides), which every GPU that loads
+ * the library holds until the process exits.  Larger problems are rejected
+ * with INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Requires rhmc_set_gauge (NO_GAUGE otherwise). */
+rhmc_status_t rhmc_apply_mdagm_mrhs_noalloc(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, double sigma,
+                                            rhmc_stream_t s);
+
 /* One staggered hop Y = D X onto parity out_parity (0: D_eo, input odd;
  * 1: D_oe, input even).  Same layouts and precision rule as above. */
 rhmc_status_t rhmc_hop(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, int out_parity,

@@ -526,6 +526,20 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   return RHMC_OK;
 }
 
+rhmc_status_t ctx_geometry(const rhmc_ctx_t *c, int *device, Geom *g, double *mass, const double2 **l64_even,
+                           const double2 **l64_odd) {
+  if (!c->have_gauge) {
+    set_error("gauge field not set");
+    return RHMC_ERR_NO_GAUGE;
+  }
+  *device = c->device;
+  *g = c->g;
+  *mass = c->mass;
+  *l64_even = c->l64[0];
+  *l64_odd = c->l64[1];
+  return RHMC_OK;
+}
+
 // ------------------------------------------------------------ per-vector SCG baseline
 static size_t scg_bytes(const Geom &g, int ns) {
   Arena a(nullptr);

@@ -75,6 +75,11 @@ rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverStat
 rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
                           const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
 
+// api.cu: read-only view of a context (device, geometry, mass, staged FP64
+// links of the two output parities); NO_GAUGE before rhmc_set_gauge.
+rhmc_status_t ctx_geometry(const rhmc_ctx_t *ctx, int *device, Geom *g, double *mass, const double2 **l64_even,
+                           const double2 **l64_odd);
+
 // scg.cu (per-vector FP64 multishift CG baseline)
 struct ScgState;
 
