@@ -166,13 +166,21 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *ctx, const void *B_dev, i
  *   alpha, beta  host [n_shifts]: residues and poles of Eq. (RA), beta > 0
  *   X_in      optional complex128 [n_shifts][V/2][3][n_pf] solutions of
  *             (A + beta_s) X = Phi; NULL = solve them (block solver, tol, p)
- *   G         complex128 [V][4][3][3] output
- *   S_out     optional host double, the action
+ *   G         complex128 [V][4][3][3] output, or NULL for the action only
+ *   S_out     optional host double, the action (G and S_out may not both be NULL)
  * The force arithmetic is FP64 in both precision modes. */
 rhmc_status_t rhmc_force(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
                          const double *beta, int n_shifts, double tol, int max_iter, rhmc_precision_t p,
                          const void *X_in_dev, void *G_dev, double *S_out, void *workspace, rhmc_info_t *info,
                          rhmc_stream_t s);
+
+/* R(A) Phi of Eq. (RA) from given shifted solutions:
+ *   Y = alpha0 Phi + sum_s alpha_s X^(s),   X^(s) = (A + beta_s)^-1 Phi,
+ * Phi, Y complex128 [V/2][3][n_pf]; X complex128 [n_shifts][V/2][3][n_pf];
+ * alpha host [n_shifts].  Y may not alias X.  (The gradient of the action
+ * with respect to Phi is 2 R(A) Phi.)  Asynchronous on stream s. */
+rhmc_status_t rhmc_rational_apply(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
+                                  int n_shifts, const void *X_dev, void *Y_dev, rhmc_stream_t s);
 
 /* Thread-local message describing the last failing call ("" if none). */
 const char *rhmc_last_error(void);

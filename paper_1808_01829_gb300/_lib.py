@@ -83,6 +83,8 @@ def load():
         lib.rhmc_block_multishift_cg.argtypes = [P, P, I, I, PD, P, D, I, I, P, ctypes.POINTER(Info), P]
         lib.rhmc_multishift_cg_pervector.argtypes = [P, P, I, I, PD, P, D, I, P, ctypes.POINTER(Info), P]
         lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
+        lib.rhmc_rational_apply.argtypes = [P, P, I, D, PD, I, P, P, P]
+        lib.rhmc_rational_apply.restype = I
         lib.rhmc_last_error.restype = ctypes.c_char_p
         lib.rhmc_kernel_launches.restype = ctypes.c_longlong
         lib.rhmc_tune_set.argtypes = [I, I]
@@ -113,5 +115,5 @@ def exported_symbols():
         "rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_workspace_bytes", "rhmc_apply_mdagm_mrhs",
         "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
         "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
-        "rhmc_apply_mdagm_mrhs_noalloc",
+        "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply",
     ]

@@ -925,10 +925,23 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n,
   return RHMC_OK;
 }
 
+rhmc_status_t rhmc_rational_apply(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, const double *alpha,
+                                  int ns, const void *X, void *Y, rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, Phi, Y, n));
+  if (!X || !alpha || ns < 1 || ns > RHMC_MAX_SHIFTS) {
+    set_error("rhmc_rational_apply: null X/alpha or n_shifts out of range");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  const long len = c->g.Vh * 3 * n;
+  return rational_combine((const double2 *)Phi, alpha0, alpha, (const double2 *)X, ns, len, (double2 *)Y, s);
+}
+
 rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, const double *alpha,
                          const double *beta, int ns, double tol, int max_iter, rhmc_precision_t p, const void *X_in,
                          void *G, double *S_out, void *ws, rhmc_info_t *info, rhmc_stream_t sv) {
-  RHMC_TRY(check_common(c, Phi, G, n));
+  RHMC_TRY(check_common(c, Phi, G ? G : (void *)S_out, n));
   if (!alpha || !beta) {
     set_error("rhmc_force: null alpha/beta");
     return RHMC_ERR_INVALID_ARG;
@@ -957,9 +970,11 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
   double2 *Y = fa.take<double2>((size_t)ns * len);
   double *alpha_d = fa.take<double>(kMaxS);
   double *parts = fa.take<double>(kParts);
-  RHMC_CUDA_TRY(cudaMemcpyAsync(alpha_d, alpha, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
-  RHMC_TRY(hop<double>(c->g, 1, c->l64[1], X, Y, nullptr, 0.0, n, ns, len, s));
-  RHMC_TRY(force_links(c->g, X, Y, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+  if (G) {
+    RHMC_CUDA_TRY(cudaMemcpyAsync(alpha_d, alpha, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+    RHMC_TRY(hop<double>(c->g, 1, c->l64[1], X, Y, nullptr, 0.0, n, ns, len, s));
+    RHMC_TRY(force_links(c->g, X, Y, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+  }
   if (S_out) {
     RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts));
     double S = 0.0;

@@ -80,6 +80,36 @@ __global__ void __launch_bounds__(256) k_force(Geom g, const double2 *__restrict
   }
 }
 
+// Y = alpha0 Phi + sum_s alpha_s X^(s): the rational approximation R(A) Phi of
+// Eq. (RA) from the shifted solutions (FP64).
+struct Coeffs {
+  double a[kMaxS];
+};
+
+__global__ void k_rational_combine(const double2 *__restrict__ Phi, double alpha0, const Coeffs alpha,
+                                   const double2 *__restrict__ X, int ns, long len, double2 *__restrict__ Y) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  const double2 p = Phi[i];
+  double2 y = make_double2(alpha0 * p.x, alpha0 * p.y);
+  for (int s = 0; s < ns; ++s) {
+    const double2 x = X[s * len + i];
+    y.x = fma(alpha.a[s], x.x, y.x);
+    y.y = fma(alpha.a[s], x.y, y.y);
+  }
+  Y[i] = y;
+}
+
+rhmc_status_t rational_combine(const double2 *Phi, double alpha0, const double *alpha_host, const double2 *X, int ns,
+                               long len, double2 *Y, cudaStream_t s) {
+  if (ns < 1 || ns > kMaxS) return RHMC_ERR_INVALID_ARG;
+  Coeffs c{};
+  for (int q = 0; q < ns; ++q) c.a[q] = alpha_host[q];
+  k_rational_combine<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(Phi, alpha0, c, X, ns, len, Y);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
 rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
                           const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s) {
   const long pairs = 4 * g.V;
