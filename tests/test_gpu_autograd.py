@@ -36,7 +36,7 @@ def test_gradients_match_finite_differences(dims, mass, n, rp):
     # action against the oracle
     Xo, _, _ = oracle.sbcgrq(dims, mass, U0, P0, ra.beta, tol=1e-13)
     So = oracle.action(ra.alpha0, ra.alpha, P0, Xo)
-    assert abs(float(S) - So) <= 1e-10 * abs(So)
+    assert abs(float(S.detach()) - So) <= 1e-10 * abs(So)
     rng = np.random.default_rng(7)
     h = 1e-4
     for _ in range(3):
