@@ -297,7 +297,10 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   const long len = rows * n;
   C<T> *P = (C<T> *)b.P, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
   C<T> *Qprev = (C<T> *)b.Qb[(k - 1) & 1], *Qcur = (C<T> *)b.Qb[k & 1];
-  const bool split = ns > 1;
+  // With the profiler on, the shifted steps run on s as well (same kernels,
+  // serialised) so that per-kernel event times are not inflated by overlap.
+  const bool split = ns > 1 && !prof_on();
+  cudaStream_t ss = split ? c->side : s;
   if (split && k >= 3) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[(k - 2) % 3], 0));
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
   RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kGramParts, s));
@@ -307,20 +310,22 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
   RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 0, 1, 1, rows, n, len, s));
-  if (split) {
-    RHMC_CUDA_TRY(cudaEventRecord(c->ev_base[k % 3], s));
-    RHMC_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_base[k % 3], 0));
-    RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, c->side));
+  if (ns > 1) {
+    if (split) {
+      RHMC_CUDA_TRY(cudaEventRecord(c->ev_base[k % 3], s));
+      RHMC_CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_base[k % 3], 0));
+    }
+    RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, ss));
     RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
-                               c->side));
-    RHMC_CUDA_TRY(cudaEventRecord(c->ev_side[k % 3], c->side));
+                               ss));
+    if (split) RHMC_CUDA_TRY(cudaEventRecord(c->ev_side[k % 3], ss));
   }
   return RHMC_OK;
 }
 
 // Make stream s wait for everything enqueued so far on the side stream.
 static rhmc_status_t join_side(rhmc_ctx *c, int k, int ns, cudaStream_t s) {
-  if (ns > 1 && k >= 1) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[k % 3], 0));
+  if (ns > 1 && k >= 1 && !prof_on()) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[k % 3], 0));
   return RHMC_OK;
 }
 

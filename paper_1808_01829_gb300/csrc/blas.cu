@@ -21,33 +21,23 @@ namespace rhmc {
 
 // ------------------------------------------------------------ Gram partials
 // G = A^dagger B.  Thread layout: BS x BS blocks of the n x n result (register
-// blocking), the remaining threads split the rows into row groups.  Row tiles
-// of A and B are double-buffered in shared memory with cp.async.  Each CTA
-// reduces its row groups in FP64; the CTAs of a cluster of kGramCluster then
-// sum their partials through distributed shared memory in a fixed order, so
-// one FP64 partial per cluster reaches global memory (deterministic).
+// blocking); the threads of one row group read each row's BS-wide chunks
+// straight from global memory (the lanes that share a chunk are served by one
+// L1 access), two rows in flight per thread.  FP32 products accumulate in FP32
+// per thread; each CTA reduces its row groups in FP64, and the CTAs of a
+// cluster of kGramCluster sum their partials through distributed shared memory
+// in a fixed order, so one FP64 partial per cluster reaches global memory
+// (deterministic).
 constexpr int kGramCluster = 8;
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;"); }
 
-template <typename T, int N, int BS, int TR>
+template <typename T, int N, int BS>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
                                               double2 *__restrict__ partial) {
   constexpr int NB = N / BS;
-  constexpr int NBLK = NB * NB;
-  constexpr int RG = 256 / NBLK;
-  constexpr int TE = TR * N;                       // complex per tile and operand
-  constexpr int V16 = (int)(TE * sizeof(C<T>) / 16);  // 16-byte chunks per tile and operand
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C<T> *sa = reinterpret_cast<C<T> *>(smem_raw);   // [2][TR][N]
-  C<T> *sb = sa + 2 * TE;                           // [2][TR][N]
-  double2 *red = reinterpret_cast<double2 *>(sb + 2 * TE);  // [N*N]
+  constexpr int NBLK = NB * NB;   // threads per row group
+  constexpr int RG = 256 / NBLK;  // row groups per CTA
+  __shared__ double2 red[N * N];
   const int t = threadIdx.x;
   const int blk = t % NBLK, grp = t / NBLK;
   const int i0 = BS * (blk / NB), j0 = BS * (blk % NB);
@@ -56,54 +46,40 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   for (int u = 0; u < BS; ++u)
 #pragma unroll
     for (int v = 0; v < BS; ++v) acc[u][v] = czero<T>();
-  // this CTA's row range, whole tiles except possibly the last
-  const long ntiles_all = (rows + TR - 1) / TR;
-  const long per = (ntiles_all + gridDim.x - 1) / gridDim.x;
-  const long t0 = (long)blockIdx.x * per, t1 = min(ntiles_all, t0 + per);
-  auto load_tile = [&](long tile, int buf) {
-    const long r0 = tile * TR;
-    const int nr = (int)min((long)TR, rows - r0);
-    const int nv = (int)(nr * N * sizeof(C<T>) / 16);
-    const char *ga = reinterpret_cast<const char *>(A + r0 * N);
-    const char *gb = reinterpret_cast<const char *>(B + r0 * N);
-    char *da = reinterpret_cast<char *>(sa + buf * TE), *db = reinterpret_cast<char *>(sb + buf * TE);
-    for (int k = t; k < nv; k += 256) {
-      cp_async16(da + 16 * k, ga + 16 * k);
-      cp_async16(db + 16 * k, gb + 16 * k);
-    }
-    // zero the ragged tail (only the last tile)
-    for (int k = nv + t; k < V16; k += 256) {
-      reinterpret_cast<int4 *>(da)[k] = make_int4(0, 0, 0, 0);
-      reinterpret_cast<int4 *>(db)[k] = make_int4(0, 0, 0, 0);
-    }
-  };
-  if (t0 < t1) load_tile(t0, 0);
-  cp_async_commit();
-  for (long tile = t0; tile < t1; ++tile) {
-    const int buf = (int)((tile - t0) & 1);
-    if (tile + 1 < t1) load_tile(tile + 1, buf ^ 1);
-    cp_async_commit();
-    cp_async_wait_all_but_one();
-    __syncthreads();
-    if (grp < RG) {
-      const C<T> *ta = sa + buf * TE, *tb = sb + buf * TE;
-#pragma unroll 4
-      for (int r = grp; r < TR; r += RG) {
-        C<T> a[BS], b[BS];
+  if (grp < RG) {
+    // rows of this row group: grp + RG * (blockIdx + gridDim * k), two at a time
+    const long stride = (long)RG * gridDim.x;
+    long r = (long)blockIdx.x * RG + grp;
+    for (; r + stride < rows; r += 2 * stride) {
+      C<T> a0[BS], b0[BS], a1[BS], b1[BS];
 #pragma unroll
-        for (int u = 0; u < BS; ++u) {
-          a[u] = ta[r * N + i0 + u];
-          b[u] = tb[r * N + j0 + u];
-        }
-#pragma unroll
-        for (int u = 0; u < BS; ++u)
-#pragma unroll
-          for (int v = 0; v < BS; ++v) cmac_cj<T>(acc[u][v], a[u], b[v]);
+      for (int u = 0; u < BS; ++u) {
+        a0[u] = A[r * N + i0 + u];
+        b0[u] = B[r * N + j0 + u];
+        a1[u] = A[(r + stride) * N + i0 + u];
+        b1[u] = B[(r + stride) * N + j0 + u];
       }
+#pragma unroll
+      for (int u = 0; u < BS; ++u)
+#pragma unroll
+        for (int v = 0; v < BS; ++v) {
+          cmac_cj<T>(acc[u][v], a0[u], b0[v]);
+          cmac_cj<T>(acc[u][v], a1[u], b1[v]);
+        }
     }
-    __syncthreads();
+    if (r < rows) {
+      C<T> a0[BS], b0[BS];
+#pragma unroll
+      for (int u = 0; u < BS; ++u) {
+        a0[u] = A[r * N + i0 + u];
+        b0[u] = B[r * N + j0 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < BS; ++u)
+#pragma unroll
+        for (int v = 0; v < BS; ++v) cmac_cj<T>(acc[u][v], a0[u], b0[v]);
+    }
   }
-  cp_async_wait_all();
   // reduce the row groups in FP64 into red[N*N]
   for (int k = t; k < N * N; k += 256) red[k] = make_double2(0.0, 0.0);
   __syncthreads();
@@ -166,6 +142,29 @@ __global__ void __launch_bounds__(256) k_block_axpy(const C<TA> *__restrict__ Ai
 }
 
 // ------------------------------------------------------------ fused all-shift update
+// Whole-row loads: 16-byte vector loads when the row is 16-byte aligned.
+template <typename T, int N> struct Row {
+  __device__ static void load(const C<T> *src, C<T> *dst) {
+    constexpr int PER16 = 16 / (int)sizeof(C<T>);  // complex numbers per 16 bytes
+    if (N % PER16 == 0) {
+      const float4 *v = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+      for (int q = 0; q < N / PER16; ++q) {
+        const float4 w = v[q];
+        if (PER16 == 2) {
+          reinterpret_cast<float2 *>(dst)[2 * q] = make_float2(w.x, w.y);
+          reinterpret_cast<float2 *>(dst)[2 * q + 1] = make_float2(w.z, w.w);
+        } else {
+          reinterpret_cast<float4 *>(dst)[q] = w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) dst[k] = src[k];
+    }
+  }
+};
+
 // coef layout (type C<T>): [0, N*N) rho^-1; then for s: M1^(s) at (1+2s)*N*N,
 // M2^(s) at (2+2s)*N*N.  upd[s] != 0 selects the shifts updated this iteration.
 // X^(s) is of type TX (FP64 in the FP64 solver, FP32 partial sums in the mixed
@@ -228,10 +227,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
       const C<T> *m2 = m1 + N * N;
       C<T> *Ps = P + s * fstride;
       C<T> p[N];
-      if (live) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) p[k] = Ps[r * N + k];
-      }
+      if (live) Row<T, N>::load(Ps + r * N, p);
       __syncwarp();
       if (live) {
         C<T> a1[CG], a2[CG];
@@ -363,17 +359,10 @@ template <typename T, int N>
 static cudaError_t launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *partial, int nparts,
                                cudaStream_t s) {
   constexpr int BS = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
-  constexpr int TR = sizeof(T) == 4 ? 128 : 64;
-  const size_t smem = 4 * (size_t)TR * N * sizeof(C<T>) + (size_t)N * N * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gram<T, N, BS, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nparts * kGramCluster);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -382,7 +371,7 @@ static cudaError_t launch_gram(const C<T> *A, const C<T> *B, long rows, double2 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gram<T, N, BS, TR>, A, B, rows, partial);
+  return cudaLaunchKernelEx(&cfg, k_gram<T, N, BS>, A, B, rows, partial);
 }
 
 // nparts: number of FP64 partial n x n sums written (one per cluster of CTAs).
