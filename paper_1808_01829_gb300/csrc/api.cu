@@ -91,7 +91,7 @@ void set_error(const char *fmt, ...) {
   } while (0)
 
 constexpr int kParts = 304;           // partial sums of the simple reductions (2 CTAs per SM)
-constexpr int kGramParts = 38;        // Gram partials: one per cluster of 8 CTAs (304 CTAs)
+constexpr int kGramParts = 1;         // the Gram kernels deliver the summed n x n matrix
 constexpr double kReliableDelta = 0.1;
 constexpr int kCheckEvery = 8;        // iterations between host checks
 constexpr int kMaxRefine = 4;
@@ -192,7 +192,8 @@ struct SolveBufs {
   void *coef, *mw;
   // FP64 helpers
   double2 *R64, *T64, *AP64, *rinv64;
-  double2 *partial;
+  double2 *partial;   // the summed Gram matrix (n x n)
+  double2 *gscratch;  // per-CTA Gram partials
   double *npart;
   SolverState *st;
 };
@@ -214,7 +215,8 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   b.T64 = a.take<double2>(len);
   b.AP64 = a.take<double2>(len);
   b.rinv64 = a.take<double2>((size_t)n * n);
-  b.partial = a.take<double2>((size_t)kGramParts * n * n);
+  b.partial = a.take<double2>((size_t)n * n);
+  b.gscratch = a.take<double2>((size_t)kGramCtas * n * n);
   b.npart = a.take<double>((size_t)kParts * kMaxN);
   b.st = a.take<SolverState>(1);
 }
@@ -303,10 +305,10 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   cudaStream_t ss = split ? c->side : s;
   if (split && k >= 3) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[(k - 2) % 3], 0));
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
-  RHMC_TRY(gram<T>(P, AP, rows, n, b.partial, kGramParts, s));
+  RHMC_TRY(gram<T>(P, AP, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
   RHMC_TRY(block_axpy<T, T>(AP, Qprev, (const C<T> *)b.mw, W, rows, n, s));
-  RHMC_TRY(gram<T>(W, W, rows, n, b.partial, kGramParts, s));
+  RHMC_TRY(gram<T>(W, W, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
   RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 0, 1, 1, rows, n, len, s));
@@ -344,11 +346,11 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   if (mixed) {
     // the FP32 basis only needs FP32 orthonormality: QR of the rounded block
     RHMC_TRY((convert<double, float>(B, (float2 *)b.W, len, s)));
-    RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.partial, kGramParts, s));
+    RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.gscratch, b.partial, s));
     RHMC_TRY(nxn_qr_init<float>(b.partial, kGramParts, n, ns, b.st, (float2 *)b.mw, s));
     RHMC_TRY((block_axpy<float, float>((float2 *)b.W, nullptr, (float2 *)b.mw, (float2 *)b.Qb[0], rows, n, s)));
   } else {
-    RHMC_TRY(gram<double>(B, B, rows, n, b.partial, kGramParts, s));
+    RHMC_TRY(gram<double>(B, B, rows, n, b.gscratch, b.partial, s));
     RHMC_TRY(nxn_qr_init<double>(b.partial, kGramParts, n, ns, b.st, b.rinv64, s));
     RHMC_TRY(block_axpy<double, T>(B, nullptr, b.rinv64, (C<T> *)b.Qb[0], rows, n, s));
   }
@@ -415,7 +417,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
       // thin QR of the FP32-rounded true residual (Q is an FP32 basis)
       RHMC_TRY((convert<double, float>(b.R64, (float2 *)b.W, len, s)));
-      RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.partial, kGramParts, s));
+      RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.gscratch, b.partial, s));
       RHMC_TRY(nxn_reliable<float>(b.partial, kGramParts, n, b.st, k, (float2 *)b.mw, s));
       RHMC_TRY((block_axpy<float, float>((float2 *)b.W, nullptr, (float2 *)b.mw, (float2 *)b.Qb[k & 1], rows, n, s)));
       stats.dirac++;

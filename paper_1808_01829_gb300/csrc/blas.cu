@@ -10,8 +10,6 @@
 //               (lines 6-7 for s = 0 with M1 = alpha_k delta_{k-1}, M2 = rho_k^dagger;
 //                lines 11-12 with M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger)
 //   flush       X64 += X32, X32 = 0 (mixed precision reliable-update flush)
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "common.cuh"
@@ -19,98 +17,139 @@
 
 namespace rhmc {
 
-// ------------------------------------------------------------ Gram partials
-// G = A^dagger B.  Thread layout: BS x BS blocks of the n x n result (register
-// blocking); the threads of one row group read each row's BS-wide chunks
-// straight from global memory (the lanes that share a chunk are served by one
-// L1 access), two rows in flight per thread.  FP32 products accumulate in FP32
-// per thread; each CTA reduces its row groups in FP64, and the CTAs of a
-// cluster of kGramCluster sum their partials through distributed shared memory
-// in a fixed order, so one FP64 partial per cluster reaches global memory
-// (deterministic).
-constexpr int kGramCluster = 8;
+// ------------------------------------------------------------ Gram
+// G = A^dagger B (n x n), summed over all rows, in two launches:
+//   k_gram      every warp streams its own 16-row tiles of A and B through a
+//               private double buffer in shared memory (cp.async, only warp
+//               synchronisation); each lane owns n*n/32 entries of G and
+//               accumulates them in FP32; the CTA sums its warps in FP64 and
+//               writes one partial per entry, transposed ([entry][CTA]);
+//   k_gram_sum  one CTA per entry sums the partials in a fixed order (FP64),
+//               so the result is deterministic.
+// For n = 16 lane L owns row i = L/2 of G and 8 consecutive columns, so a row
+// of the tile costs one 8-byte and four 16-byte shared loads per 8 complex MACs.
+constexpr int kGramTileRows = 16;
+constexpr int kGramWarps = 8;
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
 
-template <typename T, int N, int BS>
+template <typename T, int N, bool SAME>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
                                               double2 *__restrict__ partial) {
-  constexpr int NB = N / BS;
-  constexpr int NBLK = NB * NB;   // threads per row group
-  constexpr int RG = 256 / NBLK;  // row groups per CTA
-  __shared__ double2 red[N * N];
-  const int t = threadIdx.x;
-  const int blk = t % NBLK, grp = t / NBLK;
-  const int i0 = BS * (blk / NB), j0 = BS * (blk % NB);
-  C<T> acc[BS][BS];
+  constexpr int TE = kGramTileRows * N;  // complex per tile and operand
+  constexpr int E = (N * N + 31) / 32;   // entries per lane
+  constexpr bool STRUCT = (N == 16);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C<T> *ws = reinterpret_cast<C<T> *>(smem_raw) + (size_t)warp * 2 * (SAME ? 1 : 2) * TE;
+  C<T> *sa[2] = {ws, ws + (SAME ? 1 : 2) * TE};
+  C<T> *sb[2] = {SAME ? sa[0] : ws + TE, SAME ? sa[1] : ws + 3 * TE};
+  C<T> acc[E];
 #pragma unroll
-  for (int u = 0; u < BS; ++u)
-#pragma unroll
-    for (int v = 0; v < BS; ++v) acc[u][v] = czero<T>();
-  if (grp < RG) {
-    // rows of this row group: grp + RG * (blockIdx + gridDim * k), two at a time
-    const long stride = (long)RG * gridDim.x;
-    long r = (long)blockIdx.x * RG + grp;
-    for (; r + stride < rows; r += 2 * stride) {
-      C<T> a0[BS], b0[BS], a1[BS], b1[BS];
-#pragma unroll
-      for (int u = 0; u < BS; ++u) {
-        a0[u] = A[r * N + i0 + u];
-        b0[u] = B[r * N + j0 + u];
-        a1[u] = A[(r + stride) * N + i0 + u];
-        b1[u] = B[(r + stride) * N + j0 + u];
+  for (int q = 0; q < E; ++q) acc[q] = czero<T>();
+  const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
+  const long wstride = (long)gridDim.x * kGramWarps;
+  long tile = (long)blockIdx.x * kGramWarps + warp;
+  auto issue = [&](long tl, int st) {
+    const long r0 = tl * kGramTileRows;
+    const int nr = (int)min((long)kGramTileRows, rows - r0);
+    if (nr == kGramTileRows) {
+      constexpr int NV = (int)(TE * sizeof(C<T>) / 16);
+      const char *ga = reinterpret_cast<const char *>(A + r0 * N);
+      const char *gb = reinterpret_cast<const char *>(B + r0 * N);
+      for (int k = lane; k < NV; k += 32) {
+        cp_async16(reinterpret_cast<char *>(sa[st]) + 16 * k, ga + 16 * k);
+        if (!SAME) cp_async16(reinterpret_cast<char *>(sb[st]) + 16 * k, gb + 16 * k);
       }
+    } else {  // ragged last tile: plain loads, zero fill
+      for (int k = lane; k < TE; k += 32) {
+        const bool in = k < nr * N;
+        sa[st][k] = in ? A[r0 * N + k] : czero<T>();
+        if (!SAME) sb[st][k] = in ? B[r0 * N + k] : czero<T>();
+      }
+    }
+    cp_async_commit();
+  };
+  int st = 0;
+  if (tile < ntiles) issue(tile, 0);
+  for (; tile < ntiles; tile += wstride) {
+    if (tile + wstride < ntiles)
+      issue(tile + wstride, st ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    const C<T> *ta = sa[st], *tb = sb[st];
+    if (STRUCT) {
+      const int i = lane >> 1, j0 = (lane & 1) * 8;
+#pragma unroll 4
+      for (int r = 0; r < kGramTileRows; ++r) {
+        const C<T> a = ta[r * N + i];
+        C<T> b[8];
 #pragma unroll
-      for (int u = 0; u < BS; ++u)
+        for (int q = 0; q < 8; ++q) b[q] = tb[r * N + j0 + q];
 #pragma unroll
-        for (int v = 0; v < BS; ++v) {
-          cmac_cj<T>(acc[u][v], a0[u], b0[v]);
-          cmac_cj<T>(acc[u][v], a1[u], b1[v]);
+        for (int q = 0; q < 8; ++q) cmac_cj<T>(acc[q], a, b[q]);
+      }
+    } else {
+#pragma unroll 4
+      for (int r = 0; r < kGramTileRows; ++r)
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int e = lane + 32 * q;
+          if (e < N * N) cmac_cj<T>(acc[q], ta[r * N + e / N], tb[r * N + e % N]);
         }
     }
-    if (r < rows) {
-      C<T> a0[BS], b0[BS];
-#pragma unroll
-      for (int u = 0; u < BS; ++u) {
-        a0[u] = A[r * N + i0 + u];
-        b0[u] = B[r * N + j0 + u];
-      }
-#pragma unroll
-      for (int u = 0; u < BS; ++u)
-#pragma unroll
-        for (int v = 0; v < BS; ++v) cmac_cj<T>(acc[u][v], a0[u], b0[v]);
-    }
+    __syncwarp();
+    st ^= 1;
   }
-  // reduce the row groups in FP64 into red[N*N]
-  for (int k = t; k < N * N; k += 256) red[k] = make_double2(0.0, 0.0);
+  cp_async_wait0();
   __syncthreads();
-  for (int g = 0; g < RG; ++g) {
-    if (grp == g) {
+  // CTA reduction in FP64 (reuses the tile buffers), then one partial per entry
+  double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [kGramWarps][N*N]
 #pragma unroll
-      for (int u = 0; u < BS; ++u)
-#pragma unroll
-        for (int v = 0; v < BS; ++v) {
-          double2 &d = red[(i0 + u) * N + j0 + v];
-          d.x += (double)acc[u][v].x;
-          d.y += (double)acc[u][v].y;
-        }
+  for (int q = 0; q < E; ++q) {
+    const int e = STRUCT ? (lane >> 1) * N + (lane & 1) * 8 + q : lane + 32 * q;
+    if (e < N * N) red[warp * N * N + e] = make_double2((double)acc[q].x, (double)acc[q].y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    double2 sum = red[e];
+    for (int w = 1; w < kGramWarps; ++w) {
+      sum.x += red[w * N * N + e].x;
+      sum.y += red[w * N * N + e].y;
+    }
+    partial[(long)e * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// out[e] = sum over the nparts partials of entry e, fixed order.
+__global__ void __launch_bounds__(128) k_gram_sum(const double2 *__restrict__ partial, int nparts,
+                                                  double2 *__restrict__ out) {
+  __shared__ double2 red[128];
+  const int e = blockIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+    const double2 v = partial[(long)e * nparts + p];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[threadIdx.x].x += red[threadIdx.x + w].x;
+      red[threadIdx.x].y += red[threadIdx.x + w].y;
     }
     __syncthreads();
   }
-  // cluster reduction through distributed shared memory, fixed order
-  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-  cl.sync();
-  if (cl.block_rank() == 0) {
-    for (int k = t; k < N * N; k += 256) {
-      double2 sum = red[k];
-      for (unsigned q = 1; q < cl.num_blocks(); ++q) {
-        const double2 *rem = cl.map_shared_rank(red, q);
-        sum.x += rem[k].x;
-        sum.y += rem[k].y;
-      }
-      partial[(long)(blockIdx.x / cl.num_blocks()) * N * N + k] = sum;
-    }
-  }
-  cl.sync();
+  if (threadIdx.x == 0) out[e] = red[0];
 }
 
 // ------------------------------------------------------------ Y = C + A M
@@ -356,42 +395,39 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
   }
 
 template <typename T, int N>
-static cudaError_t launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *partial, int nparts,
-                               cudaStream_t s) {
-  constexpr int BS = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nparts * kGramCluster);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kGramCluster;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gram<T, N, BS>, A, B, rows, partial);
+static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
+  const bool same = (A == B);
+  const size_t smem = (size_t)kGramWarps * 2 * (same ? 1 : 2) * kGramTileRows * N * sizeof(C<T>);
+  const size_t smem_red = (size_t)kGramWarps * N * N * sizeof(double2);
+  const size_t bytes = std::max(smem, smem_red);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
+  const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, kGramCtas);
+  if (same)
+    k_gram<T, N, true><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+  else
+    k_gram<T, N, false><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+  k_gram_sum<<<N * N, 128, 0, s>>>(scratch, grid, out);
 }
 
-// nparts: number of FP64 partial n x n sums written (one per cluster of CTAs).
+// G = A^dagger B into out (n x n, FP64); scratch holds kGramCtas * n * n partials.
 template <typename T>
-rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *partial, int nparts, cudaStream_t s) {
+rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *scratch, double2 *out, cudaStream_t s) {
   prof_begin(sizeof(T) == 4 ? PROF_GRAM32 : PROF_GRAM64, s);
-  cudaError_t e = cudaSuccess;
-#define L_GRAM(NN) e = launch_gram<T, NN>(A, B, rows, partial, nparts, s)
+#define L_GRAM(NN) launch_gram<T, NN>(A, B, rows, scratch, out, s)
   RHMC_DISPATCH_N(n, L_GRAM)
 #undef L_GRAM
-  if (e != cudaSuccess) {
-    set_error("gram launch: %s", cudaGetErrorString(e));
-    return RHMC_ERR_CUDA;
-  }
   prof_end(s, (double)rows * n * sizeof(C<T>) * (A == B ? 1 : 2));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
-template rhmc_status_t gram<float>(const float2 *, const float2 *, long, int, double2 *, int, cudaStream_t);
-template rhmc_status_t gram<double>(const double2 *, const double2 *, long, int, double2 *, int, cudaStream_t);
+template rhmc_status_t gram<float>(const float2 *, const float2 *, long, int, double2 *, double2 *, cudaStream_t);
+template rhmc_status_t gram<double>(const double2 *, const double2 *, long, int, double2 *, double2 *, cudaStream_t);
 
 template <typename TA, typename TY>
 rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY> *Y, long rows, int n,

@@ -37,8 +37,9 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
                   int n, int nbatch, long bstride, cudaStream_t s);
 
 // blas.cu
+constexpr int kGramCtas = 4 * 152;  // CTAs of the Gram kernel (its scratch holds kGramCtas * n * n partials)
 template <typename T>
-rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *partial, int nparts, cudaStream_t s);
+rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *scratch, double2 *out, cudaStream_t s);
 template <typename TA, typename TY>
 rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY> *Y, long rows, int n,
                          cudaStream_t s);
