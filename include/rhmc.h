@@ -69,9 +69,13 @@ typedef struct {
 
 typedef enum {
   RHMC_FP64 = 0,       /* everything in FP64 */
-  RHMC_MIXED_FP32 = 1  /* FP32 operator and block updates inside an FP64
+  RHMC_MIXED_FP32 = 1, /* FP32 operator and block updates inside an FP64-accurate
                           reliable-update / defect-correction loop; FP64 n x n
-                          coefficient algebra, true residuals and force */
+                          coefficient algebra, FP64 force.  The residuals of the
+                          loop use the double-float operator (RHMC_DF64) */
+  RHMC_DF64 = 2        /* operator only (apply / hop): FP64-accurate double-float
+                          arithmetic (pairs of FP32, about 2^-44 relative) on the
+                          FP32 units, which on this GPU are 74x faster than FP64 */
 } rhmc_precision_t;
 
 /* Largest number of right-hand sides per block (n_pf). */
@@ -200,7 +204,8 @@ long long rhmc_kernel_launches(void);
  * of one category (RHMC_PROF_*). */
 enum {
   RHMC_PROF_HOP_FP32 = 0, RHMC_PROF_HOP_FP64, RHMC_PROF_GRAM_FP32, RHMC_PROF_GRAM_FP64, RHMC_PROF_BLOCK_AXPY,
-  RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER, RHMC_PROF_NCAT
+  RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER,
+  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_NCAT
 };
 rhmc_status_t rhmc_profile_enable(int on);
 
@@ -214,13 +219,16 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_RELIABLE_DELTA_MILLI  mixed precision: reliable update when the
  *                                 base residual fell by value/1000 (0: 0.1)
  *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 8)
+ *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
+ *                                 true residuals with native FP64 instead of RHMC_DF64
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
   RHMC_TUNE_UPDATE_THREADS = 1,
   RHMC_TUNE_FLUSH_EVERY = 2,
   RHMC_TUNE_RELIABLE_DELTA_MILLI = 3,
-  RHMC_TUNE_CHECK_EVERY = 4
+  RHMC_TUNE_CHECK_EVERY = 4,
+  RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5
 };
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);

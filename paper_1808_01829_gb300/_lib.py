@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "librhmc.so")
 
 RHMC_FP64 = 0
 RHMC_MIXED_FP32 = 1
+RHMC_DF64 = 2
 RHMC_MAX_NRHS = 16
 RHMC_MAX_SHIFTS = 64
 
@@ -30,7 +31,7 @@ STATUS = {
 
 
 PROF_CATEGORIES = ["hop_fp32", "hop_fp64", "gram_fp32", "gram_fp64", "block_axpy", "update_fp32", "update_fp64",
-                   "nxn", "force", "other"]
+                   "nxn", "force", "other", "hop_df", "nxn_shifts"]
 
 
 class RhmcError(RuntimeError):

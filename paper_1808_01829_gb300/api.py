@@ -20,7 +20,8 @@ import torch
 
 from . import _lib
 
-PRECISION = {"fp64": _lib.RHMC_FP64, "mixed": _lib.RHMC_MIXED_FP32, "fp32": _lib.RHMC_MIXED_FP32}
+PRECISION = {"fp64": _lib.RHMC_FP64, "mixed": _lib.RHMC_MIXED_FP32, "fp32": _lib.RHMC_MIXED_FP32,
+             "df64": _lib.RHMC_DF64}
 
 
 @dataclass

@@ -120,6 +120,7 @@ struct rhmc_ctx {
   int bc_t = -1;
   double2 *l64[2] = {nullptr, nullptr};
   float2 *l32[2] = {nullptr, nullptr};
+  float4 *ldf[2] = {nullptr, nullptr};  // double-float copy of the FP64 link records
   bool have_gauge = false;
   void *pool = nullptr;
   size_t pool_bytes = 0;
@@ -183,6 +184,28 @@ static rhmc_status_t apply_A(const rhmc_ctx *c, const C<T> *X, C<T> *Y, C<T> *tm
   RHMC_TRY(hop<T>(c->g, 1, LinksOf<T>::get(c, 1), X, tmp, nullptr, 0.0, n, 1, 0, s));
   RHMC_TRY(hop<T>(c->g, 0, LinksOf<T>::get(c, 0), tmp, Y, X, 4.0 * c->mass * c->mass + sigma, n, 1, 0, s));
   return RHMC_OK;
+}
+
+// Y = (A + sigma) X with FP64 accuracy on the FP32 units (double-float):
+// split writes X as (hi, lo) into `split`, tmp holds the odd intermediate;
+// Y is written in FP64.  split, tmp, Y: FP64-field-sized buffers.
+static rhmc_status_t apply_A_df(const rhmc_ctx *c, const double2 *X, double2 *Y, double2 *tmp, double2 *split, int n,
+                                double sigma, cudaStream_t s) {
+  const long len = c->g.Vh * 3 * n;
+  RHMC_TRY(df_split(X, (float4 *)split, len, s));
+  RHMC_TRY(hop_df(c->g, 1, c->ldf[1], (const float4 *)split, (float4 *)tmp, nullptr, 0.0, n, s));
+  RHMC_TRY(hop_df(c->g, 0, c->ldf[0], (const float4 *)tmp, (float4 *)Y, (const float4 *)split,
+                  4.0 * c->mass * c->mass + sigma, n, s));
+  RHMC_TRY(df_merge((float4 *)Y, len, s));
+  return RHMC_OK;
+}
+
+// FP64-accurate operator for residuals of the mixed path: double-float unless
+// the native-FP64 tuning key is set.
+static rhmc_status_t apply_A_accurate(const rhmc_ctx *c, const double2 *X, double2 *Y, double2 *tmp,
+                                      double2 *split, int n, double sigma, cudaStream_t s) {
+  if (tune_get(TUNE_NATIVE_FP64_RESIDUALS)) return apply_A<double>(c, X, Y, tmp, n, sigma, s);
+  return apply_A_df(c, X, Y, tmp, split, n, sigma, s);
 }
 
 // ------------------------------------------------------------ solver workspace
@@ -413,7 +436,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     if (mixed && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
-      RHMC_TRY(apply_A<double>(c, X, b.AP64, b.T64, n, sigma0, s));
+      RHMC_TRY(apply_A_accurate(c, X, b.AP64, b.T64, b.R64, n, sigma0, s));
       RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
       // thin QR of the FP32-rounded true residual (Q is an FP32 basis)
       RHMC_TRY((convert<double, float>(b.R64, (float2 *)b.W, len, s)));
@@ -483,7 +506,10 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   for (int q = 0; q < ns; ++q) {
     double2 *Xq = X + q * len;
     for (int round = 0;; ++round) {
-      RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], s));
+      if (prm.mixed)
+        RHMC_TRY(apply_A_accurate(c, Xq, b1.AP64, b1.T64, b1.R64, n, shifts[q], s));
+      else
+        RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], s));
       RHMC_TRY(sub(B, b1.AP64, rb.Bref, len, s));
       st.dirac++;
       double rn[kMaxN];
@@ -641,7 +667,8 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
   c->bc_t = lat->bc_t == 1 ? 1 : -1;
   for (int p = 0; p < 2; ++p) {
     if (cudaMalloc(&c->l64[p], sizeof(double2) * 72 * c->g.Vh) != cudaSuccess ||
-        cudaMalloc(&c->l32[p], sizeof(float2) * 72 * c->g.Vh) != cudaSuccess) {
+        cudaMalloc(&c->l32[p], sizeof(float2) * 72 * c->g.Vh) != cudaSuccess ||
+        cudaMalloc(&c->ldf[p], sizeof(float4) * 72 * c->g.Vh) != cudaSuccess) {
       set_error("rhmc_create: out of device memory for links");
       rhmc_destroy(c);
       return RHMC_ERR_CUDA;
@@ -669,6 +696,7 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
   for (int p = 0; p < 2; ++p) {
     if (c->l64[p]) cudaFree(c->l64[p]);
     if (c->l32[p]) cudaFree(c->l32[p]);
+    if (c->ldf[p]) cudaFree(c->ldf[p]);
   }
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->pool) cudaFree(c->pool);
@@ -690,6 +718,7 @@ rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *c, const void *U, rhmc_stream_t sv) {
   DeviceGuard dg(c->device);
   cudaStream_t s = (cudaStream_t)sv;
   RHMC_TRY(stage_links(c->g, (const double2 *)U, c->bc_t, c->l64, c->l32, s));
+  for (int p = 0; p < 2; ++p) RHMC_TRY(stage_links_df(c->g, c->l64[p], c->ldf[p], s));
   RHMC_CUDA_TRY(cudaStreamSynchronize(s));
   c->have_gauge = true;
   return RHMC_OK;
@@ -735,6 +764,12 @@ rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *c, const void *X, void *Y, int n
     RHMC_TRY(ensure_pool(c, sizeof(double2) * len + 256));
     return apply_A<double>(c, (const double2 *)X, (double2 *)Y, (double2 *)c->pool, n, sigma, s);
   }
+  if (p == RHMC_DF64) {
+    RHMC_TRY(ensure_pool(c, 2 * (sizeof(double2) * len + 256)));
+    Arena a(c->pool);
+    double2 *tmp = a.take<double2>(len), *split = a.take<double2>(len);
+    return apply_A_df(c, (const double2 *)X, (double2 *)Y, tmp, split, n, sigma, s);
+  }
   RHMC_TRY(ensure_pool(c, 3 * (sizeof(float2) * len + 256)));
   Arena a(c->pool);
   float2 *x32 = a.take<float2>(len), *y32 = a.take<float2>(len), *t32 = a.take<float2>(len);
@@ -755,6 +790,12 @@ rhmc_status_t rhmc_hop(rhmc_ctx_t *c, const void *X, void *Y, int n, int out_par
   cudaStream_t s = (cudaStream_t)sv;
   const long len = c->g.Vh * 3 * n;
   if (p == RHMC_FP64) return hop<double>(c->g, out_par, c->l64[out_par], (const double2 *)X, (double2 *)Y, nullptr, 0, n, 1, 0, s);
+  if (p == RHMC_DF64) {
+    RHMC_TRY(ensure_pool(c, sizeof(double2) * len + 256));
+    RHMC_TRY(df_split((const double2 *)X, (float4 *)c->pool, len, s));
+    RHMC_TRY(hop_df(c->g, out_par, c->ldf[out_par], (const float4 *)c->pool, (float4 *)Y, nullptr, 0.0, n, s));
+    return df_merge((float4 *)Y, len, s);
+  }
   RHMC_TRY(ensure_pool(c, 2 * (sizeof(float2) * len + 256)));
   Arena a(c->pool);
   float2 *x32 = a.take<float2>(len), *y32 = a.take<float2>(len);
@@ -834,7 +875,7 @@ rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *c, const void *B, int n, int 
   RHMC_TRY(check_common(c, B, X, n));
   RHMC_TRY(check_shifts(ns, shifts, tol));
   if (p != RHMC_FP64 && p != RHMC_MIXED_FP32) {
-    set_error("unknown precision %d", (int)p);
+    set_error("precision %d not supported by the solver", (int)p);
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);

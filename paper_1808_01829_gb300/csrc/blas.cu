@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   constexpr bool STRUCT = (N == 16);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C<T> *ws = reinterpret_cast<C<T> *>(smem_raw) + (size_t)warp * 2 * (SAME ? 1 : 2) * TE;
-  C<T> *sa[2] = {ws, ws + (SAME ? 1 : 2) * TE};
-  C<T> *sb[2] = {SAME ? sa[0] : ws + TE, SAME ? sa[1] : ws + 3 * TE};
+  constexpr int STAGE = (SAME ? 1 : 2) * TE;  // complex per pipeline stage
+  C<T> *ws = reinterpret_cast<C<T> *>(smem_raw) + (size_t)warp * 2 * STAGE;
+  auto sa = [&](int st) { return ws + st * STAGE; };
+  auto sb = [&](int st) { return SAME ? ws + st * STAGE : ws + st * STAGE + TE; };
   C<T> acc[E];
 #pragma unroll
   for (int q = 0; q < E; ++q) acc[q] = czero<T>();
@@ -64,14 +65,14 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
       const char *ga = reinterpret_cast<const char *>(A + r0 * N);
       const char *gb = reinterpret_cast<const char *>(B + r0 * N);
       for (int k = lane; k < NV; k += 32) {
-        cp_async16(reinterpret_cast<char *>(sa[st]) + 16 * k, ga + 16 * k);
-        if (!SAME) cp_async16(reinterpret_cast<char *>(sb[st]) + 16 * k, gb + 16 * k);
+        cp_async16(reinterpret_cast<char *>(sa(st)) + 16 * k, ga + 16 * k);
+        if (!SAME) cp_async16(reinterpret_cast<char *>(sb(st)) + 16 * k, gb + 16 * k);
       }
     } else {  // ragged last tile: plain loads, zero fill
       for (int k = lane; k < TE; k += 32) {
         const bool in = k < nr * N;
-        sa[st][k] = in ? A[r0 * N + k] : czero<T>();
-        if (!SAME) sb[st][k] = in ? B[r0 * N + k] : czero<T>();
+        sa(st)[k] = in ? A[r0 * N + k] : czero<T>();
+        if (!SAME) sb(st)[k] = in ? B[r0 * N + k] : czero<T>();
       }
     }
     cp_async_commit();
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
       cp_async_commit();
     cp_async_wait1();
     __syncwarp();
-    const C<T> *ta = sa[st], *tb = sb[st];
+    const C<T> *ta = sa(st), *tb = sb(st);
     if (STRUCT) {
       const int i = lane >> 1, j0 = (lane & 1) * 8;
 #pragma unroll 4
@@ -226,6 +227,8 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   __shared__ int supd[kMaxS];
   const int c0 = compute_q ? 0 : (1 + 2 * s_begin) * N * N;  // first coefficient staged
   const int ncoef = (1 + 2 * s_end) * N * N - c0;
+  // per-warp row buffer after the coefficients: [warps][32 / TPR][N]
+  C<T> *wrow_all = sc + ncoef;
   for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = coef[c0 + k];
   for (int k = threadIdx.x; k < s_end; k += blockDim.x) supd[k] = upd[k];
   __syncthreads();
@@ -236,6 +239,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / TPR;
   const int j0 = (lane - slot * TPR) * CG;
+  C<T> *wrow = wrow_all + warp * RPW * N;
   const long rows_per_cta = (long)(blockDim.x >> 5) * RPW;
   for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
     const long r = rbase + (long)warp * RPW + slot;
@@ -265,10 +269,19 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
       const C<T> *m1 = sc + (1 + 2 * s) * N * N - c0;
       const C<T> *m2 = m1 + N * N;
       C<T> *Ps = P + s * fstride;
-      C<T> p[N];
-      if (live) Row<T, N>::load(Ps + r * N, p);
+      // each lane loads only its own CG columns; the row is assembled in the
+      // warp's shared row buffer and read back whole (no redundant global loads)
+      C<T> own[CG];
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < CG; ++c) own[c] = Ps[r * N + j0 + c];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) wrow[slot * N + j0 + c] = own[c];
+      }
       __syncwarp();
       if (live) {
+        C<T> p[N];
+        Row<T, N>::load(wrow + slot * N, p);
         C<T> a1[CG], a2[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
@@ -453,14 +466,15 @@ template <typename T, typename TX, int N>
 static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
                           int s_end, int compute_q, long rows, long fstride, cudaStream_t s) {
   constexpr int CG = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
-  const size_t smem = (size_t)((1 + 2 * s_end) - (compute_q ? 0 : 1 + 2 * s_begin)) * N * N * sizeof(C<T>);
+  int threads = tune_get(TUNE_UPDATE_THREADS);
+  if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
+  const size_t smem = (size_t)((1 + 2 * s_end) - (compute_q ? 0 : 1 + 2 * s_begin)) * N * N * sizeof(C<T>) +
+                      (size_t)(threads / 32) * (32 / (N / CG)) * N * sizeof(C<T>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_all<T, TX, N, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
-  int threads = tune_get(TUNE_UPDATE_THREADS);
-  if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
   const long rows_per_cta = (long)(threads / 32) * (32 / (N / CG));
   long grid = (rows + rows_per_cta - 1) / rows_per_cta;
   grid = std::min(grid, (long)(8 * 152));

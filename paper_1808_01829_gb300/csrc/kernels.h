@@ -36,6 +36,13 @@ template <typename T>
 rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
                   int n, int nbatch, long bstride, cudaStream_t s);
 
+// double-float (FP64-accurate, FP32 units) operator pieces
+rhmc_status_t stage_links_df(const Geom &g, const double2 *l64, float4 *ldf, cudaStream_t s);
+rhmc_status_t df_split(const double2 *in, float4 *out, long len, cudaStream_t s);
+rhmc_status_t df_merge(float4 *io, long len, cudaStream_t s);
+rhmc_status_t hop_df(const Geom &g, int par, const float4 *links, const float4 *in, float4 *out, const float4 *self,
+                     double a, int n, cudaStream_t s);
+
 // blas.cu
 constexpr int kGramCtas = 4 * 152;  // CTAs of the Gram kernel (its scratch holds kGramCtas * n * n partials)
 template <typename T>

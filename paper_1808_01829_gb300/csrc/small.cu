@@ -467,7 +467,7 @@ template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
                          cudaStream_t s) {
   if (nshift > 1) {
-    prof_begin(PROF_NXN, s);
+    prof_begin(PROF_NXN_SHIFTS, s);
     k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze);
     prof_end(s, 0.0);
     RHMC_LAUNCH_CHECK();

@@ -35,6 +35,8 @@ def test_hop_fp64_fp32(dims, n, bc):
         assert colrel(got, ref) <= 1e-12
         got32 = ctx.hop(to_gpu(X), par, "fp32").cpu().numpy()
         assert colrel(got32, ref) <= 1e-6
+        gotdf = ctx.hop(to_gpu(X), par, "df64").cpu().numpy()
+        assert colrel(gotdf, ref) <= 1e-12
     ctx.close()
 
 
@@ -51,6 +53,8 @@ def test_apply_mdagm(dims, n, bc, sigma):
     assert colrel(got, ref) <= 1e-12
     got32 = ctx.apply_mdagm_mrhs(to_gpu(X), sigma, "fp32").cpu().numpy()
     assert colrel(got32, ref) <= 1e-6
+    gotdf = ctx.apply_mdagm_mrhs(to_gpu(X), sigma, "df64").cpu().numpy()
+    assert colrel(gotdf, ref) <= 1e-12
     ctx.close()
 
 
@@ -68,6 +72,8 @@ def test_apply_full_size_sampled():
     assert colrel(got, ref) <= 1e-12
     got32 = ctx.apply_mdagm_mrhs(to_gpu(X), 0.0, "fp32").cpu().numpy()[sites]
     assert colrel(got32, ref) <= 1e-6
+    gotdf = ctx.apply_mdagm_mrhs(to_gpu(X), 0.0, "df64").cpu().numpy()[sites]
+    assert colrel(gotdf, ref) <= 1e-12
     ctx.close()
 
 

@@ -175,3 +175,27 @@ def test_not_converged_reported():
                                       allow_not_converged=True)
     assert info.iters <= 8 and info.true_rel_resid_max > 1e-10
     ctx.close()
+
+
+def test_mixed_residuals_native_fp64_and_double_float_agree():
+    """The mixed solver's residual operator: double-float (default) and native FP64 both
+    reach the tolerance, with solutions within the solution-error bound of the oracle."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n = (8, 8, 8, 8), 0.05, 4
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1208)
+    B = syn.gaussian_pseudofermions(dims, n, 2208)
+    ctx = make_ctx(dims, mass, U)
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
+    try:
+        for native in (0, 1):
+            lib.rhmc_tune_set(5, native)
+            Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-9, precision="mixed")
+            assert info.true_rel_resid_max <= 1e-9
+            _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-9, Xo)
+    finally:
+        lib.rhmc_tune_set(5, 0)
+    ctx.close()
