@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   __shared__ int supd[kMaxS];
   const int c0 = compute_q ? 0 : (1 + 2 * s_begin) * N * N;  // first coefficient staged
   const int ncoef = (1 + 2 * s_end) * N * N - c0;
-  // per-warp row buffer after the coefficients: [warps][32 / TPR][N]
+  // per-warp row buffer after the coefficients: [warps][32 / TPR][RS], rows
+  // padded by 16 bytes so that the rows of a warp start in different banks
+  constexpr int RS = N + 16 / (int)sizeof(C<T>);
   C<T> *wrow_all = sc + ncoef;
   for (int k = threadIdx.x; k < ncoef; k += blockDim.x) sc[k] = coef[c0 + k];
   for (int k = threadIdx.x; k < s_end; k += blockDim.x) supd[k] = upd[k];
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / TPR;
   const int j0 = (lane - slot * TPR) * CG;
-  C<T> *wrow = wrow_all + warp * RPW * N;
+  C<T> *wrow = wrow_all + warp * RPW * RS;
   const long rows_per_cta = (long)(blockDim.x >> 5) * RPW;
   for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
     const long r = rbase + (long)warp * RPW + slot;
@@ -276,12 +278,12 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
 #pragma unroll
         for (int c = 0; c < CG; ++c) own[c] = Ps[r * N + j0 + c];
 #pragma unroll
-        for (int c = 0; c < CG; ++c) wrow[slot * N + j0 + c] = own[c];
+        for (int c = 0; c < CG; ++c) wrow[slot * RS + j0 + c] = own[c];
       }
       __syncwarp();
       if (live) {
         C<T> p[N];
-        Row<T, N>::load(wrow + slot * N, p);
+        Row<T, N>::load(wrow + slot * RS, p);
         C<T> a1[CG], a2[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
@@ -469,7 +471,7 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
   int threads = tune_get(TUNE_UPDATE_THREADS);
   if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
   const size_t smem = (size_t)((1 + 2 * s_end) - (compute_q ? 0 : 1 + 2 * s_begin)) * N * N * sizeof(C<T>) +
-                      (size_t)(threads / 32) * (32 / (N / CG)) * N * sizeof(C<T>);
+                      (size_t)(threads / 32) * (32 / (N / CG)) * (N + 16 / sizeof(C<T>)) * sizeof(C<T>);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_all<T, TX, N, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
