@@ -205,7 +205,7 @@ long long rhmc_kernel_launches(void);
 enum {
   RHMC_PROF_HOP_FP32 = 0, RHMC_PROF_HOP_FP64, RHMC_PROF_GRAM_FP32, RHMC_PROF_GRAM_FP64, RHMC_PROF_BLOCK_AXPY,
   RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER,
-  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_NCAT
+  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_UPDATE_TC, RHMC_PROF_NCAT
 };
 rhmc_status_t rhmc_profile_enable(int on);
 
@@ -221,6 +221,8 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 8)
  *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
  *                                 true residuals with native FP64 instead of RHMC_DF64
+ *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, n_rhs = 16: shifted updates on the
+ *                                 tensor cores (tcgen05, 3xTF32) = 1, CUDA cores = 2
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -228,7 +230,8 @@ enum {
   RHMC_TUNE_FLUSH_EVERY = 2,
   RHMC_TUNE_RELIABLE_DELTA_MILLI = 3,
   RHMC_TUNE_CHECK_EVERY = 4,
-  RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5
+  RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5,
+  RHMC_TUNE_UPDATE_TENSOR = 6
 };
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);

@@ -215,6 +215,7 @@ struct SolveBufs {
   void *coef, *mw;
   // FP64 helpers
   double2 *R64, *T64, *AP64, *rinv64;
+  float *btiles;      // tensor-core B tiles of the shifted updates
   double2 *partial;   // the summed Gram matrix (n x n)
   double2 *gscratch;  // per-CTA Gram partials
   double *npart;
@@ -238,6 +239,7 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   b.T64 = a.take<double2>(len);
   b.AP64 = a.take<double2>(len);
   b.rinv64 = a.take<double2>((size_t)n * n);
+  b.btiles = a.take<float>((size_t)ns * 2 * 64 * 32);
   b.partial = a.take<double2>((size_t)n * n);
   b.gscratch = a.take<double2>((size_t)kGramCtas * n * n);
   b.npart = a.take<double>((size_t)kParts * kMaxN);
@@ -295,6 +297,7 @@ struct StateView {
   double res[kMaxS][kMaxN];
   int active[kMaxS];
   int breakdown;
+  int device_timeout;
 };
 
 static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cudaStream_t s) {
@@ -302,10 +305,16 @@ static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cuda
   StateView *h = reinterpret_cast<StateView *>(c->h_pin);
   RHMC_CUDA_TRY(cudaMemcpyAsync(h->res, st->res, sizeof(v.res), cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaMemcpyAsync(h->active, st->active, sizeof(v.active), cudaMemcpyDeviceToHost, s));
-  RHMC_CUDA_TRY(cudaMemcpyAsync(&h->breakdown, &st->breakdown, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaMemcpyAsync(&h->breakdown, &st->breakdown, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaStreamSynchronize(s));
   std::memcpy(&v, h, sizeof(StateView));
   return RHMC_OK;
+}
+
+// Tensor-core shifted updates: FP32 fields, 16 right-hand sides.
+template <typename T> static bool use_tensor_update(int n) {
+  if (sizeof(T) != 4 || n != 16) return false;
+  return tune_get(TUNE_UPDATE_TENSOR) == 1;
 }
 
 // One SBCGrQ iteration (device work only).  The base recursion runs on the
@@ -341,8 +350,12 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
       RHMC_CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_base[k % 3], 0));
     }
     RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, ss));
-    RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
-                               ss));
+    if (use_tensor_update<T>(n))
+      RHMC_TRY(update_shifts_tc((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
+                                b.st->upd, 1, ns, rows, len, b.btiles, &b.st->device_timeout, ss));
+    else
+      RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
+                                 ss));
     if (split) RHMC_CUDA_TRY(cudaEventRecord(c->ev_side[k % 3], ss));
   }
   return RHMC_OK;
@@ -408,6 +421,11 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     }
     RHMC_TRY(join_side(c, k, ns, s));
     RHMC_TRY(read_state(c, b.st, v, s));
+    if (v.device_timeout) {
+      set_error("a bounded device-side wait expired in the tensor-core update (iteration %d)", k);
+      stats.iters = k;
+      return RHMC_ERR_DEVICE_TIMEOUT;
+    }
     if (v.breakdown) {
       set_error("breakdown in coefficient step %d at iteration %d", v.breakdown, k);
       stats.iters = k;
@@ -488,6 +506,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
                                : solve_phase1<double>(c, B, n, ns, shifts, X, p1, b, st, s);
   if (rc != RHMC_OK && rc != RHMC_ERR_NOT_CONVERGED) return rc;
   const rhmc_status_t rc1 = rc;
+
   // phase 2: FP64 true residual per shift, defect correction where needed
   Arena ra(ws);
   RefineBufs rb;

@@ -89,7 +89,7 @@ void count_launch();
 // algorithmic bytes.  No-ops when profiling is off.
 enum ProfCat {
   PROF_HOP32 = 0, PROF_HOP64, PROF_GRAM32, PROF_GRAM64, PROF_AXPY, PROF_UPDATE32, PROF_UPDATE64,
-  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_NCAT
+  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_UPDATE_TC, PROF_NCAT
 };
 bool prof_on();
 
@@ -101,6 +101,7 @@ enum TuneKey {
   TUNE_RELIABLE_DELTA_MILLI, // mixed: reliable update when the base residual fell by this / 1000 (0: 100)
   TUNE_CHECK_EVERY,          // iterations between host convergence checks (0: 8)
   TUNE_NATIVE_FP64_RESIDUALS, // mixed: native FP64 instead of double-float for residuals (0: double-float)
+  TUNE_UPDATE_TENSOR,         // mixed, n = 16: shifted updates on tcgen05 (1) or CUDA cores (2); 0: built-in
   TUNE_NKEYS
 };
 int tune_get(int key);

@@ -27,6 +27,7 @@ struct SolverState {
   int active[kMaxS];          // shift still being updated
   int upd[kMaxS];             // shift updated in the current iteration
   int breakdown;              // nonzero: which coefficient step failed
+  int device_timeout;         // a bounded device-side wait expired
 };
 
 // dslash.cu
@@ -56,6 +57,11 @@ template <typename T, typename TX>
 rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
                          int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s);
 rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s);
+
+// update_tc.cu: shifted updates on the tensor cores (mixed path, n = 16)
+rhmc_status_t update_shifts_tc(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
+                               int s_begin, int s_end, long rows, long fstride, float *btiles, int *err,
+                               cudaStream_t s);
 template <typename TI, typename TO>
 rhmc_status_t convert(const C<TI> *in, C<TO> *out, long len, cudaStream_t s);
 rhmc_status_t sub(const double2 *a, const double2 *b, double2 *out, long len, cudaStream_t s);

@@ -282,7 +282,10 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
     st->upd[c.t] = 0;
     for (int j = 0; j < n; ++j) st->res[c.t][j] = 1.0;
   }
-  if (c.t == 0) st->breakdown = 0;
+  if (c.t == 0) {
+    st->breakdown = 0;
+    st->device_timeout = 0;
+  }
 }
 
 // line 4: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P; also -alpha_k for line 5.

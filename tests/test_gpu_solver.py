@@ -199,3 +199,28 @@ def test_mixed_residuals_native_fp64_and_double_float_agree():
     finally:
         lib.rhmc_tune_set(5, 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 4, 10)])
+def test_tensor_core_shift_update_matches_oracle(dims):
+    """Mixed solve at n_pf = 16 with the shifted updates on tcgen05 (3xTF32): same
+    oracle criteria as the CUDA-core path; both paths reach the tolerance."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    mass, n = 0.05, 16
+    ra = rational_approx(-1.0 / 64, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1209)
+    B = syn.gaussian_pseudofermions(dims, n, 2209)
+    ctx = make_ctx(dims, mass, U)
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
+    try:
+        for mode in (1, 2):
+            lib.rhmc_tune_set(6, mode)
+            Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-8, precision="mixed")
+            assert info.true_rel_resid_max <= 1e-8
+            _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-8, Xo)
+    finally:
+        lib.rhmc_tune_set(6, 0)
+    ctx.close()
