@@ -314,7 +314,7 @@ static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cuda
 // Tensor-core shifted updates: FP32 fields, 16 right-hand sides.
 template <typename T> static bool use_tensor_update(int n) {
   if (sizeof(T) != 4 || n != 16) return false;
-  return tune_get(TUNE_UPDATE_TENSOR) == 1;
+  return tune_get(TUNE_UPDATE_TENSOR) != 2;  // built-in choice: tensor cores
 }
 
 // One SBCGrQ iteration (device work only).  The base recursion runs on the
