@@ -222,7 +222,7 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
  *                                 true residuals with native FP64 instead of RHMC_DF64
  *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, n_rhs = 16: shifted updates on the
- *                                 tensor cores (tcgen05, 3xTF32) = 1 (built-in), CUDA cores = 2
+ *                                 tensor cores (tcgen05, 3xTF32) = 1, CUDA cores = 2 (built-in)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,

@@ -314,7 +314,11 @@ static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cuda
 // Tensor-core shifted updates: FP32 fields, 16 right-hand sides.
 template <typename T> static bool use_tensor_update(int n) {
   if (sizeof(T) != 4 || n != 16) return false;
-  return tune_get(TUNE_UPDATE_TENSOR) != 2;  // built-in choice: tensor cores
+  // Built-in choice: CUDA cores.  Measured at 24^4: the tcgen05 (3xTF32) path
+  // leaves a larger FP32 drift in the shifted systems (phase-1 true residual
+  // 5.2e-6 against 4.4e-6), which costs more defect-correction iterations than
+  // the update saves.
+  return tune_get(TUNE_UPDATE_TENSOR) == 1;
 }
 
 // One SBCGrQ iteration (device work only).  The base recursion runs on the
