@@ -153,57 +153,73 @@ __global__ void __launch_bounds__(128) k_gram_sum(const double2 *__restrict__ pa
   if (threadIdx.x == 0) out[e] = red[0];
 }
 
-// ------------------------------------------------------------ Y = C + A M
-// One thread per row; M (n x n) in shared memory.  TA: type of A, TC: type
-// of C, TY: type of Y (conversion between precisions happens here).
-template <typename TA, typename TY, int N>
-__global__ void __launch_bounds__(256) k_block_axpy(const C<TA> *__restrict__ Ain, const C<TY> *__restrict__ Cin,
-                                                    const C<TA> *__restrict__ M, C<TY> *__restrict__ Y, long rows) {
-  __shared__ C<TA> sm[N * N];
-  for (int k = threadIdx.x; k < N * N; k += blockDim.x) sm[k] = M[k];
-  __syncthreads();
-  const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  C<TA> a[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) a[k] = Ain[r * N + k];
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    C<TA> acc = czero<TA>();
-#pragma unroll
-    for (int k = 0; k < N; ++k) cmac<TA>(acc, a[k], sm[k * N + j]);
-    if (Cin) {
-      const C<TY> c = Cin[r * N + j];
-      Y[r * N + j] = mk<TY>((TY)(c.x + acc.x), (TY)(c.y + acc.y));
-    } else {
-      Y[r * N + j] = mk<TY>((TY)acc.x, (TY)acc.y);
-    }
-  }
-}
-
-// ------------------------------------------------------------ fused all-shift update
 // Whole-row loads: 16-byte vector loads when the row is 16-byte aligned.
 template <typename T, int N> struct Row {
   __device__ static void load(const C<T> *src, C<T> *dst) {
-    constexpr int PER16 = 16 / (int)sizeof(C<T>);  // complex numbers per 16 bytes
-    if (N % PER16 == 0) {
+    if (sizeof(C<T>) == 8 && N % 2 == 0) {  // FP32 complex: two per 16-byte load
       const float4 *v = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-      for (int q = 0; q < N / PER16; ++q) {
+      for (int q = 0; q < N / 2; ++q) {
         const float4 w = v[q];
-        if (PER16 == 2) {
-          reinterpret_cast<float2 *>(dst)[2 * q] = make_float2(w.x, w.y);
-          reinterpret_cast<float2 *>(dst)[2 * q + 1] = make_float2(w.z, w.w);
-        } else {
-          reinterpret_cast<float4 *>(dst)[q] = w;
-        }
+        dst[2 * q] = mk<T>((T)w.x, (T)w.y);
+        dst[2 * q + 1] = mk<T>((T)w.z, (T)w.w);
       }
-    } else {
+    } else {  // FP64 complex is one 16-byte load each
 #pragma unroll
       for (int k = 0; k < N; ++k) dst[k] = src[k];
     }
   }
 };
+
+// ------------------------------------------------------------ Y = C + A M
+// CG output columns per lane, N / CG lanes per row (a row never straddles a
+// warp); each lane loads only its slice of the A row, the row is assembled in
+// a padded per-warp buffer and read back whole.  M (n x n) sits in shared
+// memory.  TA: type of A and M, TY: type of C and Y (precision conversion here).
+template <typename TA, typename TY, int N, int CG>
+__global__ void __launch_bounds__(256) k_block_axpy(const C<TA> *__restrict__ Ain, const C<TY> *__restrict__ Cin,
+                                                    const C<TA> *__restrict__ M, C<TY> *__restrict__ Y, long rows) {
+  constexpr int TPR = N / CG;
+  constexpr int RPW = 32 / TPR;
+  constexpr int RS = N + (16 / (int)sizeof(C<TA>) > 0 ? 16 / (int)sizeof(C<TA>) : 1);
+  __shared__ C<TA> sm[N * N];
+  __shared__ __align__(16) C<TA> rowbuf[8][RPW * RS];
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) sm[k] = M[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / TPR;
+  const int j0 = (lane - slot * TPR) * CG;
+  C<TA> *wrow = rowbuf[warp];
+  const long rows_per_cta = (long)(blockDim.x >> 5) * RPW;
+  for (long rbase = (long)blockIdx.x * rows_per_cta; rbase < rows; rbase += (long)gridDim.x * rows_per_cta) {
+    const long r = rbase + (long)warp * RPW + slot;
+    const bool live = slot < RPW && r < rows;
+    if (live) {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) wrow[slot * RS + j0 + c] = Ain[r * N + j0 + c];
+    }
+    __syncwarp();
+    if (live) {
+      C<TA> a[N];
+      Row<TA, N>::load(wrow + slot * RS, a);
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        C<TA> acc = czero<TA>();
+#pragma unroll
+        for (int k = 0; k < N; ++k) cmac<TA>(acc, a[k], sm[k * N + j0 + c]);
+        if (Cin) {
+          const C<TY> cv = Cin[r * N + j0 + c];
+          Y[r * N + j0 + c] = mk<TY>((TY)(cv.x + acc.x), (TY)(cv.y + acc.y));
+        } else {
+          Y[r * N + j0 + c] = mk<TY>((TY)acc.x, (TY)acc.y);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ fused all-shift update
 
 // coef layout (type C<T>): [0, N*N) rho^-1; then for s: M1^(s) at (1+2s)*N*N,
 // M2^(s) at (2+2s)*N*N.  upd[s] != 0 selects the shifts updated this iteration.
@@ -250,21 +266,28 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
     C<T> q[CG];
 #pragma unroll
     for (int c = 0; c < CG; ++c) q[c] = czero<T>();
-    if (live) {
-      if (compute_q) {
+    if (compute_q) {
+      // the W row is assembled in the warp's row buffer from the lanes' slices
+      if (live) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const C<T> w = W[r * N + k];
+        for (int c = 0; c < CG; ++c) wrow[slot * RS + j0 + c] = W[r * N + j0 + c];
+      }
+      __syncwarp();
+      if (live) {
+        C<T> w[N];
+        Row<T, N>::load(wrow + slot * RS, w);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
 #pragma unroll
           for (int c = 0; c < CG; ++c)
-            if (k <= j0 + c) cmac<T>(q[c], w, sc[k * N + j0 + c]);
-        }
+            if (k <= j0 + c) cmac<T>(q[c], w[k], sc[k * N + j0 + c]);
 #pragma unroll
         for (int c = 0; c < CG; ++c) Q[r * N + j0 + c] = q[c];
-      } else {
-#pragma unroll
-        for (int c = 0; c < CG; ++c) q[c] = Q[r * N + j0 + c];
       }
+      __syncwarp();
+    } else if (live) {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) q[c] = Q[r * N + j0 + c];
     }
     for (int s = s_begin; s < s_end; ++s) {
       if (!supd[s]) continue;
@@ -447,10 +470,15 @@ template rhmc_status_t gram<double>(const double2 *, const double2 *, long, int,
 template <typename TA, typename TY>
 rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY> *Y, long rows, int n,
                          cudaStream_t s) {
-  const int bs = 128;
-  const long grid = (rows + bs - 1) / bs;
+  const int bs = 256;
   prof_begin(PROF_AXPY, s);
-#define L_AXPY(NN) k_block_axpy<TA, TY, NN><<<grid, bs, 0, s>>>(A, Cin, M, Y, rows)
+#define L_AXPY(NN)                                                                           \
+  do {                                                                                       \
+    constexpr int CG = (NN % 4 == 0) ? 4 : ((NN % 2 == 0) ? 2 : 1);                          \
+    const long rpc = (long)(bs / 32) * (32 / (NN / CG));                                     \
+    const long grid = std::min<long>((rows + rpc - 1) / rpc, 8 * 152);                      \
+    k_block_axpy<TA, TY, NN, CG><<<(unsigned)grid, bs, 0, s>>>(A, Cin, M, Y, rows);          \
+  } while (0)
   RHMC_DISPATCH_N(n, L_AXPY)
 #undef L_AXPY
   prof_end(s, (double)rows * n * (sizeof(C<TA>) + sizeof(C<TY>) * (Cin ? 2 : 1)));
