@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="8^4 n_pf=4 quick check (not a bench line)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 per-vector SCG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
     return ap.parse_args()
 
 
@@ -184,6 +185,59 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ batched ensembles
+BATCH = {
+    "workload": "6 ensembles 8^4,12^4,16^4,16^3x32,20^4,24^4 (eps=0.5), n_pf 2,4,8,8,12,16, 12 shifts of "
+                "x^(-1/(4 n_pf)) on [2e-3,64], m=0.025, tol 1e-8, mixed",
+    "dims": [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (16, 16, 16, 32), (20, 20, 20, 20), (24, 24, 24, 24)],
+    "n_pf": [2, 4, 8, 8, 12, 16],
+    "mass": 0.025,
+    "tol": 1e-8,
+}
+
+
+def run_batch(dev, reps=3):
+    """One batched SBCGrQ over six uneven ensembles (rhmc_block_multishift_cg_batch)
+    against the same six solves issued one after another on one stream."""
+    import torch
+    from paper_1808_01829_gb300 import synthetic as syn
+    from paper_1808_01829_gb300.api import RhmcContext, block_multishift_cg_batch
+    from paper_1808_01829_gb300.remez import rational_approx
+
+    items = []
+    for k, (dims, n) in enumerate(zip(BATCH["dims"], BATCH["n_pf"])):
+        ra = rational_approx(-1.0 / (4 * n), 2e-3, 64.0, 12)
+        ctx = RhmcContext(dims, BATCH["mass"], device=dev.index or 0)
+        ctx.set_gauge(torch.from_numpy(syn.random_links(dims, 0.5, syn.seed_gauge(10 + k))).to(dev))
+        B = torch.from_numpy(syn.gaussian_pseudofermions(dims, n, syn.seed_phi(10 + k))).to(dev)
+        items.append((ctx, B, ra.beta))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        out = []
+        for it in range(reps + 1):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                out.append(a.elapsed_time(b))
+        return statistics.median(out), r
+
+    seq_ms, seq = timed(lambda: [c.block_multishift_cg(B, sh, BATCH["tol"], precision="mixed")[1]
+                                 for c, B, sh in items])
+    bat_ms, bat = timed(lambda: [i for _, i in block_multishift_cg_batch(items, BATCH["tol"], precision="mixed")])
+    sites_rhs = sum(int(torch.tensor(d).prod()) // 2 * n for d, n in zip(BATCH["dims"], BATCH["n_pf"]))
+    res = {"workload": BATCH["workload"], "ms": bat_ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / bat_ms,
+           "iters": [i.iters for i in bat], "true_rel_resid_max": max(i.true_rel_resid_max for i in bat),
+           "site_rhs_shifts_per_s": sites_rhs * 12 / (bat_ms * 1e-3)}
+    for c, _, _ in items:
+        c.close()
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -286,6 +340,10 @@ def run_gpu(args):
                 "speedup": a.elapsed_time(b) / ms}
         del Xs
 
+    batch = None
+    if not args.no_batch and not args.small:
+        batch = run_batch(dev)
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         t_iter, t_force, threads = cpu_sample(cfg, U, Phi, ra)
@@ -314,6 +372,7 @@ def run_gpu(args):
                        "phase1_rel_resid_max": last.phase1_rel_resid_max,
                        "true_rel_resid_max": last.true_rel_resid_max},
             "baseline_fp64_scg": base,
+            "batched_ensemble": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -154,6 +154,30 @@ rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *ctx, const void *B_dev, int n
                                        const double *shifts, void *X_dev, double tol, int max_iter,
                                        rhmc_precision_t p, void *workspace, rhmc_info_t *info, rhmc_stream_t s);
 
+/* One member of a batched solve: its own context (lattice, gauge field),
+ * right-hand sides, shifts, output and (optional) workspace, as in
+ * rhmc_block_multishift_cg.  status is written by the call. */
+typedef struct {
+  rhmc_ctx_t *ctx;
+  const void *B;
+  int n_rhs;
+  int n_shifts;
+  const double *shifts;
+  void *X;
+  void *workspace;    /* NULL: the context's pool */
+  rhmc_info_t *info;  /* optional */
+  rhmc_status_t status;
+} rhmc_batch_item_t;
+
+/* Several independent SBCGrQ solves at once (ensembles of different lattice
+ * sizes, widths and shifts): every item runs on its context's own stream from
+ * a worker thread, with its iterations in captured CUDA graphs, so the small
+ * lattices' kernels overlap the large ones' on the GPU.  Work starts after what
+ * is already queued on stream s, and s waits for all of it.  Each context may
+ * appear once.  Returns the first failing item's status (all items run). */
+rhmc_status_t rhmc_block_multishift_cg_batch(rhmc_batch_item_t *items, int count, double tol, int max_iter,
+                                             rhmc_precision_t p, rhmc_stream_t s);
+
 /* Baseline: plain per-vector FP64 multishift CG (SCG, Sec. III), one
  * right-hand side at a time with a width-1 operator.  Same arguments and
  * output as rhmc_block_multishift_cg with p = RHMC_FP64. */
@@ -212,17 +236,20 @@ rhmc_status_t rhmc_profile_enable(int on);
 /* Launch-parameter tuning, process-wide (used by the autotuner).  Keys:
  *   RHMC_TUNE_HOP_RHS_PER_THREAD  right-hand sides per thread in the hop
  *                                 kernel: 1, 2 or 4 (must divide n_rhs)
- *   RHMC_TUNE_UPDATE_THREADS      threads per CTA of the fused shift update
+ *   RHMC_TUNE_UPDATE_THREADS      threads per CTA of the fused shift update: a
+ *                                 multiple of 32 up to 256 (other values: 256)
  *   RHMC_TUNE_FLUSH_EVERY         mixed precision: add the FP32 solution increments
  *                                 into the FP64 solutions every k iterations as
  *                                 well as at reliable updates (0: only there)
  *   RHMC_TUNE_RELIABLE_DELTA_MILLI  mixed precision: reliable update when the
  *                                 base residual fell by value/1000 (0: 0.1)
- *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 8)
+ *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 6)
  *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
  *                                 true residuals with native FP64 instead of RHMC_DF64
  *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, n_rhs = 16: shifted updates on the
  *                                 tensor cores (tcgen05, 3xTF32) = 1, CUDA cores = 2 (built-in)
+ *   RHMC_TUNE_GRAPHS              solver iterations in captured CUDA graphs (0, 1: built-in)
+ *                                 or as eager launches (2)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -231,7 +258,8 @@ enum {
   RHMC_TUNE_RELIABLE_DELTA_MILLI = 3,
   RHMC_TUNE_CHECK_EVERY = 4,
   RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5,
-  RHMC_TUNE_UPDATE_TENSOR = 6
+  RHMC_TUNE_UPDATE_TENSOR = 6,
+  RHMC_TUNE_GRAPHS = 7
 };
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);

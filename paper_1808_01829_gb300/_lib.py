@@ -57,6 +57,20 @@ class Info(ctypes.Structure):
     ]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("ctx", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("n_rhs", ctypes.c_int),
+        ("n_shifts", ctypes.c_int),
+        ("shifts", ctypes.POINTER(ctypes.c_double)),
+        ("X", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("info", ctypes.POINTER(Info)),
+        ("status", ctypes.c_int),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -82,6 +96,8 @@ def load():
         lib.rhmc_apply_mdagm_mrhs_noalloc.argtypes = [P, P, P, I, D, P]
         lib.rhmc_apply_mdagm_mrhs_noalloc.restype = I
         lib.rhmc_block_multishift_cg.argtypes = [P, P, I, I, PD, P, D, I, I, P, ctypes.POINTER(Info), P]
+        lib.rhmc_block_multishift_cg_batch.argtypes = [ctypes.POINTER(BatchItem), I, D, I, I, P]
+        lib.rhmc_block_multishift_cg_batch.restype = I
         lib.rhmc_multishift_cg_pervector.argtypes = [P, P, I, I, PD, P, D, I, P, ctypes.POINTER(Info), P]
         lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
         lib.rhmc_rational_apply.argtypes = [P, P, I, D, PD, I, P, P, P]
@@ -116,5 +132,5 @@ def exported_symbols():
         "rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_workspace_bytes", "rhmc_apply_mdagm_mrhs",
         "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
         "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
-        "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply",
+        "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply", "rhmc_block_multishift_cg_batch",
     ]

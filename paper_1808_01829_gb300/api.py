@@ -183,3 +183,32 @@ class RhmcContext:
                                  ctypes.byref(info), _stream(Phi))
         _lib.check(rc, "rhmc_force")
         return G, S.value, self._info(info, buf, ns, n)
+
+
+def block_multishift_cg_batch(items, tol: float, max_iter: int = 0, precision: str = "mixed"):
+    """Batched SBCGrQ over independent ensembles (rhmc_block_multishift_cg_batch).
+
+    items: sequence of (RhmcContext, B, shifts).  Returns a list of (X, SolveInfo)
+    in the same order.  Every context must have its gauge field set and may
+    appear once."""
+    n_items = len(items)
+    arr = (_lib.BatchItem * n_items)()
+    keep, outs = [], []
+    for i, (rctx, B, shifts) in enumerate(items):
+        n = B.shape[-1]
+        _check_field(B, "B", rctx.field_shape(n))
+        ns = len(shifts)
+        X = torch.empty((ns,) + tuple(B.shape), dtype=B.dtype, device=B.device)
+        sh = _doubles(shifts)
+        buf = (ctypes.c_double * (ns * n))()
+        info = _lib.Info()
+        info.per_shift_resid = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
+        arr[i] = _lib.BatchItem(rctx._h, B.data_ptr(), n, ns, ctypes.cast(sh, ctypes.POINTER(ctypes.c_double)),
+                                X.data_ptr(), None, ctypes.pointer(info), 0)
+        keep += [sh, buf, info]
+        outs.append((rctx, X, info, buf, ns, n))
+    lib = _lib.load()
+    rc = lib.rhmc_block_multishift_cg_batch(arr, n_items, float(tol), int(max_iter), PRECISION[precision],
+                                            _stream(items[0][1]))
+    _lib.check(rc, "rhmc_block_multishift_cg_batch")
+    return [(X, rctx._info(info, buf, ns, n)) for (rctx, X, info, buf, ns, n) in outs]

@@ -26,6 +26,8 @@
 #include <cstdarg>
 #include <cstring>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -93,7 +95,9 @@ void set_error(const char *fmt, ...) {
 constexpr int kParts = 304;           // partial sums of the simple reductions (2 CTAs per SM)
 constexpr int kGramParts = 1;         // the Gram kernels deliver the summed n x n matrix
 constexpr double kReliableDelta = 0.1;
-constexpr int kCheckEvery = 8;        // iterations between host checks
+constexpr int kCheckEvery = 6;        // iterations between host checks (a multiple of 6 keeps the
+                                      // k % 2 and k % 3 slot pattern of a captured chunk fixed)
+constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
@@ -127,8 +131,18 @@ struct rhmc_ctx {
   double *h_pin = nullptr;  // pinned host staging (readbacks)
   size_t h_pin_bytes = 0;
   cudaStream_t side = nullptr;     // shifted coefficient steps and updates
+  cudaStream_t own = nullptr;      // the context's stream in batched solves
+  cudaStream_t cap = nullptr;      // graph capture (the caller's stream may be the legacy default stream)
   cudaEvent_t ev_base[3] = {};     // base update of iteration k done (slot k % 3)
   cudaEvent_t ev_side[3] = {};     // shifted updates of iteration k done
+  struct GraphEntry {
+    std::vector<double> key;        // what the captured chunk depends on
+    cudaGraphExec_t exec;
+    long long launches;             // kernels in one replay
+    unsigned long long last_use;
+  };
+  std::vector<GraphEntry> graphs;   // captured SBCGrQ chunks (CUDA graphs)
+  unsigned long long graph_clock = 0;
 };
 
 namespace rhmc {
@@ -311,6 +325,9 @@ static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cuda
   return RHMC_OK;
 }
 
+// Captured CUDA graphs for the solver chunks (not while profiling).
+static bool use_graphs() { return !prof_on() && tune_get(TUNE_GRAPHS) != 2; }
+
 // Tensor-core shifted updates: FP32 fields, 16 right-hand sides.
 template <typename T> static bool use_tensor_update(int n) {
   if (sizeof(T) != 4 || n != 16) return false;
@@ -330,7 +347,7 @@ template <typename T> static bool use_tensor_update(int n) {
 //             the buffer Q_k = Qb[k & 1] that side(k-2) was reading.
 template <typename T, typename TX>
 static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc, int n, int ns, double sigma0, int k,
-                                      double tol_shift, int freeze, cudaStream_t s) {
+                                      int chunk_start, double tol_shift, int freeze, cudaStream_t s) {
   const long rows = c->g.Vh * 3;
   const long len = rows * n;
   C<T> *P = (C<T> *)b.P, *W = (C<T> *)b.W, *AP = (C<T> *)b.AP, *Todd = (C<T> *)b.Todd;
@@ -339,7 +356,8 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   // serialised) so that per-kernel event times are not inflated by overlap.
   const bool split = ns > 1 && !prof_on();
   cudaStream_t ss = split ? c->side : s;
-  if (split && k >= 3) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[(k - 2) % 3], 0));
+  // (chunk boundaries are joined on the host, so only waits inside a chunk are needed)
+  if (split && k - 2 > chunk_start) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[(k - 2) % 3], 0));
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
   RHMC_TRY(gram<T>(P, AP, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
@@ -368,6 +386,76 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
 // Make stream s wait for everything enqueued so far on the side stream.
 static rhmc_status_t join_side(rhmc_ctx *c, int k, int ns, cudaStream_t s) {
   if (ns > 1 && k >= 1 && !prof_on()) RHMC_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_side[k % 3], 0));
+  return RHMC_OK;
+}
+
+// Run iterations chunk_start+1 .. chunk_start+len, joined back to stream s.
+template <typename T>
+static rhmc_status_t run_chunk(rhmc_ctx *c, const SolveBufs &b, double2 *X, int n, int ns, double sigma0,
+                               int chunk_start, int len, double target, int freeze, cudaStream_t s) {
+  for (int q = 1; q <= len; ++q) {
+    const int k = chunk_start + q;
+    if (std::is_same<T, float>::value)
+      RHMC_TRY((sbcgrq_iteration<float, float>(c, b, (float *)b.Xinc, n, ns, sigma0, k, chunk_start, target, freeze,
+                                                s)));
+    else
+      RHMC_TRY((sbcgrq_iteration<double, double>(c, b, (double *)X, n, ns, sigma0, k, chunk_start, target, freeze,
+                                                  s)));
+  }
+  return join_side(c, chunk_start + len, ns, s);
+}
+
+// The same chunk as a CUDA graph, captured once per (workspace, sizes, shift,
+// tolerance, tuning) and replayed for every later chunk that starts at a
+// multiple of kCheckEvery.  Capture runs on the context's capture stream (the
+// legacy default stream cannot be captured); the graph is launched on s.
+template <typename T>
+static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X, int n, int ns, double sigma0,
+                                     int chunk_start, int len, double target, int freeze, cudaStream_t s) {
+  std::vector<double> key = {(double)(uintptr_t)b.P, (double)(uintptr_t)X, (double)n,
+                             (double)ns, sigma0, target, (double)freeze, (double)sizeof(T), (double)len,
+                             (double)(chunk_start % kCheckEvery)};
+  for (int t = 0; t < TUNE_NKEYS; ++t) key.push_back((double)tune_get(t));
+  rhmc_ctx::GraphEntry *hit = nullptr;
+  for (auto &e : c->graphs)
+    if (e.key == key) hit = &e;
+  if (!hit) {
+    if ((int)c->graphs.size() >= kGraphCacheMax) {  // evict the least recently used
+      auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                  [](const rhmc_ctx::GraphEntry &a, const rhmc_ctx::GraphEntry &b2) {
+                                    return a.last_use < b2.last_use;
+                                  });
+      cudaGraphExecDestroy(lru->exec);
+      c->graphs.erase(lru);
+    }
+    const long long before = rhmc_kernel_launches();
+    RHMC_CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    const rhmc_status_t rc = run_chunk<T>(c, b, X, n, ns, sigma0, chunk_start, len, target, freeze, c->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
+    const long long captured = rhmc_kernel_launches() - before;
+    g_launches.fetch_sub(captured);  // recorded, not run: counted at every replay instead
+    if (rc != RHMC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ec != cudaSuccess) {
+      set_error("stream capture of a solver chunk failed: %s", cudaGetErrorString(ec));
+      return RHMC_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      set_error("graph instantiation failed: %s", cudaGetErrorString(ei));
+      return RHMC_ERR_CUDA;
+    }
+    c->graphs.push_back({key, exec, captured, 0});
+    hit = &c->graphs.back();
+  }
+  hit->last_use = ++c->graph_clock;
+  RHMC_CUDA_TRY(cudaGraphLaunch(hit->exec, s));
+  g_launches.fetch_add(hit->launches);
   return RHMC_OK;
 }
 
@@ -413,17 +501,15 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   const int kmax = prm.fixed_iters > 0 ? prm.fixed_iters : prm.max_iter;
   while (k < kmax) {
     const int chunk = prm.fixed_iters > 0 ? kmax : std::min(check_every, kmax - k);
-    for (int q = 0; q < chunk; ++q) {
-      ++k;
-      if (mixed)
-        RHMC_TRY((sbcgrq_iteration<float, float>(c, b, (float *)b.Xinc, n, ns, sigma0, k, target,
-                                                  prm.fixed_iters > 0 ? 0 : 1, s)));
-      else
-        RHMC_TRY((sbcgrq_iteration<double, double>(c, b, (double *)X, n, ns, sigma0, k, target,
-                                                    prm.fixed_iters > 0 ? 0 : 1, s)));
-      stats.dirac++;
-    }
-    RHMC_TRY(join_side(c, k, ns, s));
+    const int freeze = prm.fixed_iters > 0 ? 0 : 1;
+    const bool graph = use_graphs() && chunk == kCheckEvery && check_every == kCheckEvery && k > 0 &&
+                       k % kCheckEvery == 0;
+    if (graph)
+      RHMC_TRY(run_chunk_graph<T>(c, b, X, n, ns, sigma0, k, chunk, target, freeze, s));
+    else
+      RHMC_TRY(run_chunk<T>(c, b, X, n, ns, sigma0, k, chunk, target, freeze, s));
+    k += chunk;
+    stats.dirac += chunk;
     RHMC_TRY(read_state(c, b.st, v, s));
     if (v.device_timeout) {
       set_error("a bounded device-side wait expired in the tensor-core update (iteration %d)", k);
@@ -697,7 +783,9 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
       return RHMC_ERR_CUDA;
     }
   }
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("rhmc_create: cannot create the side stream");
     rhmc_destroy(c);
     return RHMC_ERR_CUDA;
@@ -722,6 +810,8 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
     if (c->ldf[p]) cudaFree(c->ldf[p]);
   }
   if (c->side) cudaStreamSynchronize(c->side);
+  for (auto &e : c->graphs) cudaGraphExecDestroy(e.exec);
+  c->graphs.clear();
   if (c->pool) cudaFree(c->pool);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (int q = 0; q < 3; ++q) {
@@ -729,6 +819,8 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);
   }
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->own) cudaStreamDestroy(c->own);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return RHMC_OK;
 }
@@ -909,6 +1001,63 @@ rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *c, const void *B, int n, int 
   }
   return block_solve_entry(c, (const double2 *)B, n, ns, shifts, (double2 *)X, tol, max_iter, p == RHMC_MIXED_FP32,
                            0, ws, info, s);
+}
+
+rhmc_status_t rhmc_block_multishift_cg_batch(rhmc_batch_item_t *items, int count, double tol, int max_iter,
+                                             rhmc_precision_t p, rhmc_stream_t sv) {
+  if (!items || count < 1 || count > 64) {
+    set_error("rhmc_block_multishift_cg_batch: bad item list (count %d)", count);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i) {
+    rhmc_batch_item_t &it = items[i];
+    it.status = check_common(it.ctx, it.B, it.X, it.n_rhs);
+    if (it.status == RHMC_OK) it.status = check_shifts(it.n_shifts, it.shifts, tol);
+    if (it.status != RHMC_OK) return it.status;
+    for (int j = 0; j < i; ++j)
+      if (items[j].ctx == it.ctx) {
+        set_error("rhmc_block_multishift_cg_batch: items %d and %d share a context", j, i);
+        return RHMC_ERR_INVALID_ARG;
+      }
+  }
+  cudaStream_t s = (cudaStream_t)sv;
+  cudaEvent_t start;
+  RHMC_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  RHMC_CUDA_TRY(cudaEventRecord(start, s));
+  std::vector<std::string> msg(count);
+  std::vector<std::thread> pool;
+  for (int i = 0; i < count; ++i)
+    pool.emplace_back([&, i] {
+      rhmc_batch_item_t &it = items[i];
+      rhmc_ctx *c = it.ctx;
+      DeviceGuard dg(c->device);
+      cudaStreamWaitEvent(c->own, start, 0);
+      void *ws = it.workspace;
+      if (!ws) {
+        it.status = ensure_pool(c, rhmc_workspace_bytes(c, it.n_rhs, it.n_shifts, p));
+        ws = c->pool;
+      }
+      if (it.status == RHMC_OK)
+        it.status = block_solve_entry(c, (const double2 *)it.B, it.n_rhs, it.n_shifts, it.shifts, (double2 *)it.X,
+                                      tol, max_iter, p == RHMC_MIXED_FP32, 0, ws, it.info, c->own);
+      if (it.status != RHMC_OK) msg[i] = rhmc_last_error();
+    });
+  for (auto &t : pool) t.join();
+  cudaEventDestroy(start);
+  rhmc_status_t worst = RHMC_OK;
+  for (int i = 0; i < count; ++i) {
+    // the caller's stream continues after every item's work
+    cudaEvent_t done;
+    RHMC_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    RHMC_CUDA_TRY(cudaEventRecord(done, items[i].ctx->own));
+    RHMC_CUDA_TRY(cudaStreamWaitEvent(s, done, 0));
+    cudaEventDestroy(done);
+    if (items[i].status != RHMC_OK && worst == RHMC_OK) {
+      worst = items[i].status;
+      set_error("batch item %d: %s", i, msg[i].c_str());
+    }
+  }
+  return worst;
 }
 
 rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n, int ns, const double *shifts,

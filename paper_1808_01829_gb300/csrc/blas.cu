@@ -12,6 +12,8 @@
 //   flush       X64 += X32, X32 = 0 (mixed precision reliable-update flush)
 #include <algorithm>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -438,12 +440,11 @@ static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratc
   const size_t smem = (size_t)kGramWarps * 2 * (same ? 1 : 2) * kGramTileRows * N * sizeof(C<T>);
   const size_t smem_red = (size_t)kGramWarps * N * N * sizeof(double2);
   const size_t bytes = std::max(smem, smem_red);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_gram<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gram<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  });
   const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
   const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, kGramCtas);
   if (same)
@@ -497,14 +498,13 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
                           int s_end, int compute_q, long rows, long fstride, cudaStream_t s) {
   constexpr int CG = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
   int threads = tune_get(TUNE_UPDATE_THREADS);
-  if (threads <= 0 || threads > 1024 || threads % 32) threads = 256;
+  if (threads <= 0 || threads > 256 || threads % 32) threads = 256;  // __launch_bounds__(256)
   const size_t smem = (size_t)((1 + 2 * s_end) - (compute_q ? 0 : 1 + 2 * s_begin)) * N * N * sizeof(C<T>) +
                       (size_t)(threads / 32) * (32 / (N / CG)) * (N + 16 / sizeof(C<T>)) * sizeof(C<T>);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_update_all<T, TX, N, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+  });
   const long rows_per_cta = (long)(threads / 32) * (32 / (N / CG));
   long grid = (rows + rows_per_cta - 1) / rows_per_cta;
   grid = std::min(grid, (long)(8 * 152));

@@ -102,6 +102,7 @@ enum TuneKey {
   TUNE_CHECK_EVERY,          // iterations between host convergence checks (0: 8)
   TUNE_NATIVE_FP64_RESIDUALS, // mixed: native FP64 instead of double-float for residuals (0: double-float)
   TUNE_UPDATE_TENSOR,         // mixed, n = 16: shifted updates on tcgen05 (1) or CUDA cores (2); 0: built-in
+  TUNE_GRAPHS,                // solver chunks as captured CUDA graphs (0/1) or eager launches (2)
   TUNE_NKEYS
 };
 int tune_get(int key);

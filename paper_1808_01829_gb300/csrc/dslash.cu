@@ -10,6 +10,8 @@
 // site needs are contiguous: a CTA stages the records of its site tile into
 // shared memory with coalesced 16-byte loads and every thread of the tile (one
 // per (site, right-hand side)) reads them from there.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -223,14 +225,13 @@ static void launch_hop(const Geom &g, int par, const C<T> *links, const C<T> *in
   const int threads = ((tile * tps + 31) / 32) * 32;
   const size_t smem = (stage ? (size_t)tile * 72 * sizeof(LS) : 0) + (size_t)tile * 8 * sizeof(int);
   const unsigned grid = (unsigned)((g.Vh + tile - 1) / tile);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::once_flag attr_done;
+  std::call_once(attr_done, [&] {
     cudaFuncSetAttribute(k_hop<T, R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     cudaFuncSetAttribute(k_hop<T, R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     cudaFuncSetAttribute(k_hop<T, R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     cudaFuncSetAttribute(k_hop<T, R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr_done = true;
-  }
+  });
   if (self) {
     if (stage)
       k_hop<T, R, true, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (T)a, n, tile, nbatch, bstride);
@@ -405,12 +406,11 @@ rhmc_status_t hop_df(const Geom &g, int par, const float4 *links, const float4 *
   const int tile = max(1, 128 / n);
   const int threads = ((tile * n + 31) / 32) * 32;
   const size_t smem = (size_t)tile * 72 * sizeof(float4) + (size_t)tile * 8 * sizeof(int);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_hop_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_hop_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  });
   const float ah = (float)a, al = (float)(a - (double)ah);
   const unsigned grid = (unsigned)((g.Vh + tile - 1) / tile);
   prof_begin(PROF_HOP_DF, s);

@@ -22,6 +22,8 @@
 // update X^(s) and P^(s).  A wait that does not finish within its iteration
 // limit sets an error flag; the kernel then frees its tensor memory and
 // returns.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -275,11 +277,10 @@ rhmc_status_t update_shifts_tc(const float2 *Q, float2 *P, float2 *X, const floa
   k_tc_prepare_b<<<s_end - s_begin, 256, 0, s>>>(coef, s_begin, s_end, btiles);
   RHMC_LAUNCH_CHECK();
   const size_t smem = 1024 + (size_t)(2 * kTcRows * kTcK + 2 * kTcN * kTcK) * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   const long tiles = (rows + kTcRows - 1) / kTcRows;
   const int grid = (int)std::min<long>(tiles, 4 * 152);
   int nupd = s_end - s_begin;

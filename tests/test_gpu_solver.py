@@ -96,7 +96,7 @@ def test_n1_equals_scalar_cg_iterates():
 
 
 def kcheck_slack():
-    return 8  # host checks every 8 iterations
+    return 6  # host checks every 6 iterations
 
 
 def test_pervector_scg_baseline_matches_oracle():
