@@ -370,6 +370,7 @@ def run_gpu(args):
             "solver": {"iters": last.iters, "dirac_calls": last.dirac_calls, "reliable_updates": last.reliable_updates,
                        "refinements": last.refinements, "refine_iters": last.refine_iters,
                        "phase1_rel_resid_max": last.phase1_rel_resid_max,
+                       "phase1_ms": last.phase1_ms, "refine_ms": last.refine_ms,
                        "true_rel_resid_max": last.true_rel_resid_max},
             "baseline_fp64_scg": base,
             "batched_ensemble": batch,

@@ -92,6 +92,8 @@ typedef struct {
   double true_rel_resid_max; /* max_{s,j} ||B e_j - (A+sigma_s) X^(s) e_j|| / ||B e_j||, FP64 */
   double phase1_rel_resid_max; /* the same before any defect correction */
   double *per_shift_resid;   /* optional caller array [n_shifts*n_rhs] (shift-major), or NULL */
+  double phase1_ms;          /* device time of the multishift solve (events on the call's stream) */
+  double refine_ms;          /* device time of the true-residual checks and defect corrections */
 } rhmc_info_t;
 
 /* Create a context on CUDA device `device` for lattice `lat`.
@@ -250,6 +252,8 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 tensor cores (tcgen05, 3xTF32) = 1, CUDA cores = 2 (built-in)
  *   RHMC_TUNE_GRAPHS              solver iterations in captured CUDA graphs (0, 1: built-in)
  *                                 or as eager launches (2)
+ *   RHMC_TUNE_HOP_STAGED          FP32 hop with tiles staged in shared memory by cp.async
+ *                                 for even n (1) or the register-staged kernel (0, 2: built-in)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -259,7 +263,8 @@ enum {
   RHMC_TUNE_CHECK_EVERY = 4,
   RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5,
   RHMC_TUNE_UPDATE_TENSOR = 6,
-  RHMC_TUNE_GRAPHS = 7
+  RHMC_TUNE_GRAPHS = 7,
+  RHMC_TUNE_HOP_STAGED = 8
 };
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);

@@ -54,6 +54,8 @@ class Info(ctypes.Structure):
         ("true_rel_resid_max", ctypes.c_double),
         ("phase1_rel_resid_max", ctypes.c_double),
         ("per_shift_resid", ctypes.POINTER(ctypes.c_double)),
+        ("phase1_ms", ctypes.c_double),
+        ("refine_ms", ctypes.c_double),
     ]
 
 

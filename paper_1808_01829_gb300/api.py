@@ -34,6 +34,8 @@ class SolveInfo:
     true_rel_resid_max: float
     phase1_rel_resid_max: float
     per_shift_resid: list
+    phase1_ms: float = 0.0
+    refine_ms: float = 0.0
 
 
 def _stream(t: torch.Tensor):
@@ -127,7 +129,7 @@ class RhmcContext:
     def _info(self, info: _lib.Info, buf, ns, n):
         return SolveInfo(info.iters, info.dirac_calls, info.reliable_updates, info.refinements, info.refine_iters,
                          info.true_rel_resid_max, info.phase1_rel_resid_max,
-                         [list(buf[q * n:(q + 1) * n]) for q in range(ns)])
+                         [list(buf[q * n:(q + 1) * n]) for q in range(ns)], info.phase1_ms, info.refine_ms)
 
     # -- rhmc_block_multishift_cg
     def block_multishift_cg(self, B: torch.Tensor, shifts: Sequence[float], tol: float, max_iter: int = 0,

@@ -459,6 +459,32 @@ static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X
   return RHMC_OK;
 }
 
+// Device time between marks on one stream (events; read after the stream has
+// been synchronised).
+struct PhaseTimer {
+  cudaStream_t s;
+  cudaEvent_t ev[3] = {};
+  int n = 0;
+  explicit PhaseTimer(cudaStream_t s_) : s(s_) {
+    for (auto &e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[n++], s);
+  }
+  void mark() {
+    if (n < 3) cudaEventRecord(ev[n++], s);
+  }
+  double ms(int phase) {
+    float t = 0.f;
+    if (phase + 1 >= n || cudaEventSynchronize(ev[phase + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, ev[phase], ev[phase + 1]) != cudaSuccess)
+      return 0.0;
+    return t;
+  }
+  ~PhaseTimer() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 // Core solve of (A + sigma_s) X^(s) = B, shifts ascending, X FP64 [ns][len].
 // Returns OK when the recursive residuals reached the target (phase 1 only).
 template <typename T>
@@ -592,8 +618,10 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   SolveStats st;
   SolveParams p1 = prm;
   if (prm.fixed_iters <= 0) p1.tol = 0.5 * prm.tol;
+  PhaseTimer timer(s);
   rhmc_status_t rc = prm.mixed ? solve_phase1<float>(c, B, n, ns, shifts, X, p1, b, st, s)
                                : solve_phase1<double>(c, B, n, ns, shifts, X, p1, b, st, s);
+  timer.mark();
   if (rc != RHMC_OK && rc != RHMC_ERR_NOT_CONVERGED) return rc;
   const rhmc_status_t rc1 = rc;
 
@@ -650,7 +678,10 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
       RHMC_TRY(add_inplace(Xq, rb.E, len, s));  // X_q += E
     }
   }
+  timer.mark();
   if (info) {
+    info->phase1_ms = timer.ms(0);
+    info->refine_ms = timer.ms(1);
     info->iters = st.iters;
     info->dirac_calls = st.dirac;
     info->reliable_updates = st.reliable;

@@ -12,7 +12,9 @@
 //   flush       X64 += X32, X32 = 0 (mixed precision reliable-update flush)
 #include <algorithm>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -156,6 +158,33 @@ __global__ void __launch_bounds__(128) k_gram_sum(const double2 *__restrict__ pa
 }
 
 // Whole-row loads: 16-byte vector loads when the row is 16-byte aligned.
+// A lane's slice of CG consecutive complex numbers (32-byte aligned for FP32
+// complex with CG = 4): 16-byte vector accesses where the type allows.
+template <typename T, int CG> __device__ __forceinline__ void ld_slice(const C<T> *p, C<T> *v) {
+  if constexpr (sizeof(C<T>) == 8 && CG % 2 == 0) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < CG / 2; ++i) {
+      const float4 w = q[i];
+      v[2 * i] = mk<T>(w.x, w.y);
+      v[2 * i + 1] = mk<T>(w.z, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CG; ++c) v[c] = p[c];
+  }
+}
+template <typename T, int CG> __device__ __forceinline__ void st_slice(C<T> *p, const C<T> *v) {
+  if constexpr (sizeof(C<T>) == 8 && CG % 2 == 0) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < CG / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  } else {
+#pragma unroll
+    for (int c = 0; c < CG; ++c) p[c] = v[c];
+  }
+}
+
 template <typename T, int N> struct Row {
   __device__ static void load(const C<T> *src, C<T> *dst) {
     if (sizeof(C<T>) == 8 && N % 2 == 0) {  // FP32 complex: two per 16-byte load
@@ -291,17 +320,33 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
 #pragma unroll
       for (int c = 0; c < CG; ++c) q[c] = Q[r * N + j0 + c];
     }
-    for (int s = s_begin; s < s_end; ++s) {
-      if (!supd[s]) continue;
+    // software pipeline over the live shifts: the P^(s) and X^(s) slices of the
+    // next live shift are loaded while the current one is combined, so that a
+    // warp keeps two shifts' rows in flight
+    auto next_live = [&](int from) {
+      while (from < s_end && !supd[from]) ++from;
+      return from;
+    };
+    int s = next_live(s_begin);
+    C<T> own[CG];
+    CX ox[CG];
+    if (live && s < s_end) {
+      ld_slice<T, CG>(P + s * fstride + r * N + j0, own);
+      ld_slice<TX, CG>(X + s * fstride + r * N + j0, ox);
+    }
+    while (s < s_end) {
+      const int sn = next_live(s + 1);
+      C<T> nown[CG];
+      CX nox[CG];
+      if (live && sn < s_end) {
+        ld_slice<T, CG>(P + sn * fstride + r * N + j0, nown);
+        ld_slice<TX, CG>(X + sn * fstride + r * N + j0, nox);
+      }
       const C<T> *m1 = sc + (1 + 2 * s) * N * N - c0;
       const C<T> *m2 = m1 + N * N;
-      C<T> *Ps = P + s * fstride;
-      // each lane loads only its own CG columns; the row is assembled in the
+      // each lane holds only its own CG columns; the row is assembled in the
       // warp's shared row buffer and read back whole (no redundant global loads)
-      C<T> own[CG];
       if (live) {
-#pragma unroll
-        for (int c = 0; c < CG; ++c) own[c] = Ps[r * N + j0 + c];
 #pragma unroll
         for (int c = 0; c < CG; ++c) wrow[slot * RS + j0 + c] = own[c];
       }
@@ -322,17 +367,25 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
             cmac<T>(a1[c], p[k], m1[k * N + j0 + c]);
             cmac<T>(a2[c], p[k], m2[k * N + j0 + c]);
           }
-        CX *Xs = X + s * fstride + r * N + j0;
+        C<T> pn[CG];
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
-          CX x = Xs[c];
-          x.x += a1[c].x;
-          x.y += a1[c].y;
-          Xs[c] = x;
-          Ps[r * N + j0 + c] = mk<T>(q[c].x + a2[c].x, q[c].y + a2[c].y);
+          ox[c].x += a1[c].x;
+          ox[c].y += a1[c].y;
+          pn[c] = mk<T>(q[c].x + a2[c].x, q[c].y + a2[c].y);
         }
+        st_slice<TX, CG>(X + s * fstride + r * N + j0, ox);
+        st_slice<T, CG>(P + s * fstride + r * N + j0, pn);
       }
       __syncwarp();
+      if (sn < s_end) {
+#pragma unroll
+        for (int c = 0; c < CG; ++c) {
+          own[c] = nown[c];
+          ox[c] = nox[c];
+        }
+      }
+      s = sn;
     }
   }
 }
@@ -507,7 +560,8 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
   });
   const long rows_per_cta = (long)(threads / 32) * (32 / (N / CG));
   long grid = (rows + rows_per_cta - 1) / rows_per_cta;
-  grid = std::min(grid, (long)(8 * 152));
+  // persistent grid: as many CTAs as are resident at once (shared memory bound)
+  grid = std::min(grid, (long)resident_ctas(k_update_all<T, TX, N, CG>, threads, smem));
   k_update_all<T, TX, N, CG><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd,
                                                                    s_begin, s_end, compute_q, rows, fstride);
 }

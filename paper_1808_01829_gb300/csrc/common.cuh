@@ -4,8 +4,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "../../include/rhmc.h"
 
@@ -103,6 +107,7 @@ enum TuneKey {
   TUNE_NATIVE_FP64_RESIDUALS, // mixed: native FP64 instead of double-float for residuals (0: double-float)
   TUNE_UPDATE_TENSOR,         // mixed, n = 16: shifted updates on tcgen05 (1) or CUDA cores (2); 0: built-in
   TUNE_GRAPHS,                // solver chunks as captured CUDA graphs (0/1) or eager launches (2)
+  TUNE_HOP_STAGED,            // FP32 hop with cp.async-staged tiles: built-in (0), always (1), never (2)
   TUNE_NKEYS
 };
 int tune_get(int key);
@@ -127,5 +132,22 @@ void prof_end(cudaStream_t s, double bytes);
       return RHMC_ERR_CUDA;                                                                    \
     }                                                                                          \
   } while (0)
+
+// CTAs of kernel f resident on the whole GPU at once (cached per kernel and size).
+template <typename F> static int resident_ctas(F f, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void *, int, size_t, int>, int> cache;
+  int per_sm = 0, nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(reinterpret_cast<const void *>(f), threads, smem, dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const int v = per_sm * std::max(nsm, 1);
+  cache[key] = v;
+  return v;
+}
 
 }  // namespace rhmc

@@ -245,6 +245,206 @@ static void launch_hop(const Geom &g, int par, const C<T> *links, const C<T> *in
   }
 }
 
+// ------------------------------------------------------------ hop, cp.async staged
+// FP32, one field, even n: persistent CTAs walk over tiles of TS output sites.
+// All threads stage the next tile into shared memory with 16-byte cp.async
+// copies (L2 only) while the current tile is multiplied:
+//   the TS link records (TS * 72 complex, contiguous),
+//   the 8 neighbour rows of every site (3n complex each, gathered),
+//   the TS rows of `self` for the fused axpy (contiguous).
+// Two buffers, one cp.async group per tile, so every thread keeps a whole
+// tile's share of loads in flight without holding them in registers.  Every
+// thread owns R right-hand sides of one site.
+namespace {
+template <int R> struct SVec;  // shared-memory vector loads
+template <> struct SVec<1> {
+  __device__ static void ld(const float2 *p, float2 *v) { v[0] = p[0]; }
+};
+template <> struct SVec<2> {
+  __device__ static void ld(const float2 *p, float2 *v) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+  }
+};
+template <> struct SVec<4> {
+  __device__ static void ld(const float2 *p, float2 *v) {
+    SVec<2>::ld(p, v);
+    SVec<2>::ld(p + 2, v + 2);
+  }
+};
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+}  // namespace
+
+template <int R, bool SELF>
+__global__ void __launch_bounds__(128) k_hop_staged(Geom g, int par, const float2 *__restrict__ links,
+                                                    const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                    const float2 *__restrict__ self, float a, int n, int TS,
+                                                    int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int tps = n / R;
+  const int row = 3 * n;      // complex numbers of one site row
+  const int cpr = 3 * n / 2;  // 16-byte chunks of one site row
+  const unsigned link_b = (unsigned)TS * 72 * 8, nb_b = (unsigned)TS * 8 * row * 8;
+  const unsigned stage_b = link_b + nb_b + (SELF ? (unsigned)TS * row * 8 : 0u);
+  int *snb = reinterpret_cast<int *>(smem_raw + 2 * stage_b);  // [2][TS * 8] neighbour ranks
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  // per-thread walk over (row, chunk) pairs: start and stride without divisions in the loop
+  const int q0 = tid % cpr, r0 = tid / cpr, dq = nthr % cpr, dr = nthr / cpr;
+
+  auto fill_nb = [&](int tile, int buf) {
+    const int h0 = tile * TS;
+    const int ns = min(TS, (int)g.Vh - h0);
+    for (int k = tid; k < ns * 8; k += nthr) {
+      const int site = k >> 3, d = k & 7;
+      int x[4];
+      site_coords(g, par, h0 + site, x);
+      const int mu = d & 3, st = d < 4 ? 1 : -1;
+      int y0 = x[0], y1 = x[1], y2 = x[2], y3 = x[3];
+      if (mu == 0) y0 = (y0 + st + g.L[0]) % g.L[0];
+      else if (mu == 1) y1 = (y1 + st + g.L[1]) % g.L[1];
+      else if (mu == 2) y2 = (y2 + st + g.L[2]) % g.L[2];
+      else y3 = (y3 + st + g.L[3]) % g.L[3];
+      const int lex = y0 + g.L[0] * (y1 + g.L[1] * (y2 + g.L[2] * y3));
+      snb[buf * TS * 8 + k] = lex >> 1;
+    }
+  };
+  auto issue = [&](int tile, int buf) {
+    const int h0 = tile * TS;
+    const int ns = min(TS, (int)g.Vh - h0);
+    const unsigned base = (unsigned)__cvta_generic_to_shared(smem_raw + buf * stage_b);
+    const char *lsrc = reinterpret_cast<const char *>(links + (long)h0 * 72);
+    for (int c = tid; c < ns * 36; c += nthr) cp_async16(base + 16u * c, lsrc + 16L * c);
+    const int *nb = snb + buf * TS * 8;
+    int q = q0, r = r0;
+    while (r < ns * 8) {
+      cp_async16(base + link_b + (unsigned)(r * row * 8 + q * 16),
+                 reinterpret_cast<const char *>(in + (long)nb[r] * row) + 16 * q);
+      q += dq;
+      r += dr;
+      if (q >= cpr) {
+        q -= cpr;
+        ++r;
+      }
+    }
+    if (SELF) {
+      const char *ssrc = reinterpret_cast<const char *>(self + (long)h0 * row);
+      for (int c = tid; c < ns * cpr; c += nthr) cp_async16(base + link_b + nb_b + 16u * c, ssrc + 16L * c);
+    }
+  };
+  const int ls = tid / tps;
+  const int j0 = (tid - ls * tps) * R;
+  int tile = blockIdx.x;
+  if (tile < ntiles) {
+    fill_nb(tile, 0);
+    __syncthreads();
+    issue(tile, 0);
+  }
+  cp_async_commit();
+  for (int i = 0; tile < ntiles; tile += gridDim.x, ++i) {
+    const int buf = i & 1;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) fill_nb(next, buf ^ 1);
+    __syncthreads();  // neighbour table ready; buffer buf ^ 1 no longer read
+    if (next < ntiles) issue(next, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of the current tile landed
+    __syncthreads();     // ... and everyone else's
+    const int h0 = tile * TS;
+    const int ns = min(TS, (int)g.Vh - h0);
+    if (ls < ns) {
+      const unsigned char *sb = smem_raw + buf * stage_b;
+      const float2 *sl = reinterpret_cast<const float2 *>(sb) + ls * 72;
+      const float2 *sn = reinterpret_cast<const float2 *>(sb + link_b) + ls * 8 * row + j0;
+      float2 acc[3][R];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[c][r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int d = 0; d < 8; ++d) {
+        float2 v[3][R];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) SVec<R>::ld(sn + d * row + c * n, v[c]);
+#pragma unroll
+        for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 3; ++cb) {
+            const float2 e = sl[d * 9 + ca * 3 + cb];
+#pragma unroll
+            for (int r = 0; r < R; ++r) cmac<float>(acc[ca][r], e, v[cb][r]);
+          }
+      }
+      const long o = (long)(h0 + ls) * row + j0;
+      if (SELF) {
+        const float2 *ss = reinterpret_cast<const float2 *>(sb + link_b + nb_b) + ls * row + j0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float2 sv[R];
+          SVec<R>::ld(ss + c * n, sv);
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[c][r] = make_float2(a * sv[r].x - acc[c][r].x, a * sv[r].y - acc[c][r].y);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Vec<float, R>::st(out + o + c * n, acc[c]);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int R>
+static bool launch_hop_staged(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
+                              const float2 *self, double a, int n, cudaStream_t s) {
+  const int tps = n / R;
+  const long per_site = 576 + 8L * 24 * n + (self ? 24L * n : 0);
+  const int TS = (int)std::min<long>(128 / tps, (96 * 1024) / per_site);
+  if (TS < 1) return false;
+  const int threads = ((TS * tps + 31) / 32) * 32;
+  const size_t smem = 2 * (size_t)TS * per_site + 2 * (size_t)TS * 8 * sizeof(int);
+  const int ntiles = (int)((g.Vh + TS - 1) / TS);
+  static std::once_flag attr_done;
+  std::call_once(attr_done, [] {
+    cudaFuncSetAttribute(k_hop_staged<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(k_hop_staged<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  });
+  const int resident = self ? resident_ctas(k_hop_staged<R, true>, threads, smem)
+                            : resident_ctas(k_hop_staged<R, false>, threads, smem);
+  const int grid = std::min(ntiles, resident);
+  if (self)
+    k_hop_staged<R, true><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (float)a, n, TS, ntiles);
+  else
+    k_hop_staged<R, false><<<grid, threads, smem, s>>>(g, par, links, in, out, self, (float)a, n, TS, ntiles);
+  return true;
+}
+
+// The staged kernel applies to FP32 single fields with 16-byte aligned rows.
+template <typename T>
+static bool try_hop_staged(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out,
+                           const C<T> *self, double a, int n, int nbatch, int R, cudaStream_t s) {
+  if constexpr (sizeof(C<T>) != 8) {
+    return false;
+  } else {
+    const int mode = tune_get(TUNE_HOP_STAGED);
+    // built-in: the register-staged kernel (measured faster at 24^4, n = 8 and 16)
+    if (mode != 1 || nbatch != 1 || n % 2) return false;
+    auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al16(links) || !al16(in) || !al16(out) || (self && !al16(self))) return false;
+    const float2 *L = reinterpret_cast<const float2 *>(links), *X = reinterpret_cast<const float2 *>(in),
+                 *S = reinterpret_cast<const float2 *>(self);
+    float2 *Y = reinterpret_cast<float2 *>(out);
+    if (R == 4) return launch_hop_staged<4>(g, par, L, X, Y, S, a, n, s);
+    if (R == 2) return launch_hop_staged<2>(g, par, L, X, Y, S, a, n, s);
+    return launch_hop_staged<1>(g, par, L, X, Y, S, a, n, s);
+  }
+}
+
 template <typename T>
 rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
                   int n, int nbatch, long bstride, cudaStream_t s) {
@@ -253,7 +453,8 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
   int R = tune_get(TUNE_HOP_RHS_PER_THREAD);
   // measured at 24^4 (FP32): 2 per thread best for n >= 12, 1 otherwise; FP64 is ALU bound
   if (R <= 0 || n % R != 0) R = (sizeof(T) == 4 && n >= 12 && n % 2 == 0) ? 2 : 1;
-  if (R == 4)
+  if (try_hop_staged<T>(g, par, links, in, out, self, a, n, nbatch, R, s)) {
+  } else if (R == 4)
     launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   else if (R == 2)
     launch_hop<T, 2>(g, par, links, in, out, self, a, n, nbatch, bstride, s);

@@ -26,10 +26,13 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                    help="rhmc_tune_set(KEY, VALUE) before the solves (repeatable)")
     a = ap.parse_args(argv)
 
     import torch
 
+    from . import _lib
     from . import synthetic as syn
     from .api import RhmcContext
     from .remez import rational_approx
@@ -37,6 +40,9 @@ def main(argv=None):
     ra = rational_approx(-1.0 / 64, 4e-4, 64.0, 16) if a.shifts == 16 else None
     if ra is None:
         ra = rational_approx(-1.0 / (4 * a.n), 2e-3, 64.0, a.shifts)
+    for kv in a.tune:
+        k, v = kv.split("=")
+        _lib.check(_lib.load().rhmc_tune_set(int(k), int(v)), "rhmc_tune_set")
     ctx = RhmcContext(a.dims, a.mass)
     ctx.set_gauge(torch.from_numpy(syn.random_links(a.dims, 0.5, syn.seed_gauge(3))).cuda())
     B = torch.from_numpy(syn.gaussian_pseudofermions(a.dims, a.n, syn.seed_phi(3))).cuda()

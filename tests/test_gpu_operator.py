@@ -58,6 +58,39 @@ def test_apply_mdagm(dims, n, bc, sigma):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,n", [((4, 4, 4, 4), 2), ((6, 4, 4, 2), 6), ((8, 4, 4, 6), 10), ((4, 6, 4, 4), 14),
+                                    ((8, 8, 8, 8), 16)])
+def test_hop_fp32_kernel_variants(dims, n):
+    """Both FP32 hop kernels (cp.async-staged tiles, register staged) and every
+    right-hand-sides-per-thread choice give the same operator (1e-6)."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    mass, sigma = 0.05, 0.21
+    U = syn.random_links(dims, 0.5, 1102)
+    X = syn.gaussian_pseudofermions(dims, n, 2102)
+    ctx = make_ctx(dims, mass, U)
+    refs = [oracle.hop(dims, U, X, par) for par in (0, 1)]
+    refA = oracle.apply_A(dims, mass, U, X, sigma=sigma)
+    try:
+        for mode in (1, 2):
+            for R in (1, 2, 4):
+                if n % R:
+                    continue
+                lib.rhmc_tune_set(8, mode)
+                lib.rhmc_tune_set(0, R)
+                for par in (0, 1):
+                    got = ctx.hop(to_gpu(X), par, "fp32").cpu().numpy()
+                    assert colrel(got, refs[par]) <= 1e-6, (mode, R, par)
+                got = ctx.apply_mdagm_mrhs(to_gpu(X), sigma, "fp32").cpu().numpy()
+                assert colrel(got, refA) <= 1e-6, (mode, R)
+    finally:
+        lib.rhmc_tune_set(8, 0)
+        lib.rhmc_tune_set(0, 0)
+    ctx.close()
+
+
 def test_apply_full_size_sampled():
     """24^4, n = 16 (the force workload's launch configuration): sampled even sites against the oracle."""
     need_gpu()
