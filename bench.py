@@ -46,6 +46,13 @@ WORKLOAD = {
     "precision": "mixed",
     "index": 3,
 }
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of a kernel, from one capture on a smaller case of the same kernel
+# (profiles/); the per-launch traffic of the bench's launches is scaled from it
+# by the units processed.  A kernel changed since its capture has no entry.
+TRAFFIC_RATIO = {
+    "update_fp32": (0.961, "profiles/k_update_all_16x16x16x32_n16.md (16^3x32, 15 shifts; scaled by bytes moved)"),
+}
 METRIC = "time/force eval at 24^4,n_pf=16 (1e-8 res): block+mixed vs FP64 CG; Dslash GB/s"
 L2_BYTES = 129 * 1024 * 1024
 
@@ -324,6 +331,10 @@ def run_gpu(args):
     hbm_kernels = [r["kernel"] for r in kt if r["GB/s"]]
     dominant = hbm_kernels[0] if hbm_kernels else None
     roof = roofline.entry(stats, dominant) if dominant else None
+    if roof and dominant in TRAFFIC_RATIO:
+        ratio, src = TRAFFIC_RATIO[dominant]
+        roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
+        roof["traffic_source"] = src
     roof_dslash = roofline.entry(stats, "hop_fp32") if "hop_fp32" in stats else None
 
     # ---- comparison: per-vector FP64 multishift CG + force (Fig. 9 analogue)
