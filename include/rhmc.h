@@ -254,6 +254,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 or as eager launches (2)
  *   RHMC_TUNE_HOP_STAGED          FP32 hop with tiles staged in shared memory by cp.async
  *                                 for even n (1) or the register-staged kernel (0, 2: built-in)
+ *   RHMC_TUNE_REFINE_LANES        defect corrections of different shifts run concurrently on
+ *                                 up to this many streams, one host thread each (0: 4, the
+ *                                 most; 1: in turn on the caller's stream)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -264,7 +267,8 @@ enum {
   RHMC_TUNE_NATIVE_FP64_RESIDUALS = 5,
   RHMC_TUNE_UPDATE_TENSOR = 6,
   RHMC_TUNE_GRAPHS = 7,
-  RHMC_TUNE_HOP_STAGED = 8
+  RHMC_TUNE_HOP_STAGED = 8,
+  RHMC_TUNE_REFINE_LANES = 9
 };
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -99,6 +100,7 @@ constexpr int kCheckEvery = 6;        // iterations between host checks (a multi
                                       // k % 2 and k % 3 slot pattern of a captured chunk fixed)
 constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
+constexpr int kRefineLanes = 4;       // concurrent defect corrections (built-in and most)
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
 struct Arena {
@@ -117,6 +119,36 @@ struct Arena {
 
 using namespace rhmc;
 
+// Host-side state of one stream of solver work: its capture stream, pinned
+// readback buffer and captured graphs.  The caller's solve runs on the main
+// lane; the defect corrections of different shifts run on lanes of their own,
+// one host thread each.
+struct SolverLane {
+  cudaStream_t s = nullptr;    // the lane's stream (null for the main lane: the caller's)
+  cudaStream_t cap = nullptr;  // graph capture (the caller's stream may be the legacy default stream)
+  double *h_pin = nullptr;     // pinned host staging (readbacks)
+  size_t h_pin_bytes = 0;
+  struct GraphEntry {
+    std::vector<double> key;   // what the captured chunk depends on
+    cudaGraphExec_t exec;
+    long long launches;        // kernels in one replay
+    unsigned long long last_use;
+  };
+  std::vector<GraphEntry> graphs;  // captured SBCGrQ chunks (CUDA graphs)
+  unsigned long long graph_clock = 0;
+  void release() {
+    for (auto &e : graphs) cudaGraphExecDestroy(e.exec);
+    graphs.clear();
+    if (h_pin) cudaFreeHost(h_pin);
+    h_pin = nullptr;
+    h_pin_bytes = 0;
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
+    if (s) cudaStreamDestroy(s);
+    s = nullptr;
+  }
+};
+
 struct rhmc_ctx {
   int device = 0;
   Geom g{};
@@ -128,21 +160,12 @@ struct rhmc_ctx {
   bool have_gauge = false;
   void *pool = nullptr;
   size_t pool_bytes = 0;
-  double *h_pin = nullptr;  // pinned host staging (readbacks)
-  size_t h_pin_bytes = 0;
   cudaStream_t side = nullptr;     // shifted coefficient steps and updates
   cudaStream_t own = nullptr;      // the context's stream in batched solves
-  cudaStream_t cap = nullptr;      // graph capture (the caller's stream may be the legacy default stream)
   cudaEvent_t ev_base[3] = {};     // base update of iteration k done (slot k % 3)
   cudaEvent_t ev_side[3] = {};     // shifted updates of iteration k done
-  struct GraphEntry {
-    std::vector<double> key;        // what the captured chunk depends on
-    cudaGraphExec_t exec;
-    long long launches;             // kernels in one replay
-    unsigned long long last_use;
-  };
-  std::vector<GraphEntry> graphs;   // captured SBCGrQ chunks (CUDA graphs)
-  unsigned long long graph_clock = 0;
+  SolverLane main;                 // the caller's stream
+  std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
 };
 
 namespace rhmc {
@@ -173,12 +196,18 @@ static rhmc_status_t ensure_pool(rhmc_ctx *c, size_t bytes) {
   return RHMC_OK;
 }
 
+// The lane the calling host thread works on (the main lane unless a
+// defect-correction worker set its own).
+static thread_local SolverLane *t_lane = nullptr;
+static SolverLane &lane(rhmc_ctx *c) { return t_lane ? *t_lane : c->main; }
+
 static rhmc_status_t ensure_pinned(rhmc_ctx *c, size_t bytes) {
-  if (c->h_pin_bytes >= bytes) return RHMC_OK;
-  if (c->h_pin) cudaFreeHost(c->h_pin);
-  c->h_pin = nullptr;
-  RHMC_CUDA_TRY(cudaMallocHost(&c->h_pin, bytes));
-  c->h_pin_bytes = bytes;
+  SolverLane &L = lane(c);
+  if (L.h_pin_bytes >= bytes) return RHMC_OK;
+  if (L.h_pin) cudaFreeHost(L.h_pin);
+  L.h_pin = nullptr;
+  RHMC_CUDA_TRY(cudaMallocHost(&L.h_pin, bytes));
+  L.h_pin_bytes = bytes;
   return RHMC_OK;
 }
 
@@ -265,18 +294,24 @@ struct RefineBufs {
   double2 *Bref, *E;
 };
 
+// Lanes of the defect-correction phase: workspace is laid out for the
+// built-in count, the tuning key can only lower it.
+static int refine_lanes(int ns) { return std::max(1, std::min(kRefineLanes, ns)); }
+
 static size_t solve_bytes(const Geom &g, int n, int ns, bool mixed, bool own_X) {
   Arena a(nullptr);
   if (own_X) a.take<double2>((size_t)ns * g.Vh * 3 * n);
   SolveBufs b;
   layout_solve(a, g, n, ns, mixed, b);
-  // refinement: Bref, E, plus a single-shift solve
+  // refinement: per lane Bref, E, plus a single-shift solve
   Arena r(nullptr);
   if (own_X) r.take<double2>((size_t)ns * g.Vh * 3 * n);
-  r.take<double2>((size_t)g.Vh * 3 * n);
-  r.take<double2>((size_t)g.Vh * 3 * n);
-  SolveBufs b1;
-  layout_solve(r, g, n, 1, mixed, b1);
+  for (int l = 0; l < refine_lanes(ns); ++l) {
+    r.take<double2>((size_t)g.Vh * 3 * n);
+    r.take<double2>((size_t)g.Vh * 3 * n);
+    SolveBufs b1;
+    layout_solve(r, g, n, 1, mixed, b1);
+  }
   return std::max(a.off, r.off) + 256;
 }
 
@@ -297,11 +332,11 @@ static rhmc_status_t colnorms(rhmc_ctx *c, const double2 *A, int n, double *out,
   const long rows = c->g.Vh * 3;
   RHMC_TRY(colnorm2<double>(A, rows, n, npart, kParts, s));
   RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts * kMaxN));
-  RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, npart, sizeof(double) * kParts * n, cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaMemcpyAsync(lane(c).h_pin, npart, sizeof(double) * kParts * n, cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaStreamSynchronize(s));
   for (int j = 0; j < n; ++j) {
     double t = 0;
-    for (int p = 0; p < kParts; ++p) t += c->h_pin[p * n + j];
+    for (int p = 0; p < kParts; ++p) t += lane(c).h_pin[p * n + j];
     out[j] = t;
   }
   return RHMC_OK;
@@ -316,7 +351,7 @@ struct StateView {
 
 static rhmc_status_t read_state(rhmc_ctx *c, SolverState *st, StateView &v, cudaStream_t s) {
   RHMC_TRY(ensure_pinned(c, sizeof(StateView) + 64));
-  StateView *h = reinterpret_cast<StateView *>(c->h_pin);
+  StateView *h = reinterpret_cast<StateView *>(lane(c).h_pin);
   RHMC_CUDA_TRY(cudaMemcpyAsync(h->res, st->res, sizeof(v.res), cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaMemcpyAsync(h->active, st->active, sizeof(v.active), cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaMemcpyAsync(&h->breakdown, &st->breakdown, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -416,23 +451,24 @@ static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X
                              (double)ns, sigma0, target, (double)freeze, (double)sizeof(T), (double)len,
                              (double)(chunk_start % kCheckEvery)};
   for (int t = 0; t < TUNE_NKEYS; ++t) key.push_back((double)tune_get(t));
-  rhmc_ctx::GraphEntry *hit = nullptr;
-  for (auto &e : c->graphs)
+  SolverLane &L = lane(c);
+  SolverLane::GraphEntry *hit = nullptr;
+  for (auto &e : L.graphs)
     if (e.key == key) hit = &e;
   if (!hit) {
-    if ((int)c->graphs.size() >= kGraphCacheMax) {  // evict the least recently used
-      auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
-                                  [](const rhmc_ctx::GraphEntry &a, const rhmc_ctx::GraphEntry &b2) {
+    if ((int)L.graphs.size() >= kGraphCacheMax) {  // evict the least recently used
+      auto lru = std::min_element(L.graphs.begin(), L.graphs.end(),
+                                  [](const SolverLane::GraphEntry &a, const SolverLane::GraphEntry &b2) {
                                     return a.last_use < b2.last_use;
                                   });
       cudaGraphExecDestroy(lru->exec);
-      c->graphs.erase(lru);
+      L.graphs.erase(lru);
     }
     const long long before = rhmc_kernel_launches();
-    RHMC_CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    const rhmc_status_t rc = run_chunk<T>(c, b, X, n, ns, sigma0, chunk_start, len, target, freeze, c->cap);
+    RHMC_CUDA_TRY(cudaStreamBeginCapture(L.cap, cudaStreamCaptureModeThreadLocal));
+    const rhmc_status_t rc = run_chunk<T>(c, b, X, n, ns, sigma0, chunk_start, len, target, freeze, L.cap);
     cudaGraph_t g = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
+    const cudaError_t ec = cudaStreamEndCapture(L.cap, &g);
     const long long captured = rhmc_kernel_launches() - before;
     g_launches.fetch_sub(captured);  // recorded, not run: counted at every replay instead
     if (rc != RHMC_OK) {
@@ -450,10 +486,10 @@ static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X
       set_error("graph instantiation failed: %s", cudaGetErrorString(ei));
       return RHMC_ERR_CUDA;
     }
-    c->graphs.push_back({key, exec, captured, 0});
-    hit = &c->graphs.back();
+    L.graphs.push_back({key, exec, captured, 0});
+    hit = &L.graphs.back();
   }
-  hit->last_use = ++c->graph_clock;
+  hit->last_use = ++L.graph_clock;
   RHMC_CUDA_TRY(cudaGraphLaunch(hit->exec, s));
   g_launches.fetch_add(hit->launches);
   return RHMC_OK;
@@ -625,32 +661,45 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   if (rc != RHMC_OK && rc != RHMC_ERR_NOT_CONVERGED) return rc;
   const rhmc_status_t rc1 = rc;
 
-  // phase 2: FP64 true residual per shift, defect correction where needed
+  // phase 2: FP64 true residual per shift, defect correction where needed.
+  // The shifts are independent here: they are spread over up to `nl` lanes
+  // (stream + host thread each, hardest shifts first), so that the
+  // latency-bound parts of one correction overlap the bulk kernels of another.
+  const int tl = tune_get(TUNE_REFINE_LANES);
+  const int nl = prof_on() ? 1 : std::min(refine_lanes(ns), tl > 0 ? tl : kRefineLanes);
+  struct LaneWork {
+    RefineBufs rb;
+    SolveBufs b1;
+    int refinements = 0, refine_iters = 0, dirac = 0;
+    double worst = 0.0, worst1 = 0.0;
+    rhmc_status_t rc = RHMC_OK;
+    std::string err;
+  };
+  std::vector<LaneWork> work(nl);
   Arena ra(ws);
-  RefineBufs rb;
-  rb.Bref = ra.take<double2>(len);
-  rb.E = ra.take<double2>(len);
-  SolveBufs b1;
-  layout_solve(ra, c->g, n, 1, prm.mixed, b1);
-  // b1 overlaps b: phase-1 buffers are dead from here on.  The residual
-  // evaluation uses b1's FP64 helpers.
+  for (auto &w : work) {
+    w.rb.Bref = ra.take<double2>(len);
+    w.rb.E = ra.take<double2>(len);
+    layout_solve(ra, c->g, n, 1, prm.mixed, w.b1);
+  }
+  // work[*] overlaps b: phase-1 buffers are dead from here on (colnorms syncs s)
   double bn[kMaxN];
-  RHMC_TRY(colnorms(c, B, n, bn, b1.npart, s));
+  RHMC_TRY(colnorms(c, B, n, bn, work[0].b1.npart, s));
   for (int j = 0; j < n; ++j) bn[j] = std::sqrt(bn[j]);
-  int refinements = 0, refine_iters = 0;
-  double worst = 0.0, worst1 = 0.0;
   std::vector<double> resid((size_t)ns * n, 0.0);
-  for (int q = 0; q < ns; ++q) {
+
+  auto refine_shift = [&](int q, LaneWork &w, cudaStream_t ls) -> rhmc_status_t {
     double2 *Xq = X + q * len;
+    SolveBufs &b1 = w.b1;
     for (int round = 0;; ++round) {
       if (prm.mixed)
-        RHMC_TRY(apply_A_accurate(c, Xq, b1.AP64, b1.T64, b1.R64, n, shifts[q], s));
+        RHMC_TRY(apply_A_accurate(c, Xq, b1.AP64, b1.T64, b1.R64, n, shifts[q], ls));
       else
-        RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], s));
-      RHMC_TRY(sub(B, b1.AP64, rb.Bref, len, s));
-      st.dirac++;
+        RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], ls));
+      RHMC_TRY(sub(B, b1.AP64, w.rb.Bref, len, ls));
+      w.dirac++;
       double rn[kMaxN];
-      RHMC_TRY(colnorms(c, rb.Bref, n, rn, b1.npart, s));
+      RHMC_TRY(colnorms(c, w.rb.Bref, n, rn, b1.npart, ls));
       double mx = 0.0, ratio_min = 1e300;
       for (int j = 0; j < n; ++j) {
         const double r = std::sqrt(rn[j]) / bn[j];
@@ -658,10 +707,10 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
         mx = std::max(mx, r);
         if (r > 0) ratio_min = std::min(ratio_min, prm.tol / r);
       }
-      if (round == 0) worst1 = std::max(worst1, mx);
+      if (round == 0) w.worst1 = std::max(w.worst1, mx);
       if (mx <= prm.tol || prm.fixed_iters > 0 || round >= kMaxRefine) {
-        worst = std::max(worst, mx);
-        break;
+        w.worst = std::max(w.worst, mx);
+        return RHMC_OK;
       }
       // defect correction: (A + sigma_q) E = R, X_q += E
       SolveParams pr = prm;
@@ -669,14 +718,61 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
       pr.fixed_iters = 0;
       pr.verify_at_convergence = false;  // the FP64 true residual is checked right after
       SolveStats st1;
-      rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s)
-                                   : solve_phase1<double>(c, rb.Bref, n, 1, &shifts[q], rb.E, pr, b1, st1, s);
+      rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls)
+                                   : solve_phase1<double>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls);
       if (rr != RHMC_OK && rr != RHMC_ERR_NOT_CONVERGED && rr != RHMC_ERR_BREAKDOWN) return rr;
-      refinements++;
-      refine_iters += st1.iters;
-      st.dirac += st1.dirac;
-      RHMC_TRY(add_inplace(Xq, rb.E, len, s));  // X_q += E
+      w.refinements++;
+      w.refine_iters += st1.iters;
+      w.dirac += st1.dirac;
+      RHMC_TRY(add_inplace(Xq, w.rb.E, len, ls));  // X_q += E
     }
+  };
+
+  if (nl == 1) {
+    for (int q = 0; q < ns && work[0].rc == RHMC_OK; ++q) work[0].rc = refine_shift(q, work[0], s);
+    if (work[0].rc != RHMC_OK) return work[0].rc;
+  } else {
+    while ((int)c->lanes.size() < nl) {
+      auto l = std::make_unique<SolverLane>();
+      if (cudaStreamCreateWithFlags(&l->s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&l->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        l->release();
+        set_error("cannot create a refinement stream");
+        return RHMC_ERR_CUDA;
+      }
+      c->lanes.push_back(std::move(l));
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int l = 0; l < nl; ++l)
+      pool.emplace_back([&, l] {
+        DeviceGuard dg(c->device);
+        SolverLane *L = c->lanes[l].get();
+        t_lane = L;
+        LaneWork &w = work[l];
+        for (int q = next++; q < ns && w.rc == RHMC_OK; q = next++) w.rc = refine_shift(q, w, L->s);
+        if (cudaStreamSynchronize(L->s) != cudaSuccess && w.rc == RHMC_OK) {
+          set_error("refinement stream: %s", cudaGetErrorString(cudaGetLastError()));
+          w.rc = RHMC_ERR_CUDA;
+        }
+        if (w.rc != RHMC_OK) w.err = rhmc_last_error();
+        t_lane = nullptr;
+      });
+    for (auto &t : pool) t.join();
+    for (auto &w : work)
+      if (w.rc != RHMC_OK) {
+        set_error("%s", w.err.c_str());
+        return w.rc;
+      }
+  }
+  int refinements = 0, refine_iters = 0;
+  double worst = 0.0, worst1 = 0.0;
+  for (auto &w : work) {
+    refinements += w.refinements;
+    refine_iters += w.refine_iters;
+    st.dirac += w.dirac;
+    worst = std::max(worst, w.worst);
+    worst1 = std::max(worst1, w.worst1);
   }
   timer.mark();
   if (info) {
@@ -816,7 +912,7 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
   }
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&c->main.cap, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("rhmc_create: cannot create the side stream");
     rhmc_destroy(c);
     return RHMC_ERR_CUDA;
@@ -841,17 +937,19 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
     if (c->ldf[p]) cudaFree(c->ldf[p]);
   }
   if (c->side) cudaStreamSynchronize(c->side);
-  for (auto &e : c->graphs) cudaGraphExecDestroy(e.exec);
-  c->graphs.clear();
+  for (auto &l : c->lanes) {
+    if (l->s) cudaStreamSynchronize(l->s);
+    l->release();
+  }
+  c->lanes.clear();
+  c->main.release();
   if (c->pool) cudaFree(c->pool);
-  if (c->h_pin) cudaFreeHost(c->h_pin);
   for (int q = 0; q < 3; ++q) {
     if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);
   }
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own) cudaStreamDestroy(c->own);
-  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return RHMC_OK;
 }
@@ -1144,7 +1242,7 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n,
         RHMC_TRY(scg_update2(sc, r, p, ns, len1, s));
         dirac++;
       }
-      ScgScalars *h = reinterpret_cast<ScgScalars *>(c->h_pin);
+      ScgScalars *h = reinterpret_cast<ScgScalars *>(lane(c).h_pin);
       RHMC_CUDA_TRY(cudaMemcpyAsync(h, sc, sizeof(ScgScalars), cudaMemcpyDeviceToHost, s));
       RHMC_CUDA_TRY(cudaStreamSynchronize(s));
       if (h->breakdown) {
@@ -1230,15 +1328,15 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
     RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts));
     double S = 0.0;
     RHMC_TRY(redot((const double2 *)Phi, (const double2 *)Phi, len, parts, kParts, s));
-    RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
+    RHMC_CUDA_TRY(cudaMemcpyAsync(lane(c).h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
     RHMC_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int q = 0; q < kParts; ++q) S += alpha0 * c->h_pin[q];
+    for (int q = 0; q < kParts; ++q) S += alpha0 * lane(c).h_pin[q];
     for (int q = 0; q < ns; ++q) {
       RHMC_TRY(redot((const double2 *)Phi, X + (size_t)q * len, len, parts, kParts, s));
-      RHMC_CUDA_TRY(cudaMemcpyAsync(c->h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
+      RHMC_CUDA_TRY(cudaMemcpyAsync(lane(c).h_pin, parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
       RHMC_CUDA_TRY(cudaStreamSynchronize(s));
       double t = 0.0;
-      for (int k = 0; k < kParts; ++k) t += c->h_pin[k];
+      for (int k = 0; k < kParts; ++k) t += lane(c).h_pin[k];
       S += alpha[q] * t;
     }
     *S_out = S;

@@ -108,6 +108,7 @@ enum TuneKey {
   TUNE_UPDATE_TENSOR,         // mixed, n = 16: shifted updates on tcgen05 (1) or CUDA cores (2); 0: built-in
   TUNE_GRAPHS,                // solver chunks as captured CUDA graphs (0/1) or eager launches (2)
   TUNE_HOP_STAGED,            // FP32 hop with cp.async-staged tiles: built-in (0), always (1), never (2)
+  TUNE_REFINE_LANES,          // concurrent per-shift defect corrections (0: built-in 4)
   TUNE_NKEYS
 };
 int tune_get(int key);

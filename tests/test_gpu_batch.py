@@ -87,3 +87,30 @@ def test_autotune_keeps_results(tmp_path):
     finally:
         autotune.reset()
     ctx.close()
+
+
+def test_refinement_lanes_agree():
+    """Defect corrections spread over concurrent lanes give bit-identical solutions to
+    corrections run in turn (each shift's correction is the same deterministic kernels)."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n = (8, 8, 8, 8), 0.05, 4
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1530)
+    B = syn.gaussian_pseudofermions(dims, n, 2530)
+    ctx = make_ctx(dims, mass, U)
+    out = {}
+    try:
+        for lanes in (1, 4):
+            lib.rhmc_tune_set(9, lanes)
+            X, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-10, precision="mixed")
+            assert info.refinements > 0 and info.true_rel_resid_max <= 1e-10
+            out[lanes] = X.cpu().numpy()
+    finally:
+        lib.rhmc_tune_set(9, 0)
+    assert np.array_equal(out[1], out[4])
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
+    _check_solution(dims, mass, U, B, ra.beta, out[4], 1e-10, Xo)
+    ctx.close()
