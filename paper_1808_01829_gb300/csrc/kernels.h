@@ -23,6 +23,7 @@ struct SolverState {
   double2 alpha_s[kMaxS][kMaxN * kMaxN];
   double sigma[kMaxS];        // shifts, ascending
   double d0[kMaxN];           // ||B e_j||
+  double inv_d0[kMaxN];       // 1 / ||B e_j||
   double res[kMaxS][kMaxN];   // recursive relative residual per shift and column (s = 0: base)
   int active[kMaxS];          // shift still being updated
   int upd[kMaxS];             // shift updated in the current iteration

@@ -1,7 +1,13 @@
 // n x n coefficient algebra of SBCGrQ (Algorithm 1), FP64, on the device.
 //
 // A CTA of 256 threads works on n x n complex matrices (n <= 16) held in
-// shared memory, thread t owning element (t / n, t % n).  The state of the
+// shared memory.  On this GPU an FP64 warp instruction occupies its SM
+// sub-partition's FP64 unit for about 64 cycles however many lanes are active,
+// and a dependent FP64 operation waits as long; the base-system kernels
+// therefore hand each step's work items to the fewest warps (items are packed
+// by index, not owned by element), exploit every triangular and Hermitian
+// structure, and keep one barrier per factorisation step.  The shifted step
+// (one CTA per shift) keeps the simpler element-per-thread form.  The state of the
 // recursion lives in a SolverState in device memory; quantities of iteration
 // k are written to slot k % 3 and those of k-1 read from slot (k-1) % 3, so a
 // launch never overwrites what a launch still running on the other stream reads.
@@ -241,33 +247,191 @@ __device__ void store_coef(const Cta &c, C<T> *dst, const double2 *M, double sca
   if (c.own) dst[c.t] = mk<T>((T)(scale * M[c.t].x), (T)(scale * M[c.t].y));
 }
 
+// 1/x for x > 0: FP32 estimate refined by two Newton-Raphson steps
+// r <- r + r (1 - x r) in FP64 (the estimate's 2^-23 error squares twice);
+// the exponent is split off only when x is outside the FP32 range.
+__device__ __forceinline__ double frcp_fast(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return frcp(x);
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+// 1/sqrt(x) for x > 0: Newton-Raphson y <- y (3 - x y^2) / 2 from an FP32 estimate.
+__device__ __forceinline__ double frsqrt(double x) {
+  int e = 0;
+  double m = x;
+  if (!(x > 1e-30 && x < 1e30)) {
+    m = frexp(x, &e);
+    if (e & 1) {
+      m *= 2.0;
+      e -= 1;
+    }
+  }
+  const double h = 0.5 * m;
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return e ? ldexp(y, -e / 2) : y;
+}
+
+// Index of row a of a packed lower triangle (a (a+1)/2 <= e < (a+1)(a+2)/2).
+__device__ __forceinline__ int tri_row(int e) {
+  int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= e) ++a;
+  while (a * (a + 1) / 2 > e) --a;
+  return a;
+}
+
+// LDL^dagger factorisation of the Hermitian positive definite A (n x n, full
+// storage in shared memory, its Hermitian part is used).  On return the
+// strictly lower part of A holds L (unit lower), A[k][k].x holds D_k,
+// Li = L^-1 (unit lower, full storage) and rd[k] = 1 / D_k.  Step k updates
+// the trailing lower triangle and rows k+1.. of L^-1 as one list of work
+// items; the item on the next diagonal entry also forms the next pivot's
+// reciprocal, so each step needs one barrier.  Returns false (in all threads)
+// if a pivot is not positive and finite.
+__device__ bool ldl(int n, double2 *A, double2 *Li, double *rd, int *flag) {
+  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  double2 h = make_double2(0, 0);
+  if (t < nn) {
+    const int i = t / n, j = t - (t / n) * n;
+    const double2 a = A[t], b = A[j * n + i];
+    h = (i == j) ? make_double2(a.x, 0.0) : make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  __syncthreads();
+  if (t < nn) {
+    const int i = t / n, j = t - (t / n) * n;
+    A[t] = h;
+    Li[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (t == 0) {
+    const double d = h.x;
+    *flag = !(d > 0.0) || !isfinite(d);
+    rd[0] = frcp_fast(d > 0.0 ? d : 1.0);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    if (*flag) return false;
+    const double r = rd[k];
+    const int m = n - 1 - k;
+    const int ntri = m * (m + 1) / 2, nli = m * (k + 1);
+    for (int e = t; e < ntri + nli; e += nt) {
+      if (e < ntri) {
+        // A[i][j] -= A[i][k] conj(A[j][k]) / D_k,  i >= j > k
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
+        const int i = k + 1 + a, j = k + 1 + b;
+        const double2 aik = A[i * n + k], ajk = A[j * n + k];
+        double2 v = A[i * n + j];
+        const double px = fma(aik.x, ajk.x, aik.y * ajk.y), py = fma(aik.y, ajk.x, -aik.x * ajk.y);
+        v.x = fma(-px, r, v.x);
+        v.y = fma(-py, r, v.y);
+        A[i * n + j] = v;
+        if (i == k + 1 && j == k + 1) {
+          *flag = !(v.x > 0.0) || !isfinite(v.x);
+          rd[k + 1] = frcp_fast(v.x > 0.0 ? v.x : 1.0);
+        }
+      } else {
+        // Li[i][j] -= L[i][k] Li[k][j],  i > k >= j,  L[i][k] = A[i][k] / D_k
+        const int e2 = e - ntri;
+        const int a = e2 / (k + 1), j = e2 - a * (k + 1);
+        const int i = k + 1 + a;
+        const double2 aik = A[i * n + k], lkj = Li[k * n + j];
+        const double lx = aik.x * r, ly = aik.y * r;
+        double2 v = Li[i * n + j];
+        v.x -= fma(lx, lkj.x, -ly * lkj.y);
+        v.y -= fma(lx, lkj.y, ly * lkj.x);
+        Li[i * n + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (*flag) return false;
+  for (int e = t; e < nn; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (i > j) A[e] = cscale(A[e], rd[j]);
+  }
+  __syncthreads();
+  return true;
+}
+
+// From an LDL^dagger factorisation: the thin-QR factor R = D^1/2 L^dagger
+// (upper, positive real diagonal) and R^-1 = L^-dagger D^-1/2 (upper), full
+// storage with zero lower parts.  sd, rsd: scratch for D^1/2 and D^-1/2.
+__device__ void qr_factors(int n, const double2 *A, const double2 *Li, double2 *R, double2 *Ri, double *sd,
+                           double *rsd) {
+  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  if (t < n) {
+    const double d = A[t * n + t].x;
+    const double y = frsqrt(d);
+    rsd[t] = y;
+    sd[t] = d * y;
+  }
+  __syncthreads();
+  for (int e = t; e < nn; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    double2 r = make_double2(0, 0), ri = make_double2(0, 0);
+    if (i == j) {
+      r = make_double2(sd[i], 0.0);
+      ri = make_double2(rsd[i], 0.0);
+    } else if (i < j) {
+      const double2 l = A[j * n + i], li = Li[j * n + i];  // conj(L[j][i]), conj(Li[j][i])
+      r = make_double2(sd[i] * l.x, -sd[i] * l.y);
+      ri = make_double2(li.x * rsd[j], -li.y * rsd[j]);
+    }
+    R[e] = r;
+    Ri[e] = ri;
+  }
+  __syncthreads();
+}
+
+// Column norms of an upper-triangular n x n matrix M: 16 lanes per column,
+// shuffle reduction; writes out[j] = ||M e_j|| * scale[j] (scale may be null).
+__device__ void colnorms_upper(int n, const double2 *M, double *out, const double *scale, double *norm_out) {
+  const int t = threadIdx.x;
+  const int j = t >> 4, i = t & 15;
+  double v = 0.0;
+  if (j < n && i <= j) {
+    const double2 z = M[i * n + j];
+    v = fma(z.x, z.x, z.y * z.y);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+  if (j < n && i == 0) {
+    const double nv = v > 0.0 ? v * frsqrt(v) : 0.0;
+    if (norm_out) norm_out[j] = nv;
+    if (out) out[j] = scale ? nv * scale[j] : nv;
+  }
+}
+
 #define NN 256  // shared matrix capacity (n <= 16)
 
 }  // namespace
 
 // ------------------------------------------------------------ kernels
 
-// line 2: {Q_0, delta_0} = qr(B) via Cholesky of the Gram B^dagger B; init state.
+// line 2: {Q_0, delta_0} = qr(B): delta_0 = R of the Cholesky QR of B^dagger B;
+// writes delta_0^-1 (for Q_0 = B delta_0^-1) and initialises the state.
 template <typename T>
 __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int nparts, int n, int nshift,
                                                  SolverState *st, C<T> *rinv_out) {
-  __shared__ double2 G[NN], Ri[NN];
+  __shared__ double2 A[NN], Li[NN], R[NN], Ri[NN];
+  __shared__ double rd[kMaxN], sd[kMaxN], rsd[kMaxN], nrm[kMaxN];
   __shared__ int flag;
   Cta c(n);
-  reduce_partials(c, G, partial, nparts);
-  if (!cholesky(c, G, &flag)) {
+  reduce_partials(c, A, partial, nparts);
+  if (!ldl(n, A, Li, rd, &flag)) {
     if (c.t == 0) st->breakdown = 1;
     return;
   }
-  // delta_0 = L^dagger
-  if (c.own) Ri[c.t] = conjz(G[c.j * n + c.i]);
-  __syncthreads();
-  copy(c, G, Ri);  // G = delta_0 (upper)
-  inv_upper(c, Ri, G);
+  qr_factors(n, A, Li, R, Ri, sd, rsd);
   store_coef<T>(c, rinv_out, Ri);
+  colnorms_upper(n, R, nullptr, nullptr, nrm);
+  __syncthreads();
   if (c.own) {
-    st->delta[0][c.t] = G[c.t];
-    st->rho[0][c.t] = G[c.t];
+    st->delta[0][c.t] = R[c.t];
+    st->rho[0][c.t] = R[c.t];
     const double2 e = make_double2(c.i == c.j ? 1.0 : 0.0, 0.0);
     st->alpha[0][c.t] = e;
     st->G1[0][c.t] = e;
@@ -276,7 +440,10 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
       st->alpha_s[s][c.t] = e;
     }
   }
-  if (c.t < n) st->d0[c.t] = colnorm(c, G, c.t);
+  if (c.t < n) {
+    st->d0[c.t] = nrm[c.t];
+    st->inv_d0[c.t] = frcp_fast(nrm[c.t] > 0.0 ? nrm[c.t] : 1.0);
+  }
   if (c.t < nshift) {
     st->active[c.t] = 1;
     st->upd[c.t] = 0;
@@ -288,69 +455,112 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
   }
 }
 
-// line 4: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P; also -alpha_k for line 5.
+// line 4: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P (Hermitian part),
+// from Gram1 = L D L^dagger: alpha = L^-dagger D^-1 L^-1, only i <= j formed;
+// also -alpha for line 5.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k,
                                                    C<T> *mw_out) {
-  __shared__ double2 G[NN], L[NN], Li[NN], A[NN];
+  __shared__ double2 A[NN], Li[NN], S[NN];
+  __shared__ double rd[kMaxN];
   __shared__ int flag;
   Cta c(n);
   const int cur = k % kSlots;
-  reduce_partials(c, G, partial, nparts);
+  const int t = c.t, nt = blockDim.x, nn = n * n;
+  reduce_partials(c, A, partial, nparts);
+  // Gram1_k (Hermitian part) for the shifted step
   if (c.own) {
-    // Hermitian part (the Gram of P with an Hermitian operator)
-    const double2 a = G[c.t], b = G[c.j * n + c.i];
-    L[c.t] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    const double2 a = A[t], b = A[c.j * n + c.i];
+    st->G1[cur][t] = (c.i == c.j) ? make_double2(a.x, 0.0) : make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
   }
-  __syncthreads();
-  copy(c, G, L);
-  if (c.own) st->G1[cur][c.t] = G[c.t];
-  if (!cholesky(c, L, &flag)) {
-    if (c.t == 0) st->breakdown = 2;
+  if (!ldl(n, A, Li, rd, &flag)) {
+    if (t == 0) st->breakdown = 2;
     return;
   }
-  // L^-1 via the upper inverse of L^dagger:  (L^dagger)^-1 = (L^-1)^dagger
-  if (c.own) A[c.t] = conjz(L[c.j * n + c.i]);
+  // S[k][j] = Li[k][j] / D_k
+  for (int e = t; e < nn; e += nt) {
+    const int kk = e / n;
+    S[e] = cscale(Li[e], rd[kk]);
+  }
   __syncthreads();
-  inv_upper(c, Li, A);     // Li = (L^dagger)^-1 = L^-dagger
-  mm(c, A, Li, Li, false, true);  // alpha = L^-dagger L^-1
-  if (c.own) st->alpha[cur][c.t] = A[c.t];
-  store_coef<T>(c, mw_out, A, -1.0);
+  // alpha[i][j] = sum_{q >= j} conj(Li[q][i]) S[q][j], i <= j (column-major packing)
+  for (int e = t; e < n * (n + 1) / 2; e += nt) {
+    const int j = tri_row(e), i = e - j * (j + 1) / 2;
+    double ax = 0.0, ay = 0.0;
+    for (int q = j; q < n; ++q) {
+      const double2 l = Li[q * n + i], sv = S[q * n + j];
+      ax = fma(l.x, sv.x, fma(l.y, sv.y, ax));
+      ay = fma(l.x, sv.y, fma(-l.y, sv.x, ay));
+    }
+    const double2 v = make_double2(ax, ay), vc = make_double2(ax, -ay);
+    st->alpha[cur][i * n + j] = v;
+    mw_out[i * n + j] = mk<T>((T)(-ax), (T)(-ay));
+    if (i != j) {
+      st->alpha[cur][j * n + i] = vc;
+      mw_out[j * n + i] = mk<T>((T)(-ax), (T)(ay));
+    }
+  }
 }
 
-// lines 5-8: rho_k from the Cholesky of W^dagger W; base coefficients; delta_k.
+// lines 5-8: rho_k = R factor of the Cholesky QR of W^dagger W; base coefficients
+// rho_k^-1 (Q_k = W rho_k^-1), M1 = alpha_k delta_{k-1} (line 6), M2 = rho_k^dagger
+// (line 7); delta_k = rho_k delta_{k-1} (line 8) and the base column residuals.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k,
                                                  C<T> *coef) {
-  __shared__ double2 G[NN], R[NN], Ri[NN], M[NN];
+  __shared__ double2 A[NN], Li[NN], R[NN], Ri[NN];
+  __shared__ double rd[kMaxN], sd[kMaxN], rsd[kMaxN];
   __shared__ int flag;
   Cta c(n);
   const int cur = k % kSlots, prev = (k - 1) % kSlots;
-  const int nn = n * n;
-  reduce_partials(c, G, partial, nparts);
-  if (!cholesky(c, G, &flag)) {
-    if (c.t == 0) st->breakdown = 3;
+  const int t = c.t, nt = blockDim.x, nn = n * n;
+  reduce_partials(c, A, partial, nparts);
+  if (!ldl(n, A, Li, rd, &flag)) {
+    if (t == 0) st->breakdown = 3;
     return;
   }
-  if (c.own) R[c.t] = conjz(G[c.j * n + c.i]);  // rho_k = L^dagger (upper)
-  __syncthreads();
-  inv_upper(c, Ri, R);
+  qr_factors(n, A, Li, R, Ri, sd, rsd);
+  // A, Li are free now: alpha_k and delta_{k-1} into shared memory
+  double2 *Al = A, *Dp = Li;
+  if (c.own) {
+    Al[t] = st->alpha[cur][t];
+    Dp[t] = st->delta[prev][t];
+    st->rho[cur][t] = R[t];
+  }
   store_coef<T>(c, coef, Ri);
-  if (c.own) st->rho[cur][c.t] = R[c.t];
-  // M1 = alpha_k delta_{k-1}   (line 6)
-  mm(c, M, st->alpha[cur], st->delta[prev]);
-  store_coef<T>(c, coef + nn, M);
-  // M2 = rho_k^dagger          (line 7)
-  if (c.own) M[c.t] = conjz(R[c.j * n + c.i]);
+  if (c.own) coef[2 * nn + t] = mk<T>((T)R[c.j * n + c.i].x, (T)(-R[c.j * n + c.i].y));  // rho^dagger
   __syncthreads();
-  store_coef<T>(c, coef + 2 * nn, M);
-  // delta_k = rho_k delta_{k-1} (line 8)
-  mm(c, M, R, st->delta[prev]);
-  if (c.own) st->delta[cur][c.t] = M[c.t];
-  if (c.t < n) st->res[0][c.t] = colnorm(c, M, c.t) / st->d0[c.t];
-  if (c.t == 0) st->upd[0] = 1;
+  // M1[i][j] = sum_{q <= j} alpha[i][q] delta[q][j] (n^2 items, column-major so a
+  // warp's items share their length); delta_k[i][j] = sum_{i <= q <= j} rho[i][q] delta[q][j]
+  double2 *Dk = Ri;  // Ri was stored above
+  for (int e = t; e < nn + n * (n + 1) / 2; e += nt) {
+    if (e < nn) {
+      const int j = e / n, i = e - (e / n) * n;
+      double ax = 0.0, ay = 0.0;
+      for (int q = 0; q <= j; ++q) {
+        const double2 a = Al[i * n + q], d = Dp[q * n + j];
+        ax = fma(a.x, d.x, fma(-a.y, d.y, ax));
+        ay = fma(a.x, d.y, fma(a.y, d.x, ay));
+      }
+      coef[nn + i * n + j] = mk<T>((T)ax, (T)ay);
+    } else {
+      const int e2 = e - nn;
+      const int j = tri_row(e2), i = e2 - j * (j + 1) / 2;
+      double ax = 0.0, ay = 0.0;
+      for (int q = i; q <= j; ++q) {
+        const double2 a = R[i * n + q], d = Dp[q * n + j];
+        ax = fma(a.x, d.x, fma(-a.y, d.y, ax));
+        ay = fma(a.x, d.y, fma(a.y, d.x, ay));
+      }
+      Dk[i * n + j] = make_double2(ax, ay);
+      if (i != j) Dk[j * n + i] = make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  if (c.own) st->delta[cur][t] = Dk[t];
+  colnorms_upper(n, Dk, st->res[0], st->inv_d0, nullptr);
+  if (t == 0) st->upd[0] = 1;
 }
-
 // lines 9-12 for shift s = blockIdx.x + 1.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef,
@@ -404,7 +614,7 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   mm(c, B, A1, A2);
   __shared__ double colres[kMaxN];
   if (c.t < n) {
-    const double r = colnorm(c, B, c.t) * frcp(st->d0[c.t]);
+    const double r = colnorm(c, B, c.t) * st->inv_d0[c.t];
     colres[c.t] = r;
     st->res[s][c.t] = r;
   }
@@ -417,26 +627,25 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   }
 }
 
-// Reliable update: delta_k <- R factor of the true residual (Gram partials of
-// R^dagger R); writes (delta')^-1 for Q = R (delta')^-1.
+// Reliable update: delta_k <- R factor of the true residual (Gram of R^dagger R);
+// writes (delta')^-1 for Q = R (delta')^-1.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st,
                                                       int k, C<T> *rinv_out) {
-  __shared__ double2 G[NN], R[NN], Ri[NN];
+  __shared__ double2 A[NN], Li[NN], R[NN], Ri[NN];
+  __shared__ double rd[kMaxN], sd[kMaxN], rsd[kMaxN];
   __shared__ int flag;
   Cta c(n);
   const int cur = k % kSlots;
-  reduce_partials(c, G, partial, nparts);
-  if (!cholesky(c, G, &flag)) {
+  reduce_partials(c, A, partial, nparts);
+  if (!ldl(n, A, Li, rd, &flag)) {
     if (c.t == 0) st->breakdown = 5;
     return;
   }
-  if (c.own) R[c.t] = conjz(G[c.j * n + c.i]);
-  __syncthreads();
-  inv_upper(c, Ri, R);
+  qr_factors(n, A, Li, R, Ri, sd, rsd);
   if (c.own) st->delta[cur][c.t] = R[c.t];
   store_coef<T>(c, rinv_out, Ri);
-  if (c.t < n) st->res[0][c.t] = colnorm(c, R, c.t) / st->d0[c.t];
+  colnorms_upper(n, R, st->res[0], st->inv_d0, nullptr);
 }
 
 // ------------------------------------------------------------ launchers
