@@ -50,9 +50,7 @@ WORKLOAD = {
 # byte of a kernel, from one capture on a smaller case of the same kernel
 # (profiles/); the per-launch traffic of the bench's launches is scaled from it
 # by the units processed.  A kernel changed since its capture has no entry.
-TRAFFIC_RATIO = {
-    "update_fp32": (0.961, "profiles/k_update_all_16x16x16x32_n16.md (16^3x32, 15 shifts; scaled by bytes moved)"),
-}
+TRAFFIC_RATIO = {}
 METRIC = "time/force eval at 24^4,n_pf=16 (1e-8 res): block+mixed vs FP64 CG; Dslash GB/s"
 L2_BYTES = 129 * 1024 * 1024
 

@@ -231,7 +231,7 @@ long long rhmc_kernel_launches(void);
 enum {
   RHMC_PROF_HOP_FP32 = 0, RHMC_PROF_HOP_FP64, RHMC_PROF_GRAM_FP32, RHMC_PROF_GRAM_FP64, RHMC_PROF_BLOCK_AXPY,
   RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER,
-  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_UPDATE_TC, RHMC_PROF_NCAT
+  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_UPDATE_TC, RHMC_PROF_UPDATE_SHIFTS32, RHMC_PROF_NCAT
 };
 rhmc_status_t rhmc_profile_enable(int on);
 
@@ -248,8 +248,11 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_CHECK_EVERY         iterations between host convergence checks (0: 6)
  *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
  *                                 true residuals with native FP64 instead of RHMC_DF64
- *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, n_rhs = 16: shifted updates on the
- *                                 tensor cores (tcgen05, 3xTF32) = 1, CUDA cores = 2 (built-in)
+ *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, shifted updates: on the tensor cores
+ *                                 (tcgen05, 3xTF32, n_rhs = 16 only) = 1; CUDA-core kernel with
+ *                                 lane-owned row slices = 2; CUDA-core kernel with column-owner
+ *                                 lanes and cp.async-staged row tiles = 0 (built-in) or 3..9
+ *                                 (tile shape variants, see the autotuner)
  *   RHMC_TUNE_GRAPHS              solver iterations in captured CUDA graphs (0, 1: built-in)
  *                                 or as eager launches (2)
  *   RHMC_TUNE_HOP_STAGED          FP32 hop with tiles staged in shared memory by cp.async

@@ -372,6 +372,11 @@ template <typename T> static bool use_tensor_update(int n) {
   // the update saves.
   return tune_get(TUNE_UPDATE_TENSOR) == 1;
 }
+// Column-owner shifted updates (FP32): the built-in choice; RHMC_TUNE_UPDATE_TENSOR = 2
+// selects the lane-slice kernel.
+template <typename T> static bool use_column_update() {
+  return sizeof(T) == 4 && tune_get(TUNE_UPDATE_TENSOR) != 2;
+}
 
 // One SBCGrQ iteration (device work only).  The base recursion runs on the
 // caller's stream s; with more than one shift the shifted coefficient step and
@@ -410,6 +415,9 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
     if (use_tensor_update<T>(n))
       RHMC_TRY(update_shifts_tc((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                 b.st->upd, 1, ns, rows, len, b.btiles, &b.st->device_timeout, ss));
+    else if (use_column_update<T>())
+      RHMC_TRY(update_shifts_cols((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
+                                  b.st->upd, 1, ns, rows, n, len, ss));
     else
       RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
                                  ss));

@@ -21,6 +21,29 @@
 
 namespace rhmc {
 
+// Instantiate a launch for the runtime width n = 1..16.
+#define RHMC_DISPATCH_N(n, MACRO) \
+  switch (n) {                    \
+    case 1: MACRO(1); break;      \
+    case 2: MACRO(2); break;      \
+    case 3: MACRO(3); break;      \
+    case 4: MACRO(4); break;      \
+    case 5: MACRO(5); break;      \
+    case 6: MACRO(6); break;      \
+    case 7: MACRO(7); break;      \
+    case 8: MACRO(8); break;      \
+    case 9: MACRO(9); break;      \
+    case 10: MACRO(10); break;    \
+    case 11: MACRO(11); break;    \
+    case 12: MACRO(12); break;    \
+    case 13: MACRO(13); break;    \
+    case 14: MACRO(14); break;    \
+    case 15: MACRO(15); break;    \
+    case 16: MACRO(16); break;    \
+    default: return RHMC_ERR_INVALID_ARG; \
+  }
+
+
 // ------------------------------------------------------------ Gram
 // G = A^dagger B (n x n), summed over all rows, in two launches:
 //   k_gram      every warp streams its own 16-row tiles of A and B through a
@@ -37,11 +60,11 @@ constexpr int kGramWarps = 8;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <typename T, int N, bool SAME>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
@@ -390,6 +413,326 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
   }
 }
 
+// ------------------------------------------------------------ shifted updates, column owners
+// FP32 shifted updates of Algorithm 1 lines 11-12 for every live shift:
+//   X^(s) += P^(s) M1^(s),   P^(s) = Q + P^(s) M2^(s)
+// (M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger).  Each warp owns tiles of
+// R = 8 rows; lane l < 2N owns output column j = l mod N of M1 (l < N) or M2
+// (N <= l < 2N) and keeps that coefficient column in registers for the shift.
+// The tile's Q rows and, three shifts deep, its P^(s) and X^(s) rows are
+// staged in the warp's shared memory by cp.async.  The P^(s) tile is then
+// rewritten with every element duplicated, (re, re, im, im), so that one
+// broadcast 16-byte load feeds a complex multiply-add done as two packed
+// FP32x2 FMAs: (acc.re, acc.im) += (p.re, p.re) (c.re, c.im) + (p.im, p.im) (-c.im, c.re).
+__device__ __forceinline__ void cpa16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+template <int NW> __device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NW) : "memory");
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+// d = a * b + c on two FP32 lanes at once (one rounding per lane)
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// X^(s) rows r, r+1 (lanes of M1) or P^(s) rows (lanes of M2) of a column-owner tile
+__device__ __forceinline__ void col_store(int mat, int j, int r, int N, long off, const float2 *xt, const float2 *qs,
+                                          float2 *X, float2 *P, float2 s0, float2 s1) {
+  if (mat == 0) {
+    const float2 x0 = xt[r * N + j], x1 = xt[(r + 1) * N + j];
+    X[off + r * N + j] = make_float2(x0.x + s0.x, x0.y + s0.y);
+    X[off + (r + 1) * N + j] = make_float2(x1.x + s1.x, x1.y + s1.y);
+  } else {
+    const float2 q0 = qs[r * N + j], q1 = qs[(r + 1) * N + j];
+    P[off + r * N + j] = make_float2(q0.x + s0.x, q0.y + s0.y);
+    P[off + (r + 1) * N + j] = make_float2(q1.x + s1.x, q1.y + s1.y);
+  }
+}
+
+// tiles of R x N complex per warp: Q, NB x (P, X) raw, the duplicated P tile (packed variant)
+template <int NB, bool PACKED> constexpr int col_tiles_per_warp() { return 1 + 2 * NB + (PACKED ? 2 : 0); }
+
+// R rows per warp tile, W warps per CTA, NB shifts in flight per warp;
+// PACKED: duplicated P tile and FP32x2 FMAs
+template <int N, int R, int W, int NB, bool PACKED>
+__global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict__ Q, float2 *__restrict__ P,
+                                                        float2 *__restrict__ X, const float2 *__restrict__ coef,
+                                                        const int *__restrict__ upd, int s_begin, int s_end, long rows,
+                                                        long fstride) {
+  constexpr int TILE = R * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int live[kMaxS];
+  __shared__ int nlive;
+  const int nsh = s_end - s_begin;
+  float2 *cs = reinterpret_cast<float2 *>(smem_raw);  // [nsh][2][N * N]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 *qs = cs + (size_t)nsh * 2 * N * N + (size_t)warp * col_tiles_per_warp<NB, PACKED>() * TILE;
+  auto ptile = [&](int b) { return qs + TILE * (1 + 2 * b); };
+  auto xtile = [&](int b) { return qs + TILE * (2 + 2 * b); };
+  float4 *dup = reinterpret_cast<float4 *>(qs + TILE * (1 + 2 * NB));  // [R][N] duplicated P tile
+  for (int k = threadIdx.x; k < nsh * 2 * N * N; k += blockDim.x) cs[k] = coef[(1 + 2 * s_begin) * N * N + k];
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int q = s_begin; q < s_end; ++q)
+      if (upd[q]) live[m++] = q;
+    nlive = m;
+  }
+  __syncthreads();
+  const int nl = nlive;
+  if (nl == 0) return;
+  const int mat = lane / N, j = lane - (lane / N) * N;
+  const bool act = lane < 2 * N;
+  const long ntiles = (rows + R - 1) / R;
+  for (long tile = (long)blockIdx.x * W + warp; tile < ntiles; tile += (long)gridDim.x * W) {
+    const long r0 = tile * R;
+    const int nr = (int)min((long)R, rows - r0);  // rows is a multiple of 8: nr is even
+    const int chunks = nr * N / 2;                 // 16-byte chunks of one tile
+    auto copy_tile = [&](float2 *dst, const float2 *src) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+      const char *s8 = reinterpret_cast<const char *>(src);
+      for (int c = lane; c < chunks; c += 32) cpa16(d + 16u * c, s8 + 16L * c);
+    };
+    copy_tile(qs, Q + r0 * N);
+#pragma unroll
+    for (int b = 0; b < NB - 1; ++b) {
+      if (b < nl) {
+        const long off = live[b] * fstride + r0 * N;
+        copy_tile(ptile(b), P + off);
+        copy_tile(xtile(b), X + off);
+      }
+      cp_async_commit();
+    }
+    for (int i = 0; i < nl; ++i) {
+      const int b = i % NB;
+      const int inext = i + NB - 1;
+      if (inext < nl) {
+        const long off = live[inext] * fstride + r0 * N;
+        copy_tile(ptile(inext % NB), P + off);
+        copy_tile(xtile(inext % NB), X + off);
+      }
+      cp_async_commit();
+      cpa_wait<NB - 1>();  // shift i's tiles (and the Q tile) have landed for this lane
+      __syncwarp();        // ... and for the whole warp
+      if (PACKED) {
+        const float2 *pt = ptile(b);
+        for (int e = lane; e < nr * N; e += 32) {
+          const float2 v = pt[e];
+          dup[e] = make_float4(v.x, v.x, v.y, v.y);
+        }
+      }
+      const int sh = live[i];
+      const float2 *xt = xtile(b);
+      const long off = sh * fstride + r0 * N;
+      if (PACKED) {
+        unsigned long long ca[N], cb[N];
+        if (act) {
+          const float2 *m = cs + ((sh - s_begin) * 2 + mat) * N * N + j;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float2 c = m[k * N];
+            ca[k] = pack2(c.x, c.y);
+            cb[k] = pack2(-c.y, c.x);
+          }
+        }
+        __syncwarp();  // duplicated tile complete
+        if (act) {
+#pragma unroll 1
+          for (int r = 0; r < nr; r += 2) {
+            unsigned long long a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
+            const float4 *d0 = dup + r * N, *d1 = d0 + N;
+#pragma unroll
+            for (int k = 0; k < N; k += 2) {
+              const float4 u0 = d0[k], v0 = d1[k];
+              a0 = fma2(pack2(u0.x, u0.y), ca[k], a0);
+              a0 = fma2(pack2(u0.z, u0.w), cb[k], a0);
+              b0 = fma2(pack2(v0.x, v0.y), ca[k], b0);
+              b0 = fma2(pack2(v0.z, v0.w), cb[k], b0);
+              if (k + 1 < N) {
+                const float4 u1 = d0[k + 1], v1 = d1[k + 1];
+                a1 = fma2(pack2(u1.x, u1.y), ca[k + 1], a1);
+                a1 = fma2(pack2(u1.z, u1.w), cb[k + 1], a1);
+                b1 = fma2(pack2(v1.x, v1.y), ca[k + 1], b1);
+                b1 = fma2(pack2(v1.z, v1.w), cb[k + 1], b1);
+              }
+            }
+            const float2 s0 = unpack2(add2(a0, a1)), s1 = unpack2(add2(b0, b1));
+            col_store(mat, j, r, N, off, xt, qs, X, P, s0, s1);
+          }
+        }
+      } else {
+        float2 cf[N];
+        if (act) {
+          const float2 *m = cs + ((sh - s_begin) * 2 + mat) * N * N + j;
+#pragma unroll
+          for (int k = 0; k < N; ++k) cf[k] = m[k * N];
+        }
+        const float2 *pt = ptile(b);
+        if (act) {
+#pragma unroll 1
+          for (int r = 0; r < nr; r += 2) {
+            float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, bx0 = 0.f, by0 = 0.f, bx1 = 0.f, by1 = 0.f;
+            const float2 *p0 = pt + r * N, *p1 = p0 + N;
+            if constexpr (N % 2 == 0) {
+#pragma unroll
+              for (int k = 0; k < N; k += 2) {
+                const float4 u = *reinterpret_cast<const float4 *>(p0 + k);
+                const float4 v = *reinterpret_cast<const float4 *>(p1 + k);
+                const float2 c0 = cf[k], c1 = cf[k + 1];
+                ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+                ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+                ax1 = fmaf(u.z, c1.x, ax1); ax1 = fmaf(-u.w, c1.y, ax1);
+                ay1 = fmaf(u.z, c1.y, ay1); ay1 = fmaf(u.w, c1.x, ay1);
+                bx0 = fmaf(v.x, c0.x, bx0); bx0 = fmaf(-v.y, c0.y, bx0);
+                by0 = fmaf(v.x, c0.y, by0); by0 = fmaf(v.y, c0.x, by0);
+                bx1 = fmaf(v.z, c1.x, bx1); bx1 = fmaf(-v.w, c1.y, bx1);
+                by1 = fmaf(v.z, c1.y, by1); by1 = fmaf(v.w, c1.x, by1);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < N; ++k) {
+                const float2 u = p0[k], v = p1[k], c0 = cf[k];
+                ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+                ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+                bx0 = fmaf(v.x, c0.x, bx0); bx0 = fmaf(-v.y, c0.y, bx0);
+                by0 = fmaf(v.x, c0.y, by0); by0 = fmaf(v.y, c0.x, by0);
+              }
+            }
+            col_store(mat, j, r, N, off, xt, qs, X, P, make_float2(ax0 + ax1, ay0 + ay1),
+                      make_float2(bx0 + bx1, by0 + by1));
+          }
+        }
+      }
+      __syncwarp();  // buffer b and the duplicated tile are refilled at the next step
+    }
+    cpa_wait<0>();
+    __syncwarp();  // the Q tile and buffers are reused by the next tile
+  }
+}
+
+template <int N, int R, int W, int NB, bool PACKED>
+static size_t col_smem(int nsh) {
+  return (size_t)nsh * 2 * N * N * sizeof(float2) + (size_t)W * col_tiles_per_warp<NB, PACKED>() * R * N * sizeof(float2);
+}
+
+template <int N, int R, int W, int NB, bool PACKED>
+static rhmc_status_t launch_update_cols(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
+                                        int s_begin, int s_end, long rows, long fstride, cudaStream_t s) {
+  const int threads = W * 32;
+  const size_t smem = col_smem<N, R, W, NB, PACKED>(s_end - s_begin);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_update_cols<N, R, W, NB, PACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  if (smem > 220 * 1024) return RHMC_ERR_INVALID_ARG;
+  const long ntiles = (rows + R - 1) / R;
+  long grid = (ntiles + W - 1) / W;
+  grid = std::min(grid, (long)resident_ctas(k_update_cols<N, R, W, NB, PACKED>, threads, smem));
+  k_update_cols<N, R, W, NB, PACKED><<<(unsigned)grid, threads, smem, s>>>(Q, P, X, coef, upd, s_begin, s_end, rows,
+                                                                             fstride);
+  return RHMC_OK;
+}
+
+// Variants of the column-owner kernel (RHMC_TUNE_UPDATE_TENSOR), rows per warp
+// tile / warps per CTA / shifts in flight: 3 = 16/8/3; 4 = 8/16/3; 5 = 8/16/3
+// with the duplicated tile and FP32x2 FMAs; 6 = 4/32/3; 7 = 8/24/2; 8 = 8/28/2
+// (built-in, 0); 9 = 4/32/2.  Measured at 24^4, n = 16, 15 live shifts, one
+// launch alone: 1116, 830, 1042, 792, 720, 694, 789 us for 3 ... 9.
+#define RHMC_COL_VARIANTS(X_)                   \
+  switch (col_variant()) {                      \
+    case 3: X_(16, 8, 3, false); break;         \
+    case 4: X_(8, 16, 3, false); break;         \
+    case 5: X_(8, 16, 3, true); break;          \
+    case 6: X_(4, 32, 3, false); break;         \
+    case 7: X_(8, 24, 2, false); break;         \
+    case 9: X_(4, 32, 2, false); break;         \
+    default: X_(8, 28, 2, false); break;        \
+  }
+static int col_variant() { return tune_get(TUNE_UPDATE_TENSOR); }
+template <int N> static size_t col_tiles_bytes() {
+  size_t b = 0;
+#define L_(R_, W_, NB_, P_) b = col_smem<N, R_, W_, NB_, P_>(0)
+  RHMC_COL_VARIANTS(L_)
+#undef L_
+  return b;
+}
+template <int N>
+static rhmc_status_t launch_update_cols_variant(const float2 *Q, float2 *P, float2 *X, const float2 *coef,
+                                                const int *upd, int s_begin, int s_end, long rows, long fstride,
+                                                cudaStream_t s) {
+  rhmc_status_t rc = RHMC_OK;
+#define L_(R_, W_, NB_, P_) \
+  rc = launch_update_cols<N, R_, W_, NB_, P_>(Q, P, X, coef, upd, s_begin, s_end, rows, fstride, s)
+  RHMC_COL_VARIANTS(L_)
+#undef L_
+  return rc;
+}
+
+static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2 *X, const float2 *coef,
+                                              const int *upd, int s_begin, int s_end, long rows, int n, long fstride,
+                                              cudaStream_t s);
+
+// Shifted updates (no base) for the FP32 mixed path with the column-owner kernel,
+// in as many launches as the shared-memory coefficient store needs.
+rhmc_status_t update_shifts_cols(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
+                                 int s_begin, int s_end, long rows, int n, long fstride, cudaStream_t s) {
+  if (rows % 8) return RHMC_ERR_INVALID_ARG;
+  // shifts per launch that fit the shared-memory coefficient store
+  size_t tiles = 0;
+#define L_TB(NN) tiles = col_tiles_bytes<NN>()
+  RHMC_DISPATCH_N(n, L_TB)
+#undef L_TB
+  const int per_launch = (int)((220 * 1024 - tiles) / (2 * n * n * sizeof(float2)));
+  if (per_launch < 1) return RHMC_ERR_INVALID_ARG;
+  for (int b = s_begin; b < s_end; b += per_launch) {
+    const int e = std::min(s_end, b + per_launch);
+    const rhmc_status_t rc = update_shifts_cols_range(Q, P, X, coef, upd, b, e, rows, n, fstride, s);
+    if (rc != RHMC_OK) return rc;
+  }
+  return RHMC_OK;
+}
+
+static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2 *X, const float2 *coef,
+                                              const int *upd, int s_begin, int s_end, long rows, int n, long fstride,
+                                              cudaStream_t s) {
+  int nupd = s_end - s_begin;
+  if (prof_on()) {  // profiling only: count the shifts this launch updates (host sync)
+    int h[kMaxS];
+    cudaStreamSynchronize(s);
+    cudaMemcpy(h, upd, sizeof(int) * s_end, cudaMemcpyDeviceToHost);
+    nupd = 0;
+    for (int q = s_begin; q < s_end; ++q) nupd += h[q] != 0;
+  }
+  prof_begin(PROF_UPDATE_SHIFTS32, s);
+  rhmc_status_t rc = RHMC_OK;
+#define L_COLS(NN) rc = launch_update_cols_variant<NN>(Q, P, X, coef, upd, s_begin, s_end, rows, fstride, s)
+  RHMC_DISPATCH_N(n, L_COLS)
+#undef L_COLS
+  prof_end(s, (double)rows * n * (sizeof(float2) + nupd * 4.0 * sizeof(float2)));
+  if (rc != RHMC_OK) {
+    set_error("update_shifts_cols: %d shifts at n = %d do not fit", s_end - s_begin, n);
+    return rc;
+  }
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
 // ------------------------------------------------------------ flush
 __global__ void k_flush(double2 *__restrict__ X64, float2 *__restrict__ X32, long len) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -466,26 +809,6 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
 }
 
 // ------------------------------------------------------------ launchers
-#define RHMC_DISPATCH_N(n, MACRO) \
-  switch (n) {                    \
-    case 1: MACRO(1); break;      \
-    case 2: MACRO(2); break;      \
-    case 3: MACRO(3); break;      \
-    case 4: MACRO(4); break;      \
-    case 5: MACRO(5); break;      \
-    case 6: MACRO(6); break;      \
-    case 7: MACRO(7); break;      \
-    case 8: MACRO(8); break;      \
-    case 9: MACRO(9); break;      \
-    case 10: MACRO(10); break;    \
-    case 11: MACRO(11); break;    \
-    case 12: MACRO(12); break;    \
-    case 13: MACRO(13); break;    \
-    case 14: MACRO(14); break;    \
-    case 15: MACRO(15); break;    \
-    case 16: MACRO(16); break;    \
-    default: return RHMC_ERR_INVALID_ARG; \
-  }
 
 template <typename T, int N>
 static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {

@@ -93,7 +93,7 @@ void count_launch();
 // algorithmic bytes.  No-ops when profiling is off.
 enum ProfCat {
   PROF_HOP32 = 0, PROF_HOP64, PROF_GRAM32, PROF_GRAM64, PROF_AXPY, PROF_UPDATE32, PROF_UPDATE64,
-  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_UPDATE_TC, PROF_NCAT
+  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_UPDATE_TC, PROF_UPDATE_SHIFTS32, PROF_NCAT
 };
 bool prof_on();
 

@@ -224,3 +224,29 @@ def test_tensor_core_shift_update_matches_oracle(dims):
     finally:
         lib.rhmc_tune_set(6, 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 2, 5, 9])
+def test_shifted_update_kernels_many_shifts(variant):
+    """Both FP32 shifted-update kernels (column owners, built-in; lane slices) on a
+    mixed solve with 40 shifts at n = 16 (the column-owner kernel splits them over
+    launches) match the oracle."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n = (4, 4, 4, 8), 0.05, 16
+    shifts = list(np.geomspace(2e-3, 60.0, 40))
+    U = syn.random_links(dims, 0.5, 1240)
+    B = syn.gaussian_pseudofermions(dims, n, 2240)
+    ctx = make_ctx(dims, mass, U)
+    try:
+        lib.rhmc_tune_set(6, variant)
+        Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-9, precision="mixed")
+    finally:
+        lib.rhmc_tune_set(6, 0)
+    assert info.true_rel_resid_max <= 1e-9
+    Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, shifts, tol=1e-13, max_iter=20000)
+    assert rc == 0
+    _check_solution(dims, mass, U, B, shifts, Xg.cpu().numpy(), 1e-9, Xo)
+    ctx.close()
