@@ -245,6 +245,118 @@ static void launch_hop(const Geom &g, int par, const C<T> *links, const C<T> *in
   }
 }
 
+// ------------------------------------------------------------ hop, all directions in flight
+// FP32, one right-hand side per thread, n threads per site, TS = 128 / n sites
+// per CTA.  The CTA's link records go to shared memory by cp.async while the
+// neighbour table is built; then every thread issues the loads of all 8
+// neighbours' 3 colour components at once (24 independent 8-byte loads, about
+// 200 bytes per thread in flight) before it multiplies anything, so the
+// latency of the gathered reads is paid once per site instead of once per
+// direction.
+// Coordinates of the site with parity `par` and parity rank h, 32-bit
+// arithmetic (V/2 < 2^31): x = 2 xh + (parity of y + z + t xor par).
+__device__ __forceinline__ void site_coords32(const Geom &g, int par, int h, int &x0, int &x1, int &x2, int &x3) {
+  const int r = h / g.Lxh;
+  const int xh = h - r * g.Lxh;
+  const int r2 = r / g.L[1];
+  x1 = r - r2 * g.L[1];
+  x3 = r2 / g.L[2];
+  x2 = r2 - x3 * g.L[2];
+  x0 = 2 * xh + (((x1 + x2 + x3) & 1) ^ par);
+}
+
+template <int N, bool SELF>
+__global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *__restrict__ links,
+                                                const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                const float2 *__restrict__ self, float a) {
+  constexpr int TILE = (128 / N) < 32 ? (128 / N) : 32;  // sites per CTA (static shared memory <= 20 KB)
+  __shared__ __align__(16) float2 sl[TILE * 72];
+  __shared__ int snb[TILE * 8];
+  const int tid = threadIdx.x;
+  const int h0 = blockIdx.x * TILE;
+  const int nsites = min(TILE, (int)g.Vh - h0);
+  {
+    const unsigned base = (unsigned)__cvta_generic_to_shared(sl);
+    const char *src = reinterpret_cast<const char *>(links + (long)h0 * 72);
+    for (int c = tid; c < nsites * 36; c += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * c), "l"(src + 16L * c) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int k = tid; k < nsites * 8; k += blockDim.x) {
+    const int site = k >> 3, d = k & 7;
+    int y0, y1, y2, y3;
+    site_coords32(g, par, h0 + site, y0, y1, y2, y3);
+    const int mu = d & 3;
+    const bool fwd = d < 4;
+    if (mu == 0) y0 = fwd ? (y0 + 1 == g.L[0] ? 0 : y0 + 1) : (y0 == 0 ? g.L[0] - 1 : y0 - 1);
+    else if (mu == 1) y1 = fwd ? (y1 + 1 == g.L[1] ? 0 : y1 + 1) : (y1 == 0 ? g.L[1] - 1 : y1 - 1);
+    else if (mu == 2) y2 = fwd ? (y2 + 1 == g.L[2] ? 0 : y2 + 1) : (y2 == 0 ? g.L[2] - 1 : y2 - 1);
+    else y3 = fwd ? (y3 + 1 == g.L[3] ? 0 : y3 + 1) : (y3 == 0 ? g.L[3] - 1 : y3 - 1);
+    const int lex = y0 + g.L[0] * (y1 + g.L[1] * (y2 + g.L[2] * y3));
+    snb[k] = (lex >> 1) * 3 * N;
+  }
+  __syncthreads();
+  const int ls = tid / N, j = tid - (tid / N) * N;
+  const bool live = ls < nsites;
+  float2 v[8][3];
+  if (live) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const float2 *nb = in + snb[ls * 8 + d] + j;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[d][c] = __ldg(nb + c * N);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  if (!live) return;
+  float2 acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = make_float2(0.f, 0.f);
+  const float2 *lk = sl + ls * 72;
+#pragma unroll
+  for (int d = 0; d < 8; ++d)
+#pragma unroll
+    for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+      for (int cb = 0; cb < 3; ++cb) cmac<float>(acc[ca], lk[d * 9 + ca * 3 + cb], v[d][cb]);
+  float2 *op = out + (long)(h0 + ls) * 3 * N + j;
+  if (SELF) {
+    const float2 *sp = self + (long)(h0 + ls) * 3 * N + j;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 sv = __ldg(sp + c * N);
+      acc[c] = make_float2(a * sv.x - acc[c].x, a * sv.y - acc[c].y);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) op[c * N] = acc[c];
+}
+
+template <int N>
+static void launch_hop_pf_n(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
+                            const float2 *self, double a, cudaStream_t s) {
+  constexpr int TILE = (128 / N) < 32 ? (128 / N) : 32;
+  const int threads = ((TILE * N + 31) / 32) * 32;
+  const unsigned grid = (unsigned)((g.Vh + TILE - 1) / TILE);
+  if (self)
+    k_hop_pf<N, true><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
+  else
+    k_hop_pf<N, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
+}
+
+static bool launch_hop_pf(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
+                          const float2 *self, double a, int n, cudaStream_t s) {
+  switch (n) {
+#define L_PF(NN) \
+  case NN: launch_hop_pf_n<NN>(g, par, links, in, out, self, a, s); return true;
+    L_PF(1) L_PF(2) L_PF(3) L_PF(4) L_PF(5) L_PF(6) L_PF(7) L_PF(8)
+    L_PF(9) L_PF(10) L_PF(11) L_PF(12) L_PF(13) L_PF(14) L_PF(15) L_PF(16)
+#undef L_PF
+    default: return false;
+  }
+}
+
 // ------------------------------------------------------------ hop, cp.async staged
 // FP32, one field, even n: persistent CTAs walk over tiles of TS output sites.
 // All threads stage the next tile into shared memory with 16-byte cp.async
@@ -424,6 +536,14 @@ static bool launch_hop_staged(const Geom &g, int par, const float2 *links, const
   return true;
 }
 
+// The all-directions-in-flight kernel: FP32 single fields, the built-in choice
+// (RHMC_TUNE_HOP_STAGED 0 or 3; 2 selects the register-staged kernel).
+template <typename T> static bool use_hop_pf(const void *links, const void *in, int nbatch) {
+  if (sizeof(C<T>) != 8 || nbatch != 1 || ((uintptr_t)links & 15)) return false;
+  const int mode = tune_get(TUNE_HOP_STAGED);
+  return mode == 0 || mode == 3;
+}
+
 // The staged kernel applies to FP32 single fields with 16-byte aligned rows.
 template <typename T>
 static bool try_hop_staged(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out,
@@ -454,6 +574,9 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
   // measured at 24^4 (FP32): 2 per thread best for n >= 12, 1 otherwise; FP64 is ALU bound
   if (R <= 0 || n % R != 0) R = (sizeof(T) == 4 && n >= 12 && n % 2 == 0) ? 2 : 1;
   if (try_hop_staged<T>(g, par, links, in, out, self, a, n, nbatch, R, s)) {
+  } else if (use_hop_pf<T>(links, in, nbatch)) {
+    launch_hop_pf(g, par, reinterpret_cast<const float2 *>(links), reinterpret_cast<const float2 *>(in),
+                  reinterpret_cast<float2 *>(out), reinterpret_cast<const float2 *>(self), a, n, s);
   } else if (R == 4)
     launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   else if (R == 2)

@@ -61,8 +61,9 @@ def test_apply_mdagm(dims, n, bc, sigma):
 @pytest.mark.parametrize("dims,n", [((4, 4, 4, 4), 2), ((6, 4, 4, 2), 6), ((8, 4, 4, 6), 10), ((4, 6, 4, 4), 14),
                                     ((8, 8, 8, 8), 16)])
 def test_hop_fp32_kernel_variants(dims, n):
-    """Both FP32 hop kernels (cp.async-staged tiles, register staged) and every
-    right-hand-sides-per-thread choice give the same operator (1e-6)."""
+    """Every FP32 hop kernel (cp.async-staged tiles, register staged, all
+    directions in flight) and every right-hand-sides-per-thread choice give the
+    same operator (1e-6)."""
     need_gpu()
     from paper_1808_01829_gb300 import _lib
 
@@ -74,7 +75,7 @@ def test_hop_fp32_kernel_variants(dims, n):
     refs = [oracle.hop(dims, U, X, par) for par in (0, 1)]
     refA = oracle.apply_A(dims, mass, U, X, sigma=sigma)
     try:
-        for mode in (1, 2):
+        for mode in (1, 2, 3):
             for R in (1, 2, 4):
                 if n % R:
                     continue
