@@ -1322,15 +1322,27 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
   } else if (info) {
     std::memset(info, 0, sizeof(*info) - sizeof(double *));
   }
-  // Y^(s) = D_oe X^(s), all shifts in one batched hop (links loaded once per tile)
+  // Y^(s) = D_oe X^(s), then the outer-product sum; FP64-accurate in
+  // double-float arithmetic on the FP32 units (native FP64 with
+  // RHMC_TUNE_NATIVE_FP64_RESIDUALS)
   Arena fa(rest);
-  double2 *Y = fa.take<double2>((size_t)ns * len);
+  void *Xf = fa.take<double2>((size_t)ns * len);  // double-float copy of X (float4 = double2 bytes)
+  void *Yf = fa.take<double2>((size_t)ns * len);
   double *alpha_d = fa.take<double>(kMaxS);
   double *parts = fa.take<double>(kParts);
   if (G) {
     RHMC_CUDA_TRY(cudaMemcpyAsync(alpha_d, alpha, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
-    RHMC_TRY(hop<double>(c->g, 1, c->l64[1], X, Y, nullptr, 0.0, n, ns, len, s));
-    RHMC_TRY(force_links(c->g, X, Y, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+    if (tune_get(TUNE_NATIVE_FP64_RESIDUALS)) {
+      double2 *Y = (double2 *)Yf;
+      RHMC_TRY(hop<double>(c->g, 1, c->l64[1], X, Y, nullptr, 0.0, n, ns, len, s));
+      RHMC_TRY(force_links(c->g, X, Y, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+    } else {
+      float4 *Xd = (float4 *)Xf, *Yd = (float4 *)Yf;
+      RHMC_TRY(df_split(X, Xd, (long)ns * len, s));
+      for (int q = 0; q < ns; ++q)
+        RHMC_TRY(hop_df(c->g, 1, c->ldf[1], Xd + (size_t)q * len, Yd + (size_t)q * len, nullptr, 0.0, n, s));
+      RHMC_TRY(force_links_df(c->g, Xd, Yd, n, ns, len, alpha_d, c->bc_t, (double2 *)G, s));
+    }
   }
   if (S_out) {
     RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts));

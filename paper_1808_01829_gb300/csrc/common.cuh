@@ -76,11 +76,18 @@ __device__ __forceinline__ long lex_of(const Geom &g, const int x[4]) {
 
 // Parity rank of the neighbour of x in direction mu (dir = +1 / -1).
 __device__ __forceinline__ long nb_rank(const Geom &g, const int x[4], int mu, int dir) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  int v = y[mu] + dir;
-  if (v < 0) v += g.L[mu];
-  if (v >= g.L[mu]) v -= g.L[mu];
-  y[mu] = v;
+  // the shifted coordinate is selected without dynamic indexing (no local memory)
+  int y[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    int v = x[nu];
+    if (nu == mu) {
+      v += dir;
+      if (v < 0) v += g.L[nu];
+      if (v >= g.L[nu]) v -= g.L[nu];
+    }
+    y[nu] = v;
+  }
   return lex_of(g, y) >> 1;
 }
 

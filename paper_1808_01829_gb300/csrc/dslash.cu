@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace rhmc {
@@ -590,47 +591,9 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
 }
 
 // ------------------------------------------------------------ double-float hop
-// FP64-accurate hop on the FP32 units.  A field or link value d is held as an
-// unevaluated pair of floats d = hi + lo (|lo| <= ulp(hi)/2), one complex as
-// float4 (re_hi, im_hi, re_lo, im_lo).  A real product a*b is formed without
-// rounding error in its leading part with an FMA (TwoProduct, Ogita, Rump and
-// Oishi 2005): p = ah*bh, e = fma(ah, bh, -p) + ah*bl + al*bh; the p are summed
-// with TwoSum (Knuth) and the e in an FP32 error accumulator, which is folded
-// in at the end.  Relative accuracy about 2^-44 per result, against 2^-24 in
-// FP32; FP64 itself runs at 1/74 of the FP32 rate on this GPU.
-namespace {
+// FP64-accurate hop on the FP32 units (double-float arithmetic of df.cuh).
+using namespace df;
 
-struct DF {
-  float h, e;  // running sum and accumulated error
-};
-// The _rn intrinsics keep the compiler from contracting these steps into FMAs,
-// which would break the exactness of TwoSum.
-__device__ __forceinline__ void df_add_prod(DF &acc, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  float err = fmaf(ah, bh, -p);
-  err = fmaf(ah, bl, err);
-  err = fmaf(al, bh, err);
-  const float s = __fadd_rn(acc.h, p);  // TwoSum(acc.h, p)
-  const float bb = __fsub_rn(s, acc.h);
-  const float t = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.h = s;
-  acc.e = __fadd_rn(acc.e, __fadd_rn(t, err));
-}
-// acc += u * v for double-float complex u, v (float4 = re_hi, im_hi, re_lo, im_lo)
-__device__ __forceinline__ void df_cmac(DF &re, DF &im, const float4 &u, const float4 &v) {
-  df_add_prod(re, u.x, u.z, v.x, v.z);
-  df_add_prod(re, -u.y, -u.w, v.y, v.w);
-  df_add_prod(im, u.x, u.z, v.y, v.w);
-  df_add_prod(im, u.y, u.w, v.x, v.z);
-}
-__device__ __forceinline__ float4 df_pack(const DF &re, const DF &im) {
-  // renormalise: (h, e) -> (hi, lo) with FastTwoSum
-  const float rh = __fadd_rn(re.h, re.e), rl = __fsub_rn(re.e, __fsub_rn(rh, re.h));
-  const float ih = __fadd_rn(im.h, im.e), il = __fsub_rn(im.e, __fsub_rn(ih, im.h));
-  return make_float4(rh, ih, rl, il);
-}
-
-}  // namespace
 
 template <bool SELF>
 __global__ void __launch_bounds__(128) k_hop_df(Geom g, int par, const float4 *__restrict__ links,

@@ -12,6 +12,7 @@
 // of every shift (coalesced loads across the lanes), the 9 complex partial
 // sums are then reduced across the group with shuffles.
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace rhmc {
@@ -71,7 +72,9 @@ __global__ void __launch_bounds__(256) k_force(Geom g, const double2 *__restrict
     }
   if (valid && lane == 0) {
     int sum = 0;
-    for (int nu = 0; nu < mu; ++nu) sum += x[nu];
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+      if (nu < mu) sum += x[nu];
     double pre = 2.0 * (par ? -1.0 : 1.0) * ((sum & 1) ? -1.0 : 1.0);
     if (mu == 3 && bc_t == -1 && x[3] == g.L[3] - 1) pre = -pre;
     double2 *o = G + pair * 9;
@@ -106,6 +109,113 @@ rhmc_status_t rational_combine(const double2 *Phi, double alpha0, const double *
   Coeffs c{};
   for (int q = 0; q < ns; ++q) c.a[q] = alpha_host[q];
   k_rational_combine<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(Phi, alpha0, c, X, ns, len, Y);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
+// The same contraction in double-float arithmetic on the FP32 units (FP64
+// accuracy, 2^-44 relative per product): X and Y arrive as double-float fields
+// (float4 per complex), alpha_s is split into a float pair once per shift and
+// folded into the W(x+mu) factor, the products u conj(v') are formed with
+// TwoProduct and summed with TwoSum; G is assembled in FP64.
+namespace {
+// (ah + al) (bh + bl) as a normalised pair
+__device__ __forceinline__ float2 df_mul(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_force_df(Geom g, const float4 *__restrict__ X, const float4 *__restrict__ Y,
+                                                  int n, int ns, long fstride, const double *__restrict__ alpha,
+                                                  int bc_t, double2 *__restrict__ G) {
+  using namespace df;
+  const long pair = (long)blockIdx.x * 16 + threadIdx.x / 16;
+  const int lane = threadIdx.x & 15;
+  const bool valid = pair < 4 * g.V;
+  const long lex = valid ? (pair >> 2) : 0;
+  const int mu = (int)(pair & 3);
+  int x[4];
+  {
+    long r = lex;
+    x[0] = (int)(r % g.L[0]);
+    r /= g.L[0];
+    x[1] = (int)(r % g.L[1]);
+    r /= g.L[1];
+    x[2] = (int)(r % g.L[2]);
+    x[3] = (int)(r / g.L[2]);
+  }
+  const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const long hx = lex >> 1;
+  const long hy = nb_rank(g, x, mu, +1);
+  const float4 *Wx = par ? Y : X;
+  const float4 *Wy = par ? X : Y;
+  DF re[9], im[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) re[q] = im[q] = DF{0.f, 0.f};
+  if (valid) {
+    for (int s = 0; s < ns; ++s) {
+      const double a = alpha[s];
+      const float ah = (float)a, al = (float)(a - (double)ah);
+      const float4 *px = Wx + s * fstride + hx * 3 * n;
+      const float4 *py = Wy + s * fstride + hy * 3 * n;
+      for (int i = lane; i < n; i += 16) {
+        float4 u[3], v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          u[c] = px[c * n + i];
+          const float4 w = py[c * n + i];
+          const float2 vr = df_mul(ah, al, w.x, w.z), vi = df_mul(ah, al, w.y, w.w);
+          v[c] = make_float4(vr.x, vi.x, vr.y, vi.y);
+        }
+#pragma unroll
+        for (int ca = 0; ca < 3; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 3; ++cb) {
+            // u conj(v): re = u.re v.re + u.im v.im, im = u.im v.re - u.re v.im
+            const int q = ca * 3 + cb;
+            df_add_prod(re[q], u[ca].x, u[ca].z, v[cb].x, v[cb].z);
+            df_add_prod(re[q], u[ca].y, u[ca].w, v[cb].y, v[cb].w);
+            df_add_prod(im[q], u[ca].y, u[ca].w, v[cb].x, v[cb].z);
+            df_add_prod(im[q], -u[ca].x, -u[ca].z, v[cb].y, v[cb].w);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      DF ro{__shfl_xor_sync(0xffffffffu, re[q].h, off), __shfl_xor_sync(0xffffffffu, re[q].e, off)};
+      DF io{__shfl_xor_sync(0xffffffffu, im[q].h, off), __shfl_xor_sync(0xffffffffu, im[q].e, off)};
+      re[q] = df_add(re[q], ro);
+      im[q] = df_add(im[q], io);
+    }
+  if (valid && lane == 0) {
+    int sum = 0;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+      if (nu < mu) sum += x[nu];
+    double pre = 2.0 * (par ? -1.0 : 1.0) * ((sum & 1) ? -1.0 : 1.0);
+    if (mu == 3 && bc_t == -1 && x[3] == g.L[3] - 1) pre = -pre;
+    double2 *o = G + pair * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      o[q] = make_double2(pre * ((double)re[q].h + (double)re[q].e), pre * ((double)im[q].h + (double)im[q].e));
+  }
+}
+
+rhmc_status_t force_links_df(const Geom &g, const float4 *X, const float4 *Y, int n, int nshift, long fstride,
+                             const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s) {
+  const long pairs = 4 * g.V;
+  const long grid = (pairs + 15) / 16;
+  prof_begin(PROF_FORCE, s);
+  k_force_df<<<(unsigned)grid, 256, 0, s>>>(g, X, Y, n, nshift, fstride, alpha_dev, bc_t, G);
+  prof_end(s, 2.0 * nshift * g.Vh * 3.0 * n * sizeof(float4) + 4.0 * g.V * 9 * sizeof(double2));
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }

@@ -92,6 +92,9 @@ rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverStat
 // force.cu
 rhmc_status_t rational_combine(const double2 *Phi, double alpha0, const double *alpha_host, const double2 *X, int ns,
                                long len, double2 *Y, cudaStream_t s);
+// the same from double-float fields (float4 per complex)
+rhmc_status_t force_links_df(const Geom &g, const float4 *X, const float4 *Y, int n, int nshift, long fstride,
+                             const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
 rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
                           const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
 

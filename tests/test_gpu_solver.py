@@ -250,3 +250,32 @@ def test_shifted_update_kernels_many_shifts(variant):
     assert rc == 0
     _check_solution(dims, mass, U, B, shifts, Xg.cpu().numpy(), 1e-9, Xo)
     ctx.close()
+
+
+def test_force_double_float_matches_native_fp64():
+    """The double-float force path (built-in) and the native FP64 one
+    (RHMC_TUNE_NATIVE_FP64_RESIDUALS) agree to 1e-12 from the same solutions,
+    and both match the oracle's force of those solutions."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n = (6, 4, 4, 8), 0.05, 5
+    ra = rational_approx(-1.0 / 20, 1e-3, 64.0, 6)
+    U = syn.random_links(dims, 0.5, 1250)
+    Phi = syn.gaussian_pseudofermions(dims, n, 2250)
+    ctx = make_ctx(dims, mass, U)
+    P = to_gpu(Phi)
+    X, _ = ctx.block_multishift_cg(P, ra.beta, 1e-10, precision="fp64")
+    G_df, S_df, _ = ctx.force(P, ra.alpha0, ra.alpha, ra.beta, 1e-10, X=X)
+    try:
+        lib.rhmc_tune_set(5, 1)
+        G_64, S_64, _ = ctx.force(P, ra.alpha0, ra.alpha, ra.beta, 1e-10, X=X)
+    finally:
+        lib.rhmc_tune_set(5, 0)
+    g_df, g_64 = G_df.cpu().numpy(), G_64.cpu().numpy()
+    assert np.linalg.norm(g_df - g_64) <= 1e-12 * np.linalg.norm(g_64)
+    assert S_df == S_64
+    Go = oracle.force(dims, U, X.cpu().numpy(), ra.alpha).reshape(g_64.shape)
+    assert np.linalg.norm(g_df - Go) <= 1e-12 * np.linalg.norm(Go)
+    ctx.close()
