@@ -401,11 +401,21 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   RHMC_TRY(apply_A<T>(c, P, AP, Todd, n, sigma0, s));
   RHMC_TRY(gram<T>(P, AP, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
-  RHMC_TRY(block_axpy<T, T>(AP, Qprev, (const C<T> *)b.mw, W, rows, n, s));
+  const bool cols = use_column_update<T>();
+  if (cols)
+    RHMC_TRY(axpy_cols((const float2 *)AP, (const float2 *)Qprev, (const float2 *)b.mw, (float2 *)W, rows, n, s));
+  else
+    RHMC_TRY(block_axpy<T, T>(AP, Qprev, (const C<T> *)b.mw, W, rows, n, s));
   RHMC_TRY(gram<T>(W, W, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
-  RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 0, 1, 1, rows, n, len, s));
+  if (cols) {
+    RHMC_TRY(axpy_cols((const float2 *)W, nullptr, (const float2 *)b.coef, (float2 *)Qcur, rows, n, s));
+    RHMC_TRY(update_shifts_cols((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
+                                b.st->upd, 0, 1, rows, n, len, s));
+  } else {
+    RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 0, 1, 1, rows, n, len, s));
+  }
   if (ns > 1) {
     if (split) {
       RHMC_CUDA_TRY(cudaEventRecord(c->ev_base[k % 3], s));
@@ -415,7 +425,7 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
     if (use_tensor_update<T>(n))
       RHMC_TRY(update_shifts_tc((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                 b.st->upd, 1, ns, rows, len, b.btiles, &b.st->device_timeout, ss));
-    else if (use_column_update<T>())
+    else if (cols)
       RHMC_TRY(update_shifts_cols((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                   b.st->upd, 1, ns, rows, n, len, ss));
     else

@@ -733,6 +733,120 @@ static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2
   return RHMC_OK;
 }
 
+// ------------------------------------------------------------ Y = C + A M, column owners
+// FP32 tall-skinny update (Algorithm 1 line 5, W = Q - (AP) alpha, and
+// Q = W rho^-1): lane l < 2N owns column j = l mod N of M (kept in registers)
+// for rows of parity l / N of each row pair; the warp's tiles of R rows of A
+// and C are staged by cp.async two tiles deep; every lane reads the A row as
+// a broadcast.
+template <int N, int R, int W>
+__global__ void __launch_bounds__(W * 32) k_axpy_cols(const float2 *__restrict__ A, const float2 *__restrict__ Cin,
+                                                      const float2 *__restrict__ M, float2 *__restrict__ Y,
+                                                      long rows) {
+  constexpr int TILE = R * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 *wb = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * 4 * TILE;  // [2 buffers][A, C]
+  const int h = lane / N, j = lane - (lane / N) * N;
+  const bool act = lane < 2 * N;
+  float2 cf[N];
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) cf[k] = M[k * N + j];
+  }
+  const long ntiles = (rows + R - 1) / R;
+  const long t0 = (long)blockIdx.x * W + warp, dt = (long)gridDim.x * W;
+  auto issue = [&](long tile, int b) {
+    const long r0 = tile * R;
+    const int chunks = (int)min((long)R, rows - r0) * N / 2;
+    const unsigned da = (unsigned)__cvta_generic_to_shared(wb + (2 * b) * TILE);
+    const unsigned dc = (unsigned)__cvta_generic_to_shared(wb + (2 * b + 1) * TILE);
+    const char *sa = reinterpret_cast<const char *>(A + r0 * N);
+    const char *sc = reinterpret_cast<const char *>(Cin ? Cin + r0 * N : nullptr);
+    for (int c = lane; c < chunks; c += 32) {
+      cpa16(da + 16u * c, sa + 16L * c);
+      if (Cin) cpa16(dc + 16u * c, sc + 16L * c);
+    }
+  };
+  if (t0 < ntiles) issue(t0, 0);
+  cp_async_commit();
+  int b = 0;
+  for (long tile = t0; tile < ntiles; tile += dt, b ^= 1) {
+    if (tile + dt < ntiles) issue(tile + dt, b ^ 1);
+    cp_async_commit();
+    cpa_wait<1>();
+    __syncwarp();
+    const long r0 = tile * R;
+    const int nr = (int)min((long)R, rows - r0);
+    const float2 *at = wb + (2 * b) * TILE, *ct = wb + (2 * b + 1) * TILE;
+    if (act) {
+#pragma unroll 1
+      for (int r = h; r < nr; r += 2) {
+        float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+        const float2 *ar = at + r * N;
+        if constexpr (N % 2 == 0) {
+#pragma unroll
+          for (int k = 0; k < N; k += 2) {
+            const float4 u = *reinterpret_cast<const float4 *>(ar + k);
+            const float2 c0 = cf[k], c1 = cf[k + 1];
+            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+            ax1 = fmaf(u.z, c1.x, ax1); ax1 = fmaf(-u.w, c1.y, ax1);
+            ay1 = fmaf(u.z, c1.y, ay1); ay1 = fmaf(u.w, c1.x, ay1);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float2 u = ar[k], c0 = cf[k];
+            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+          }
+        }
+        float2 y = make_float2(ax0 + ax1, ay0 + ay1);
+        if (Cin) {
+          const float2 cv = ct[r * N + j];
+          y.x += cv.x;
+          y.y += cv.y;
+        }
+        Y[(r0 + r) * N + j] = y;
+      }
+    }
+    __syncwarp();  // buffer b is refilled for the tile after next
+  }
+  cpa_wait<0>();
+}
+
+constexpr int kAxpyRows = 8, kAxpyWarps = 16;
+
+template <int N>
+static void launch_axpy_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows,
+                             cudaStream_t s) {
+  const int threads = kAxpyWarps * 32;
+  const size_t smem = (size_t)kAxpyWarps * 4 * kAxpyRows * N * sizeof(float2);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_axpy_cols<N, kAxpyRows, kAxpyWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+  });
+  const long ntiles = (rows + kAxpyRows - 1) / kAxpyRows;
+  long grid = (ntiles + kAxpyWarps - 1) / kAxpyWarps;
+  grid = std::min(grid, (long)resident_ctas(k_axpy_cols<N, kAxpyRows, kAxpyWarps>, threads, smem));
+  k_axpy_cols<N, kAxpyRows, kAxpyWarps><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows);
+}
+
+// Y = C + A M for FP32 fields of width n (C may be null), column-owner kernel.
+rhmc_status_t axpy_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows, int n,
+                        cudaStream_t s) {
+  if (rows % 8) return RHMC_ERR_INVALID_ARG;
+  prof_begin(PROF_AXPY, s);
+#define L_AX(NN) launch_axpy_cols<NN>(A, C, M, Y, rows, s)
+  RHMC_DISPATCH_N(n, L_AX)
+#undef L_AX
+  prof_end(s, (double)rows * n * sizeof(float2) * (C ? 3 : 2));
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
 // ------------------------------------------------------------ flush
 __global__ void k_flush(double2 *__restrict__ X64, float2 *__restrict__ X32, long len) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
