@@ -402,11 +402,14 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   RHMC_TRY(gram<T>(P, AP, rows, n, b.gscratch, b.partial, s));
   RHMC_TRY(nxn_alpha<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.mw, s));
   const bool cols = use_column_update<T>();
-  if (cols)
-    RHMC_TRY(axpy_cols((const float2 *)AP, (const float2 *)Qprev, (const float2 *)b.mw, (float2 *)W, rows, n, s));
-  else
+  if (cols) {
+    // W = Q - (AP) alpha and its Gram W^dagger W in one pass
+    RHMC_TRY(axpy_gram_cols((const float2 *)AP, (const float2 *)Qprev, (const float2 *)b.mw, (float2 *)W, rows, n,
+                            b.gscratch, b.partial, s));
+  } else {
     RHMC_TRY(block_axpy<T, T>(AP, Qprev, (const C<T> *)b.mw, W, rows, n, s));
-  RHMC_TRY(gram<T>(W, W, rows, n, b.gscratch, b.partial, s));
+    RHMC_TRY(gram<T>(W, W, rows, n, b.gscratch, b.partial, s));
+  }
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
   if (cols) {

@@ -816,6 +816,115 @@ __global__ void __launch_bounds__(W * 32) k_axpy_cols(const float2 *__restrict__
   cpa_wait<0>();
 }
 
+// Y = C + A M fused with the Gram G = Y^dagger Y (the thin-QR Gram of line 5):
+// after a row pair of Y is formed, it is written to the warp's row buffer and
+// lane (h, j) adds conj(Y[r][i]) Y[r][j] for all i to its FP32 column of G;
+// the columns are combined across the row parities, the warps (FP64, shared
+// memory) and the CTAs (partials summed in fixed order by k_gram_sum).
+template <int N, int R, int W>
+__global__ void __launch_bounds__(W * 32) k_axpy_gram_cols(const float2 *__restrict__ A,
+                                                           const float2 *__restrict__ Cin,
+                                                           const float2 *__restrict__ M, float2 *__restrict__ Y,
+                                                           long rows, double2 *__restrict__ partial) {
+  constexpr int TILE = R * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 *wb = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * (4 * TILE + 2 * N);  // [2][A, C], row pair
+  float2 *wrow = wb + 4 * TILE;
+  const int h = lane / N, j = lane - (lane / N) * N;
+  const bool act = lane < 2 * N;
+  float2 cf[N], g[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) g[k] = make_float2(0.f, 0.f);
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) cf[k] = M[k * N + j];
+  }
+  const long ntiles = (rows + R - 1) / R;
+  const long t0 = (long)blockIdx.x * W + warp, dt = (long)gridDim.x * W;
+  auto issue = [&](long tile, int b) {
+    const long r0 = tile * R;
+    const int chunks = (int)min((long)R, rows - r0) * N / 2;
+    const unsigned da = (unsigned)__cvta_generic_to_shared(wb + (2 * b) * TILE);
+    const unsigned dc = (unsigned)__cvta_generic_to_shared(wb + (2 * b + 1) * TILE);
+    const char *sa = reinterpret_cast<const char *>(A + r0 * N);
+    const char *sc = reinterpret_cast<const char *>(Cin + r0 * N);
+    for (int c = lane; c < chunks; c += 32) {
+      cpa16(da + 16u * c, sa + 16L * c);
+      cpa16(dc + 16u * c, sc + 16L * c);
+    }
+  };
+  if (t0 < ntiles) issue(t0, 0);
+  cp_async_commit();
+  int b = 0;
+  for (long tile = t0; tile < ntiles; tile += dt, b ^= 1) {
+    if (tile + dt < ntiles) issue(tile + dt, b ^ 1);
+    cp_async_commit();
+    cpa_wait<1>();
+    __syncwarp();
+    const long r0 = tile * R;
+    const int nr = (int)min((long)R, rows - r0);
+    const float2 *at = wb + (2 * b) * TILE, *ct = wb + (2 * b + 1) * TILE;
+#pragma unroll 1
+    for (int r = 0; r < nr; r += 2) {
+      float2 y = make_float2(0.f, 0.f);
+      if (act) {
+        float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+        const float2 *ar = at + (r + h) * N;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const float2 u = ar[k], c0 = cf[k];
+          if (k & 1) {
+            ax1 = fmaf(u.x, c0.x, ax1); ax1 = fmaf(-u.y, c0.y, ax1);
+            ay1 = fmaf(u.x, c0.y, ay1); ay1 = fmaf(u.y, c0.x, ay1);
+          } else {
+            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+          }
+        }
+        const float2 cv = ct[(r + h) * N + j];
+        y = make_float2(ax0 + ax1 + cv.x, ay0 + ay1 + cv.y);
+        Y[(r0 + r + h) * N + j] = y;
+        wrow[h * N + j] = y;
+      }
+      __syncwarp();
+      if (act) {
+        const float2 *wr = wrow + h * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {  // g[i] += conj(Y[r][i]) Y[r][j]
+          const float2 w = wr[i];
+          g[i].x = fmaf(w.x, y.x, fmaf(w.y, y.y, g[i].x));
+          g[i].y = fmaf(w.x, y.y, fmaf(-w.y, y.x, g[i].y));
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();  // buffer b is refilled for the tile after next
+  }
+  cpa_wait<0>();
+  // row parities: lane j += lane N + j
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    g[i].x += __shfl_down_sync(0xffffffffu, g[i].x, N);
+    g[i].y += __shfl_down_sync(0xffffffffu, g[i].y, N);
+  }
+  __syncthreads();
+  double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [W][N * N], reuses the tile buffers
+  if (lane < N) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) red[warp * N * N + i * N + lane] = make_double2((double)g[i].x, (double)g[i].y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    double2 sum = red[e];
+    for (int w = 1; w < W; ++w) {
+      sum.x += red[w * N * N + e].x;
+      sum.y += red[w * N * N + e].y;
+    }
+    partial[(long)e * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
 constexpr int kAxpyRows = 8, kAxpyWarps = 16;
 
 template <int N>
@@ -832,6 +941,39 @@ static void launch_axpy_cols(const float2 *A, const float2 *C, const float2 *M, 
   long grid = (ntiles + kAxpyWarps - 1) / kAxpyWarps;
   grid = std::min(grid, (long)resident_ctas(k_axpy_cols<N, kAxpyRows, kAxpyWarps>, threads, smem));
   k_axpy_cols<N, kAxpyRows, kAxpyWarps><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows);
+}
+
+template <int N>
+static void launch_axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows,
+                                  double2 *scratch, double2 *out, cudaStream_t s) {
+  const int threads = kAxpyWarps * 32;
+  const size_t smem = std::max((size_t)kAxpyWarps * (4 * kAxpyRows * N + 2 * N) * sizeof(float2),
+                               (size_t)kAxpyWarps * N * N * sizeof(double2));
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+  });
+  const long ntiles = (rows + kAxpyRows - 1) / kAxpyRows;
+  long grid = (ntiles + kAxpyWarps - 1) / kAxpyWarps;
+  grid = std::min(grid, (long)std::min(kGramCtas, resident_ctas(k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps>,
+                                                                  threads, smem)));
+  k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
+  k_gram_sum<<<N * N, 128, 0, s>>>(scratch, (int)grid, out);
+}
+
+// Y = C + A M and out = Y^dagger Y (FP64 sums of FP32 products) in one pass over
+// the rows; scratch holds kGramCtas * n * n partials.
+rhmc_status_t axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows, int n,
+                             double2 *scratch, double2 *out, cudaStream_t s) {
+  if (rows % 8 || !C) return RHMC_ERR_INVALID_ARG;
+  prof_begin(PROF_AXPY, s);
+#define L_AG(NN) launch_axpy_gram_cols<NN>(A, C, M, Y, rows, scratch, out, s)
+  RHMC_DISPATCH_N(n, L_AG)
+#undef L_AG
+  prof_end(s, (double)rows * n * sizeof(float2) * 3);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
 }
 
 // Y = C + A M for FP32 fields of width n (C may be null), column-owner kernel.

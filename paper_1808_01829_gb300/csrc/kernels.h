@@ -63,6 +63,9 @@ rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s);
 // Y = C + A M (FP32, C may be null) with column-owner lanes and cp.async-staged row tiles
 rhmc_status_t axpy_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows, int n,
                         cudaStream_t s);
+// Y = C + A M fused with out = Y^dagger Y (n x n FP64, scratch: kGramCtas * n * n partials)
+rhmc_status_t axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows, int n,
+                             double2 *scratch, double2 *out, cudaStream_t s);
 // FP32 shifted updates (lines 11-12) with column-owner lanes and cp.async-staged row tiles
 rhmc_status_t update_shifts_cols(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
                                  int s_begin, int s_end, long rows, int n, long fstride, cudaStream_t s);
