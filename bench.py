@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 per-vector SCG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                    help="rhmc_tune_set(KEY, VALUE) before the run (repeatable; recorded in config)")
     return ap.parse_args()
 
 
@@ -259,6 +261,11 @@ def run_gpu(args):
     from paper_1808_01829_gb300.api import RhmcContext
 
     _build.build()
+    from paper_1808_01829_gb300 import _lib as _l
+
+    for kv in args.tune:
+        k, v = kv.split("=")
+        _l.check(_l.load().rhmc_tune_set(int(k), int(v)), "rhmc_tune_set")
     cfg = dict(WORKLOAD)
     if args.small:
         cfg.update(dims=[8, 8, 8, 8], mass=0.05, n_pf=4, n_shifts=12, r=-1.0 / 16, interval=[2e-3, 64.0], index=1,
@@ -369,7 +376,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": cfg["workload"], "precision": cfg["precision"],
                        "l2": "inputs larger than L2 (U 191 MB, fields 64-127 MB each)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", **({"tune": args.tune} if args.tune else {})},
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": len_b, "d2h_bytes_per_step": G.numel() * 16},
             "gpu_launches": launches,
             "roofline": roof,

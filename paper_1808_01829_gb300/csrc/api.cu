@@ -931,9 +931,13 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
       return RHMC_ERR_CUDA;
     }
   }
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // the side stream (shifted steps) yields to the base recursion: lowest
+  // priority; captured chunks of the base recursion run at the highest
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->main.cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithPriority(&c->main.cap, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
     set_error("rhmc_create: cannot create the side stream");
     rhmc_destroy(c);
     return RHMC_ERR_CUDA;

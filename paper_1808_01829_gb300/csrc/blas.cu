@@ -1078,7 +1078,9 @@ static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratc
     cudaFuncSetAttribute(k_gram<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
-  const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, kGramCtas);
+  // one wave: as many CTAs as are resident at once (at most the partials' capacity)
+  const int resident = same ? resident_ctas(k_gram<T, N, true>, 256, bytes) : resident_ctas(k_gram<T, N, false>, 256, bytes);
+  const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, std::min(kGramCtas, resident));
   if (same)
     k_gram<T, N, true><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
   else
