@@ -50,7 +50,9 @@ WORKLOAD = {
 # byte of a kernel, from one capture on a smaller case of the same kernel
 # (profiles/); the per-launch traffic of the bench's launches is scaled from it
 # by the units processed.  A kernel changed since its capture has no entry.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {
+    "update_shifts_fp32": (0.960, "profiles/k_update_cols_16x16x16x32_n16.md (16^3x32, 15 shifts; scaled by bytes moved)"),
+}
 METRIC = "time/force eval at 24^4,n_pf=16 (1e-8 res): block+mixed vs FP64 CG; Dslash GB/s"
 L2_BYTES = 129 * 1024 * 1024
 
