@@ -56,5 +56,49 @@ __device__ __forceinline__ DF df_norm(const DF &a) {
   const float h = __fadd_rn(a.h, a.e);
   return DF{h, __fsub_rn(a.e, __fsub_rn(h, a.h))};
 }
+
+// Split x into hi = RN_float(x) and lo = RN_float(x - hi) with integer
+// operations on the IEEE-754 bit patterns (FP64 conversions run at 1/64 of
+// the FP32 rate on this GPU).  x - hi is d 2^(e - 1075) exactly for the
+// integer d = (mantissa remainder below the float's 24 bits, minus 2^29 if
+// hi rounded up), |d| <= 2^28, so lo = RN(d) 2^(e - 1075).  Zeros,
+// subnormals and values whose hi or lo leaves the normal float range take
+// the FP64 conversion.
+__device__ __forceinline__ float2 df_split1(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  // hi normal (e - 1023 in [-126, 127]) and lo normal (e - 1075 + 28 >= -126)
+  if (e < 1023 - 126 + 52 || e > 1023 + 126) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  }
+  const unsigned long long mant = b & ((1ull << 52) - 1);
+  const unsigned sign = (unsigned)(b >> 63);
+  unsigned m23 = (unsigned)(mant >> 29);
+  int rem = (int)(mant & ((1u << 29) - 1));
+  int fe = e - 1023 + 127;
+  if (rem > (1 << 28) || (rem == (1 << 28) && (m23 & 1u))) {  // round to nearest even
+    rem -= 1 << 29;
+    if (++m23 == (1u << 23)) {
+      m23 = 0;
+      ++fe;
+    }
+  }
+  const float h = __uint_as_float((sign << 31) | ((unsigned)fe << 23) | m23);
+  float l = ldexpf(__int2float_rn(rem), e - 1075);
+  if (sign) l = -l;
+  return make_float2(h, l);
+}
+// hi + lo in FP64: the floats are widened by integer operations (exact), one FP64 add
+__device__ __forceinline__ double df_widen1(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xff;
+  if (ex == 0 || ex == 0xff) return (double)f;  // zero, subnormal, inf/nan
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(ex - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7fffff) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double df_merge1(float h, float l) { return df_widen1(h) + df_widen1(l); }
 }  // namespace df
 }  // namespace rhmc

@@ -658,14 +658,14 @@ __global__ void k_df_convert(const double2 *__restrict__ in64, float4 *__restric
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= len) return;
   const double2 z = in64[i];
-  const float xh = (float)z.x, yh = (float)z.y;
-  outdf[i] = make_float4(xh, yh, (float)(z.x - (double)xh), (float)(z.y - (double)yh));
+  const float2 a = df_split1(z.x), b = df_split1(z.y);
+  outdf[i] = make_float4(a.x, b.x, a.y, b.y);
 }
 __global__ void k_df_merge(float4 *__restrict__ io, long len) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= len) return;
   const float4 v = io[i];
-  reinterpret_cast<double2 *>(io)[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  reinterpret_cast<double2 *>(io)[i] = make_double2(df_merge1(v.x, v.z), df_merge1(v.y, v.w));
 }
 
 rhmc_status_t stage_links_df(const Geom &g, const double2 *l64, float4 *ldf, cudaStream_t s) {
