@@ -256,9 +256,10 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_GRAPHS              solver iterations in captured CUDA graphs (0, 1: built-in)
  *                                 or as eager launches (2)
  *   RHMC_TUNE_HOP_STAGED          FP32 hop kernel: all 8 neighbours' loads issued at once,
- *                                 links by cp.async (0, 3: built-in); tiles staged in shared
- *                                 memory by cp.async, even n (1); register staged with one
- *                                 direction of prefetch (2)
+ *                                 links by cp.async (0: built-in; 3: one right-hand side per
+ *                                 thread; 4: two, even n); tiles staged in shared memory by
+ *                                 cp.async, even n (1); register staged with one direction of
+ *                                 prefetch (2)
  *   RHMC_TUNE_REFINE_LANES        defect corrections of different shifts run concurrently on
  *                                 up to this many streams, one host thread each (0: 4, the
  *                                 most; 1: in turn on the caller's stream)

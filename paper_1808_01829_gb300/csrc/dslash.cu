@@ -266,11 +266,12 @@ __device__ __forceinline__ void site_coords32(const Geom &g, int par, int h, int
   x0 = 2 * xh + (((x1 + x2 + x3) & 1) ^ par);
 }
 
-template <int N, bool SELF>
+template <int N, int R, bool SELF>
 __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *__restrict__ links,
                                                 const float2 *__restrict__ in, float2 *__restrict__ out,
                                                 const float2 *__restrict__ self, float a) {
-  constexpr int TILE = (128 / N) < 32 ? (128 / N) : 32;  // sites per CTA (static shared memory <= 20 KB)
+  constexpr int TPS = N / R;                                 // threads per site
+  constexpr int TILE = (128 / TPS) < 32 ? (128 / TPS) : 32;  // sites per CTA (static shared memory <= 20 KB)
   __shared__ __align__(16) float2 sl[TILE * 72];
   __shared__ int snb[TILE * 8];
   const int tid = threadIdx.x;
@@ -297,60 +298,81 @@ __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *_
     snb[k] = (lex >> 1) * 3 * N;
   }
   __syncthreads();
-  const int ls = tid / N, j = tid - (tid / N) * N;
+  const int ls = tid / TPS, j = (tid - (tid / TPS) * TPS) * R;
   const bool live = ls < nsites;
-  float2 v[8][3];
+  float2 v[8][3][R];
   if (live) {
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
       const float2 *nb = in + snb[ls * 8 + d] + j;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[d][c] = __ldg(nb + c * N);
+      for (int c = 0; c < 3; ++c) Vec<float, R>::ld(nb + c * N, v[d][c]);
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   if (!live) return;
-  float2 acc[3];
+  float2 acc[3][R];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = make_float2(0.f, 0.f);
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[c][r] = make_float2(0.f, 0.f);
   const float2 *lk = sl + ls * 72;
 #pragma unroll
   for (int d = 0; d < 8; ++d)
 #pragma unroll
     for (int ca = 0; ca < 3; ++ca)
 #pragma unroll
-      for (int cb = 0; cb < 3; ++cb) cmac<float>(acc[ca], lk[d * 9 + ca * 3 + cb], v[d][cb]);
+      for (int cb = 0; cb < 3; ++cb) {
+        const float2 e = lk[d * 9 + ca * 3 + cb];
+#pragma unroll
+        for (int r = 0; r < R; ++r) cmac<float>(acc[ca][r], e, v[d][cb][r]);
+      }
   float2 *op = out + (long)(h0 + ls) * 3 * N + j;
   if (SELF) {
     const float2 *sp = self + (long)(h0 + ls) * 3 * N + j;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float2 sv = __ldg(sp + c * N);
-      acc[c] = make_float2(a * sv.x - acc[c].x, a * sv.y - acc[c].y);
+      float2 sv[R];
+      Vec<float, R>::ld(sp + c * N, sv);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[c][r] = make_float2(a * sv[r].x - acc[c][r].x, a * sv[r].y - acc[c][r].y);
     }
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) op[c * N] = acc[c];
+  for (int c = 0; c < 3; ++c) Vec<float, R>::st(op + c * N, acc[c]);
 }
 
-template <int N>
+template <int N, int R>
 static void launch_hop_pf_n(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
                             const float2 *self, double a, cudaStream_t s) {
-  constexpr int TILE = (128 / N) < 32 ? (128 / N) : 32;
-  const int threads = ((TILE * N + 31) / 32) * 32;
+  constexpr int TPS = N / R;
+  constexpr int TILE = (128 / TPS) < 32 ? (128 / TPS) : 32;
+  const int threads = ((TILE * TPS + 31) / 32) * 32;
   const unsigned grid = (unsigned)((g.Vh + TILE - 1) / TILE);
   if (self)
-    k_hop_pf<N, true><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
+    k_hop_pf<N, R, true><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
   else
-    k_hop_pf<N, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
+    k_hop_pf<N, R, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
 }
 
 static bool launch_hop_pf(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
                           const float2 *self, double a, int n, cudaStream_t s) {
+  // two right-hand sides per thread (16-byte loads, half the load instructions): built-in
+  // for even n >= 12 (measured at 24^4: n = 16 65 us against 71 us; n = 8 no gain)
+  const int mode = tune_get(TUNE_HOP_STAGED);
+  const bool r2 = n % 2 == 0 && (mode == 4 || (mode == 0 && n >= 12));
   switch (n) {
-#define L_PF(NN) \
-  case NN: launch_hop_pf_n<NN>(g, par, links, in, out, self, a, s); return true;
+#define L_PF(NN)                                                                   \
+  case NN:                                                                         \
+    if constexpr (NN % 2 == 0) {                                                   \
+      if (r2) {                                                                    \
+        launch_hop_pf_n<NN, 2>(g, par, links, in, out, self, a, s);                \
+        return true;                                                               \
+      }                                                                            \
+    }                                                                              \
+    launch_hop_pf_n<NN, 1>(g, par, links, in, out, self, a, s);                    \
+    return true;
     L_PF(1) L_PF(2) L_PF(3) L_PF(4) L_PF(5) L_PF(6) L_PF(7) L_PF(8)
     L_PF(9) L_PF(10) L_PF(11) L_PF(12) L_PF(13) L_PF(14) L_PF(15) L_PF(16)
 #undef L_PF
@@ -542,7 +564,7 @@ static bool launch_hop_staged(const Geom &g, int par, const float2 *links, const
 template <typename T> static bool use_hop_pf(const void *links, const void *in, int nbatch) {
   if (sizeof(C<T>) != 8 || nbatch != 1 || ((uintptr_t)links & 15)) return false;
   const int mode = tune_get(TUNE_HOP_STAGED);
-  return mode == 0 || mode == 3;
+  return mode == 0 || mode == 3 || mode == 4;  // 3: one right-hand side per thread, 4: two
 }
 
 // The staged kernel applies to FP32 single fields with 16-byte aligned rows.

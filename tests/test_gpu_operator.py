@@ -75,7 +75,7 @@ def test_hop_fp32_kernel_variants(dims, n):
     refs = [oracle.hop(dims, U, X, par) for par in (0, 1)]
     refA = oracle.apply_A(dims, mass, U, X, sigma=sigma)
     try:
-        for mode in (1, 2, 3):
+        for mode in (1, 2, 3, 4):
             for R in (1, 2, 4):
                 if n % R:
                     continue
