@@ -213,12 +213,17 @@ def run_batch(dev, reps=3):
     from paper_1808_01829_gb300.api import RhmcContext, block_multishift_cg_batch
     from paper_1808_01829_gb300.remez import rational_approx
 
-    items = []
+    from paper_1808_01829_gb300 import autotune
+
+    items, tuned = [], []
+    cache = os.path.join(tempfile.mkdtemp(prefix="rhmc_tune_"), "tune.json")
     for k, (dims, n) in enumerate(zip(BATCH["dims"], BATCH["n_pf"])):
         ra = rational_approx(-1.0 / (4 * n), 2e-3, 64.0, 12)
         ctx = RhmcContext(dims, BATCH["mass"], device=dev.index or 0)
         ctx.set_gauge(torch.from_numpy(syn.random_links(dims, 0.5, syn.seed_gauge(10 + k))).to(dev))
         B = torch.from_numpy(syn.gaussian_pseudofermions(dims, n, syn.seed_phi(10 + k))).to(dev)
+        # per-ensemble launch settings (hop RHS per thread, update tile shape), untimed
+        tuned.append(autotune.tune(ctx, n, shifts=ra.beta, cache=cache))
         items.append((ctx, B, ra.beta))
     stream = torch.cuda.current_stream(dev)
 
@@ -241,6 +246,7 @@ def run_batch(dev, reps=3):
     sites_rhs = sum(int(torch.tensor(d).prod()) // 2 * n for d, n in zip(BATCH["dims"], BATCH["n_pf"]))
     res = {"workload": BATCH["workload"], "ms": bat_ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / bat_ms,
            "iters": [i.iters for i in bat], "true_rel_resid_max": max(i.true_rel_resid_max for i in bat),
+           "autotuned": [{str(k): v for k, v in t.items()} for t in tuned],
            "site_rhs_shifts_per_s": sites_rhs * 12 / (bat_ms * 1e-3)}
     for c, _, _ in items:
         c.close()

@@ -276,6 +276,14 @@ enum {
   RHMC_TUNE_HOP_STAGED = 8,
   RHMC_TUNE_REFINE_LANES = 9
 };
+
+/* The same settings for one context only (they take precedence over the
+ * process-wide ones in every call on ctx, including the concurrent solves of
+ * rhmc_block_multishift_cg_batch, so each ensemble can run its own tuned
+ * kernels).  Value 0 falls back to the process-wide setting.  get returns the
+ * value in effect for ctx. */
+rhmc_status_t rhmc_ctx_tune_set(rhmc_ctx_t *ctx, int key, int value);
+int rhmc_ctx_tune_get(const rhmc_ctx_t *ctx, int key);
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);
 rhmc_status_t rhmc_profile_read(int category, long long *launches, double *ms, double *bytes);

@@ -131,6 +131,13 @@ class RhmcContext:
                          info.true_rel_resid_max, info.phase1_rel_resid_max,
                          [list(buf[q * n:(q + 1) * n]) for q in range(ns)], info.phase1_ms, info.refine_ms)
 
+    # -- per-context launch settings (rhmc_ctx_tune_set / rhmc_ctx_tune_get)
+    def tune_set(self, key: int, value: int):
+        _lib.check(self.lib.rhmc_ctx_tune_set(self._h, int(key), int(value)), "rhmc_ctx_tune_set")
+
+    def tune_get(self, key: int) -> int:
+        return int(self.lib.rhmc_ctx_tune_get(self._h, int(key)))
+
     # -- rhmc_block_multishift_cg
     def block_multishift_cg(self, B: torch.Tensor, shifts: Sequence[float], tol: float, max_iter: int = 0,
                             precision: str = "mixed", out=None, workspace: Optional[torch.Tensor] = None,

@@ -1,14 +1,19 @@
 """Autotuner for the library's launch parameters (rhmc_tune_set).
 
-For a given workload (lattice, n_rhs) it times the candidates of each tunable
-with the library's own event profiler and keeps the fastest:
+For a given workload (lattice, n_rhs) it times, with the library's own event
+profiler, the candidates of
 
-* hop right-hand sides per thread (1, 2, 4 dividing n): FP32 and FP64 operator;
-* threads per CTA of the fused shift update (64, 128, 256): a short solve.
+* the FP32 hop: one or two right-hand sides per thread (RHMC_TUNE_HOP_STAGED
+  3 / 4), on the FP32 operator;
+* the column-owner shifted-update kernel: rows per warp tile, warps per CTA
+  and shifts in flight (RHMC_TUNE_UPDATE_TENSOR variants 4, 6, 7, 8, 9), in
+  a short mixed-precision solve with the given shifts;
 
-Results are cached in a JSON file keyed by GPU name, lattice extents and width,
-so later runs only apply them.  Tuning only changes how kernels are launched,
-never what they compute.
+and keeps the fastest.  The settings are applied to the context
+(rhmc_ctx_tune_set), so ensembles solved together by
+rhmc_block_multishift_cg_batch each run their own.  Results are cached in a
+JSON file keyed by GPU name, lattice extents and width, so later runs only
+apply them.  Tuning changes how kernels are launched, never what they compute.
 """
 from __future__ import annotations
 
@@ -20,8 +25,10 @@ import torch
 
 from . import _lib, roofline
 
-KEY_HOP_R = 0
-KEY_UPDATE_THREADS = 1
+KEY_HOP = 8          # RHMC_TUNE_HOP_STAGED
+KEY_UPDATE = 6       # RHMC_TUNE_UPDATE_TENSOR
+HOP_CANDIDATES = (3, 4)
+UPDATE_CANDIDATES = (8, 7, 6, 4, 9)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rhmc_gb300_autotune.json")
 
 
@@ -37,65 +44,66 @@ def _load(path):
     return {}
 
 
-def apply(settings: dict):
-    lib = _lib.load()
+def apply(rctx, settings: dict):
     for k, v in settings.items():
-        _lib.check(lib.rhmc_tune_set(int(k), int(v)), "rhmc_tune_set")
+        rctx.tune_set(int(k), int(v))
 
 
-def reset():
-    lib = _lib.load()
-    for k in range(8):
-        lib.rhmc_tune_set(k, 0)
+def reset(rctx):
+    for k in (KEY_HOP, KEY_UPDATE):
+        rctx.tune_set(k, 0)
+
+
+def _per_launch(stats, name, per_byte=False):
+    s = stats.get(name)
+    if not s or not s["launches"]:
+        return None
+    return s["ms"] / (max(s["bytes"], 1.0) if per_byte else s["launches"])
 
 
 def tune(rctx, n: int, shifts=None, cache: Optional[str] = DEFAULT_CACHE, force: bool = False, reps: int = 5):
-    """Tune for context rctx and width n; returns {key: value} (applied)."""
+    """Tune for context rctx and width n; returns {key: value} (applied to rctx)."""
     db = _load(cache)
     key = _key(rctx.dims, n)
     if key in db and not force:
         settings = {int(k): v for k, v in db[key].items()}
-        apply(settings)
+        apply(rctx, settings)
         return settings
-    lib = _lib.load()
     from . import synthetic as syn
 
     X = torch.from_numpy(syn.gaussian_pseudofermions(rctx.dims, n, 99)).to(rctx.device)
     settings = {}
-    # hop: right-hand sides per thread, timed on the FP32 operator
     best = None
-    for R in (1, 2, 4):
-        if n % R:
+    for mode in HOP_CANDIDATES:
+        if mode == 4 and n % 2:
             continue
-        lib.rhmc_tune_set(KEY_HOP_R, R)
+        rctx.tune_set(KEY_HOP, mode)
         try:
             rctx.apply_mdagm_mrhs(X, 0.0, "fp32")
             st = roofline.profile(lambda: [rctx.apply_mdagm_mrhs(X, 0.0, "fp32") for _ in range(reps)])
         except _lib.RhmcError:
             continue
-        t = st["hop_fp32"]["ms"] / st["hop_fp32"]["launches"]
-        if best is None or t < best[0]:
-            best = (t, R)
-    settings[KEY_HOP_R] = best[1]
-    lib.rhmc_tune_set(KEY_HOP_R, best[1])
-    # fused shift update: threads per CTA, timed inside a short solve
+        t = _per_launch(st, "hop_fp32")
+        if t is not None and (best is None or t < best[0]):
+            best = (t, mode)
+    if best:
+        settings[KEY_HOP] = best[1]
+        rctx.tune_set(KEY_HOP, best[1])
     if shifts:
         best = None
-        for thr in (64, 128, 256):
-            lib.rhmc_tune_set(KEY_UPDATE_THREADS, thr)
+        for v in UPDATE_CANDIDATES:
+            rctx.tune_set(KEY_UPDATE, v)
             try:
                 st = roofline.profile(lambda: rctx.block_multishift_cg(X, shifts, 1e-3, max_iter=12,
                                                                        precision="mixed", allow_not_converged=True))
             except _lib.RhmcError:
                 continue
-            if "update_fp32" not in st:
-                continue
-            t = st["update_fp32"]["ms"] / max(st["update_fp32"]["bytes"], 1.0)
-            if best is None or t < best[0]:
-                best = (t, thr)
+            t = _per_launch(st, "update_shifts_fp32", per_byte=True)
+            if t is not None and (best is None or t < best[0]):
+                best = (t, v)
         if best:
-            settings[KEY_UPDATE_THREADS] = best[1]
-            lib.rhmc_tune_set(KEY_UPDATE_THREADS, best[1])
+            settings[KEY_UPDATE] = best[1]
+            rctx.tune_set(KEY_UPDATE, best[1])
     if cache:
         db = _load(cache)
         db[key] = {str(k): v for k, v in settings.items()}

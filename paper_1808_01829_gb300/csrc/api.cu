@@ -65,7 +65,14 @@ static cudaEvent_t pool_event() {
 bool prof_on() { return g_prof; }
 
 static int g_tune[TUNE_NKEYS] = {0};
-int tune_get(int key) { return (key >= 0 && key < TUNE_NKEYS) ? g_tune[key] : 0; }
+// per-context settings (rhmc_ctx_tune_set) of the context the calling host
+// thread works for; nonzero entries override the process-wide ones
+static thread_local const int *t_tune_override = nullptr;
+int tune_get(int key) {
+  if (key < 0 || key >= TUNE_NKEYS) return 0;
+  if (t_tune_override && t_tune_override[key] > 0) return t_tune_override[key];
+  return g_tune[key];
+}
 
 void prof_begin(int cat, cudaStream_t s) {
   if (!g_prof) return;
@@ -165,6 +172,7 @@ struct rhmc_ctx {
   cudaEvent_t ev_base[3] = {};     // base update of iteration k done (slot k % 3)
   cudaEvent_t ev_side[3] = {};     // shifted updates of iteration k done
   SolverLane main;                 // the caller's stream
+  int tune[TUNE_NKEYS] = {};       // per-context launch settings (0: the process-wide value)
   std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
 };
 
@@ -181,6 +189,13 @@ struct DeviceGuard {
     cudaGetDevice(&cur);
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
+};
+
+// The calling thread uses ctx's launch settings for the duration of a call.
+struct TuneScope {
+  const int *prev;
+  explicit TuneScope(const rhmc_ctx *c) : prev(t_tune_override) { t_tune_override = c ? c->tune : nullptr; }
+  ~TuneScope() { t_tune_override = prev; }
 };
 
 static rhmc_status_t ensure_pool(rhmc_ctx *c, size_t bytes) {
@@ -768,6 +783,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
     for (int l = 0; l < nl; ++l)
       pool.emplace_back([&, l] {
         DeviceGuard dg(c->device);
+        TuneScope tscope(c);
         SolverLane *L = c->lanes[l].get();
         t_lane = L;
         LaneWork &w = work[l];
@@ -864,7 +880,21 @@ rhmc_status_t rhmc_tune_set(int key, int value) {
   return RHMC_OK;
 }
 
-int rhmc_tune_get(int key) { return rhmc::tune_get(key); }
+int rhmc_tune_get(int key) { return (key >= 0 && key < rhmc::TUNE_NKEYS) ? rhmc::g_tune[key] : 0; }
+
+rhmc_status_t rhmc_ctx_tune_set(rhmc_ctx_t *c, int key, int value) {
+  if (!c || key < 0 || key >= rhmc::TUNE_NKEYS || value < 0) {
+    set_error("rhmc_ctx_tune_set: bad context, key %d or value %d", key, value);
+    return RHMC_ERR_INVALID_ARG;
+  }
+  c->tune[key] = value;
+  return RHMC_OK;
+}
+
+int rhmc_ctx_tune_get(const rhmc_ctx_t *c, int key) {
+  if (!c || key < 0 || key >= rhmc::TUNE_NKEYS) return 0;
+  return c->tune[key] > 0 ? c->tune[key] : rhmc::g_tune[key];
+}
 
 rhmc_status_t rhmc_profile_enable(int on) {
   rhmc::g_recs.clear();
@@ -985,6 +1015,7 @@ rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *c, const void *U, rhmc_stream_t sv) {
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   RHMC_TRY(stage_links(c->g, (const double2 *)U, c->bc_t, c->l64, c->l32, s));
   for (int p = 0; p < 2; ++p) RHMC_TRY(stage_links_df(c->g, c->l64[p], c->ldf[p], s));
@@ -1027,6 +1058,7 @@ rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *c, const void *X, void *Y, int n
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   const long len = c->g.Vh * 3 * n;
   if (p == RHMC_FP64) {
@@ -1056,6 +1088,7 @@ rhmc_status_t rhmc_hop(rhmc_ctx_t *c, const void *X, void *Y, int n, int out_par
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   const long len = c->g.Vh * 3 * n;
   if (p == RHMC_FP64) return hop<double>(c->g, out_par, c->l64[out_par], (const double2 *)X, (double2 *)Y, nullptr, 0, n, 1, 0, s);
@@ -1148,6 +1181,7 @@ rhmc_status_t rhmc_block_multishift_cg(rhmc_ctx_t *c, const void *B, int n, int 
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   if (!ws) {
     RHMC_TRY(ensure_pool(c, rhmc_workspace_bytes(c, n, ns, p)));
@@ -1185,6 +1219,7 @@ rhmc_status_t rhmc_block_multishift_cg_batch(rhmc_batch_item_t *items, int count
       rhmc_batch_item_t &it = items[i];
       rhmc_ctx *c = it.ctx;
       DeviceGuard dg(c->device);
+      TuneScope tscope(c);
       cudaStreamWaitEvent(c->own, start, 0);
       void *ws = it.workspace;
       if (!ws) {
@@ -1220,6 +1255,7 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *c, const void *Bv, int n,
   RHMC_TRY(check_common(c, Bv, Xv, n));
   RHMC_TRY(check_shifts(ns, shifts, tol));
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   const size_t need = scg_bytes(c->g, ns);
   if (!ws) {
@@ -1307,6 +1343,7 @@ rhmc_status_t rhmc_rational_apply(rhmc_ctx_t *c, const void *Phi, int n, double 
     return RHMC_ERR_INVALID_ARG;
   }
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   const long len = c->g.Vh * 3 * n;
   return rational_combine((const double2 *)Phi, alpha0, alpha, (const double2 *)X, ns, len, (double2 *)Y, s);
@@ -1322,6 +1359,7 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
   }
   RHMC_TRY(check_shifts(ns, beta, X_in ? 0.5 : tol));
   DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   cudaStream_t s = (cudaStream_t)sv;
   if (!ws) {
     RHMC_TRY(ensure_pool(c, rhmc_workspace_bytes(c, n, ns, p)));

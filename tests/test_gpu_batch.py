@@ -78,14 +78,15 @@ def test_autotune_keeps_results(tmp_path):
     try:
         X0, _ = ctx.block_multishift_cg(B, ra.beta, 1e-9, precision="mixed")
         settings = autotune.tune(ctx, n, shifts=ra.beta, cache=str(tmp_path / "tune.json"))
-        assert 0 in settings
+        assert 8 in settings and 6 in settings
         X1, info = ctx.block_multishift_cg(B, ra.beta, 1e-9, precision="mixed")
         assert info.true_rel_resid_max <= 1e-9
         assert np.linalg.norm((X1 - X0).cpu().numpy()) <= 1e-6 * np.linalg.norm(X0.cpu().numpy())
-        # cached: a second call only applies
+        # applied to this context only; cached: a second call only applies
+        assert all(ctx.tune_get(k) == v for k, v in settings.items())
         assert autotune.tune(ctx, n, cache=str(tmp_path / "tune.json")) == settings
     finally:
-        autotune.reset()
+        autotune.reset(ctx)
     ctx.close()
 
 
