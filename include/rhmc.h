@@ -198,11 +198,36 @@ rhmc_status_t rhmc_multishift_cg_pervector(rhmc_ctx_t *ctx, const void *B_dev, i
  *             (A + beta_s) X = Phi; NULL = solve them (block solver, tol, p)
  *   G         complex128 [V][4][3][3] output, or NULL for the action only
  *   S_out     optional host double, the action (G and S_out may not both be NULL)
- * The force arithmetic is FP64 in both precision modes. */
+ * The force is FP64-accurate in both precision modes: double-float arithmetic
+ * (pairs of FP32, TwoProduct/TwoSum) on the FP32 units, or native FP64 with
+ * RHMC_TUNE_NATIVE_FP64_RESIDUALS. */
 rhmc_status_t rhmc_force(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
                          const double *beta, int n_shifts, double tol, int max_iter, rhmc_precision_t p,
                          const void *X_in_dev, void *G_dev, double *S_out, void *workspace, rhmc_info_t *info,
                          rhmc_stream_t s);
+
+/* R(A) Phi of Eq. (RA) by the block multishift solve, without storing the
+ * shifted solutions (pseudofermion heatbath and action evaluation, where only
+ * the rational sum is needed):
+ *   Y = alpha0 Phi + sum_s alpha_s (A + beta_s)^-1 Phi.
+ * FP64 throughout.  The solve keeps X^(0) (smallest shift) and one field for
+ * sum_{s>=1} alpha_s X^(s), added in the fused shifted update (the per-shift
+ * X^(s) are never written), so it needs about n_shifts - 2 fewer fields than
+ * rhmc_block_multishift_cg and moves less data per iteration.
+ *   Phi, Y   complex128 [V/2][3][n_pf] on the device (no aliasing)
+ *   alpha, beta  host [n_shifts], beta >= 0 (any sign of alpha: x^(+r) works)
+ *   workspace  rhmc_rational_solve_bytes(ctx, n_pf, n_shifts) bytes, or NULL (pool)
+ *   info     optional: iters; true_rel_resid_max = FP64 true residual of the
+ *            smallest-shift system; phase1_rel_resid_max = largest recursive
+ *            residual over all (shift, column); per_shift_resid = those
+ *            recursive residuals (caller's shift order)
+ * Returns OK once every recursive residual is <= tol, NOT_CONVERGED otherwise
+ * (Y still written).  In FP64 the recursive residuals track the true ones
+ * closely; the smallest-shift true residual is reported as a check. */
+rhmc_status_t rhmc_rational_solve(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
+                                  const double *beta, int n_shifts, double tol, int max_iter, void *Y_dev,
+                                  void *workspace, rhmc_info_t *info, rhmc_stream_t s);
+size_t rhmc_rational_solve_bytes(const rhmc_ctx_t *ctx, int n_pf, int n_shifts);
 
 /* R(A) Phi of Eq. (RA) from given shifted solutions:
  *   Y = alpha0 Phi + sum_s alpha_s X^(s),   X^(s) = (A + beta_s)^-1 Phi,

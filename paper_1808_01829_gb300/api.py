@@ -169,6 +169,25 @@ class RhmcContext:
         _lib.check(rc, "rhmc_multishift_cg_pervector")
         return X, SolveInfo(info.iters, info.dirac_calls, 0, 0, 0, -1.0, -1.0, [])
 
+    # -- rhmc_rational_solve (heatbath / action: R(A) Phi without per-shift solutions)
+    def rational_solve(self, Phi: torch.Tensor, alpha0: float, alpha: Sequence[float], beta: Sequence[float],
+                       tol: float, max_iter: int = 0, out=None, workspace: Optional[torch.Tensor] = None,
+                       allow_not_converged: bool = False):
+        n = Phi.shape[-1]
+        _check_field(Phi, "Phi", self.field_shape(n))
+        ns = len(beta)
+        if len(alpha) != ns:
+            raise ValueError("alpha and beta must have the same length")
+        Y = torch.empty_like(Phi) if out is None else out
+        buf = (ctypes.c_double * (ns * n))()
+        info = _lib.Info()
+        info.per_shift_resid = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
+        rc = self.lib.rhmc_rational_solve(self._h, _ptr(Phi), n, float(alpha0), _doubles(alpha), _doubles(beta), ns,
+                                          float(tol), int(max_iter), _ptr(Y), ws, ctypes.byref(info), _stream(Phi))
+        _lib.check(rc, "rhmc_rational_solve", allow=(2,) if allow_not_converged else ())
+        return Y, self._info(info, buf, ns, n)
+
     # -- rhmc_force
     def force(self, Phi: torch.Tensor, alpha0: float, alpha: Sequence[float], beta: Sequence[float], tol: float,
               precision: str = "mixed", X: Optional[torch.Tensor] = None, max_iter: int = 0, out=None,

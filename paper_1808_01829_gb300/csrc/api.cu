@@ -278,6 +278,7 @@ struct SolveBufs {
   double2 *gscratch;  // per-CTA Gram partials
   double *npart;
   SolverState *st;
+  int accumulate = 0;  // shifts s >= 1 add w_s X^(s) into one field after X^(0) (FP64)
 };
 
 static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, SolveBufs &b) {
@@ -336,6 +337,7 @@ struct SolveParams {
   bool mixed;
   int fixed_iters;  // > 0: exactly this many iterations, no freezing, no checks
   bool verify_at_convergence = true;  // mixed: reliable update before declaring convergence
+  const double *acc_w = nullptr;       // accumulating solve: weights of the shifts' solutions
 };
 
 struct SolveStats {
@@ -446,6 +448,9 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
     else if (cols)
       RHMC_TRY(update_shifts_cols((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                   b.st->upd, 1, ns, rows, n, len, ss));
+    else if (b.accumulate)
+      RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc + len, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows,
+                                 n, len, ss, 1));
     else
       RHMC_TRY(update_all<T, TX>(W, Qcur, P, (C<TX> *)Xacc, (const C<T> *)b.coef, b.st->upd, 1, ns, 0, rows, n, len,
                                  ss));
@@ -483,7 +488,7 @@ static rhmc_status_t run_chunk(rhmc_ctx *c, const SolveBufs &b, double2 *X, int 
 template <typename T>
 static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X, int n, int ns, double sigma0,
                                      int chunk_start, int len, double target, int freeze, cudaStream_t s) {
-  std::vector<double> key = {(double)(uintptr_t)b.P, (double)(uintptr_t)X, (double)n,
+  std::vector<double> key = {(double)(uintptr_t)b.P, (double)(uintptr_t)X, (double)b.accumulate, (double)n,
                              (double)ns, sigma0, target, (double)freeze, (double)sizeof(T), (double)len,
                              (double)(chunk_start % kCheckEvery)};
   for (int t = 0; t < TUNE_NKEYS; ++t) key.push_back((double)tune_get(t));
@@ -567,7 +572,8 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   const long len = rows * n;
   const double sigma0 = shifts[0];
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
-  RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * ns, s));
+  // accumulating solve: X^(0) and one field for sum_{s>=1} w_s X^(s)
+  RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * (b.accumulate ? std::min(ns, 2) : ns), s));
   // line 2: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
   if (mixed) {
     // the FP32 basis only needs FP32 orthonormality: QR of the rounded block
@@ -583,6 +589,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   for (int q = 0; q < ns; ++q)
     RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Qb[0], sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
   if (mixed) RHMC_CUDA_TRY(cudaMemsetAsync(b.Xinc, 0, sizeof(float2) * len * ns, s));
+  if (prm.acc_w) RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->w1, prm.acc_w, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   StateView v;
   RHMC_TRY(read_state(c, b.st, v, s));
   if (v.breakdown) {
@@ -1347,6 +1354,94 @@ rhmc_status_t rhmc_rational_apply(rhmc_ctx_t *c, const void *Phi, int n, double 
   cudaStream_t s = (cudaStream_t)sv;
   const long len = c->g.Vh * 3 * n;
   return rational_combine((const double2 *)Phi, alpha0, alpha, (const double2 *)X, ns, len, (double2 *)Y, s);
+}
+
+// R(A) Phi by the block multishift solve without per-shift solutions: FP64,
+// shifts sorted ascending, X^(0) kept (its true residual is checked), the
+// other shifts' solutions summed with their residues in the update kernel.
+rhmc_status_t rhmc_rational_solve(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, const double *alpha,
+                                  const double *beta, int ns, double tol, int max_iter, void *Y, void *ws,
+                                  rhmc_info_t *info, rhmc_stream_t sv) {
+  RHMC_TRY(check_common(c, Phi, Y, n));
+  if (!alpha || !beta || Phi == Y) {
+    set_error("rhmc_rational_solve: null alpha/beta or aliased Phi and Y");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  RHMC_TRY(check_shifts(ns, beta, tol));
+  DeviceGuard dg(c->device);
+  TuneScope tscope(c);
+  cudaStream_t s = (cudaStream_t)sv;
+  if (!ws) {
+    RHMC_TRY(ensure_pool(c, rhmc_rational_solve_bytes(c, n, ns)));
+    ws = c->pool;
+  }
+  const long len = c->g.Vh * 3 * n;
+  std::vector<int> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return beta[a] < beta[b]; });
+  std::vector<double> sh(ns), w(ns);
+  for (int q = 0; q < ns; ++q) {
+    sh[q] = beta[order[q]];
+    w[q] = alpha[order[q]];
+  }
+  Arena a(ws);
+  double2 *X2 = a.take<double2>((size_t)2 * len);  // X^(0), sum_{s>=1} w_s X^(s)
+  SolveBufs b;
+  layout_solve(a, c->g, n, ns, false, b);
+  b.accumulate = 1;
+  SolveParams prm{tol, max_iter > 0 ? max_iter : default_max_iter(c, sh[0], tol), false, 0};
+  prm.acc_w = w.data();
+  SolveStats st;
+  PhaseTimer timer(s);
+  const rhmc_status_t rc = solve_phase1<double>(c, (const double2 *)Phi, n, ns, sh.data(), X2, prm, b, st, s);
+  timer.mark();
+  if (rc != RHMC_OK && rc != RHMC_ERR_NOT_CONVERGED) return rc;
+  // recursive residuals of every shift, true FP64 residual of the base system
+  StateView v;
+  RHMC_TRY(read_state(c, b.st, v, s));
+  double rec = 0.0;
+  for (int q = 0; q < ns; ++q)
+    for (int j = 0; j < n; ++j) rec = std::max(rec, v.res[q][j]);
+  RHMC_TRY(apply_A<double>(c, X2, b.AP64, b.T64, n, sh[0], s));
+  RHMC_TRY(sub((const double2 *)Phi, b.AP64, b.R64, len, s));
+  double bn[kMaxN], rn[kMaxN];
+  RHMC_TRY(colnorms(c, (const double2 *)Phi, n, bn, b.npart, s));
+  RHMC_TRY(colnorms(c, b.R64, n, rn, b.npart, s));
+  double tr = 0.0;
+  for (int j = 0; j < n; ++j) tr = std::max(tr, std::sqrt(rn[j] / bn[j]));
+  // Y = alpha0 Phi + w_0 X^(0) + sum_{s>=1} w_s X^(s)
+  const double wts[2] = {w[0], 1.0};
+  RHMC_TRY(rational_combine((const double2 *)Phi, alpha0, wts, X2, ns > 1 ? 2 : 1, len, (double2 *)Y, s));
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  timer.mark();
+  if (info) {
+    double *user = info->per_shift_resid;
+    std::memset(info, 0, sizeof(*info));
+    info->per_shift_resid = user;
+    info->iters = st.iters;
+    info->dirac_calls = st.dirac + 1;
+    info->true_rel_resid_max = tr;
+    info->phase1_rel_resid_max = rec;
+    info->phase1_ms = timer.ms(0);
+    info->refine_ms = timer.ms(1);
+    if (user)
+      for (int q = 0; q < ns; ++q)
+        for (int j = 0; j < n; ++j) user[(size_t)order[q] * n + j] = v.res[q][j];
+  }
+  if (rc == RHMC_ERR_NOT_CONVERGED || rec > tol) {
+    set_error("rational solve: recursive residual %.3e above tol %.3e", rec, tol);
+    return RHMC_ERR_NOT_CONVERGED;
+  }
+  return RHMC_OK;
+}
+
+size_t rhmc_rational_solve_bytes(const rhmc_ctx_t *c, int n, int ns) {
+  if (!c || n < 1 || n > RHMC_MAX_NRHS || ns < 1 || ns > RHMC_MAX_SHIFTS) return 0;
+  Arena a(nullptr);
+  a.take<double2>((size_t)2 * c->g.Vh * 3 * n);
+  SolveBufs b;
+  layout_solve(a, c->g, n, ns, false, b);
+  return a.off + 256;
 }
 
 rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, const double *alpha,

@@ -290,7 +290,8 @@ template <typename T, typename TX, int N, int CG>
 __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, C<T> *__restrict__ Q,
                                                     C<T> *__restrict__ P, TX *__restrict__ Xv,
                                                     const C<T> *__restrict__ coef, const int *__restrict__ upd,
-                                                    int s_begin, int s_end, int compute_q, long rows, long fstride) {
+                                                    int s_begin, int s_end, int compute_q, long rows, long fstride,
+                                                    int acc) {
   constexpr int TPR = N / CG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T> *sc = reinterpret_cast<C<T> *>(smem_raw);  // rho^-1 (if compute_q), then the pairs of [s_begin, s_end)
@@ -350,12 +351,16 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
       while (from < s_end && !supd[from]) ++from;
       return from;
     };
+    // acc: X is one accumulator for all shifts (sum_s X^(s), the M1 already
+    // weighted), read once per row, summed in registers, written once
+    const long xs = acc ? 0 : fstride;
     int s = next_live(s_begin);
+    const bool touched = live && s < s_end;
     C<T> own[CG];
     CX ox[CG];
-    if (live && s < s_end) {
+    if (touched) {
       ld_slice<T, CG>(P + s * fstride + r * N + j0, own);
-      ld_slice<TX, CG>(X + s * fstride + r * N + j0, ox);
+      ld_slice<TX, CG>(X + s * xs + r * N + j0, ox);
     }
     while (s < s_end) {
       const int sn = next_live(s + 1);
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
       CX nox[CG];
       if (live && sn < s_end) {
         ld_slice<T, CG>(P + sn * fstride + r * N + j0, nown);
-        ld_slice<TX, CG>(X + sn * fstride + r * N + j0, nox);
+        if (!acc) ld_slice<TX, CG>(X + sn * xs + r * N + j0, nox);
       }
       const C<T> *m1 = sc + (1 + 2 * s) * N * N - c0;
       const C<T> *m2 = m1 + N * N;
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
           ox[c].y += a1[c].y;
           pn[c] = mk<T>(q[c].x + a2[c].x, q[c].y + a2[c].y);
         }
-        st_slice<TX, CG>(X + s * fstride + r * N + j0, ox);
+        if (!acc) st_slice<TX, CG>(X + s * xs + r * N + j0, ox);
         st_slice<T, CG>(P + s * fstride + r * N + j0, pn);
       }
       __syncwarp();
@@ -405,11 +410,12 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
 #pragma unroll
         for (int c = 0; c < CG; ++c) {
           own[c] = nown[c];
-          ox[c] = nox[c];
+          if (!acc) ox[c] = nox[c];
         }
       }
       s = sn;
     }
+    if (acc && touched) st_slice<TX, CG>(X + r * N + j0, ox);
   }
 }
 
@@ -1129,7 +1135,7 @@ template rhmc_status_t block_axpy<double, float>(const double2 *, const float2 *
 
 template <typename T, typename TX, int N>
 static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
-                          int s_end, int compute_q, long rows, long fstride, cudaStream_t s) {
+                          int s_end, int compute_q, long rows, long fstride, int acc, cudaStream_t s) {
   constexpr int CG = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 1);
   int threads = tune_get(TUNE_UPDATE_THREADS);
   if (threads <= 0 || threads > 256 || threads % 32) threads = 256;  // __launch_bounds__(256)
@@ -1144,12 +1150,12 @@ static void launch_update(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> 
   // persistent grid: as many CTAs as are resident at once (shared memory bound)
   grid = std::min(grid, (long)resident_ctas(k_update_all<T, TX, N, CG>, threads, smem));
   k_update_all<T, TX, N, CG><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, reinterpret_cast<TX *>(X), coef, upd,
-                                                                   s_begin, s_end, compute_q, rows, fstride);
+                                                                   s_begin, s_end, compute_q, rows, fstride, acc);
 }
 
 template <typename T, typename TX>
 rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
-                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s) {
+                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s, int acc) {
   if ((size_t)(1 + 2 * s_end) * n * n * sizeof(C<T>) > 220 * 1024) {
     set_error("update_all: %d shifts at n = %d exceed the shared-memory coefficient store", s_end, n);
     return RHMC_ERR_INVALID_ARG;
@@ -1163,7 +1169,7 @@ rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *
     for (int q = s_begin; q < s_end; ++q) nupd += h[q] != 0;
   }
   prof_begin(sizeof(T) == 4 ? PROF_UPDATE32 : PROF_UPDATE64, s);
-#define L_UPD(NN) launch_update<T, TX, NN>(W, Q, P, X, coef, upd, s_begin, s_end, compute_q, rows, fstride, s)
+#define L_UPD(NN) launch_update<T, TX, NN>(W, Q, P, X, coef, upd, s_begin, s_end, compute_q, rows, fstride, acc, s)
   RHMC_DISPATCH_N(n, L_UPD)
 #undef L_UPD
   prof_end(s, (double)rows * n * ((compute_q ? 2.0 : 1.0) * sizeof(C<T>) + nupd * 2.0 * (sizeof(C<T>) + sizeof(C<TX>))));
@@ -1171,9 +1177,9 @@ rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *
   return RHMC_OK;
 }
 template rhmc_status_t update_all<float, float>(const float2 *, float2 *, float2 *, float2 *, const float2 *,
-                                                const int *, int, int, int, long, int, long, cudaStream_t);
+                                                const int *, int, int, int, long, int, long, cudaStream_t, int);
 template rhmc_status_t update_all<double, double>(const double2 *, double2 *, double2 *, double2 *, const double2 *,
-                                                  const int *, int, int, int, long, int, long, cudaStream_t);
+                                                  const int *, int, int, int, long, int, long, cudaStream_t, int);
 
 rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s) {
   const int bs = 256;

@@ -24,6 +24,7 @@ struct SolverState {
   double sigma[kMaxS];        // shifts, ascending
   double d0[kMaxN];           // ||B e_j||
   double inv_d0[kMaxN];       // 1 / ||B e_j||
+  double w1[kMaxS];           // weight of shift s's solution update (accumulating solves), 1 otherwise
   double res[kMaxS][kMaxN];   // recursive relative residual per shift and column (s = 0: base)
   int active[kMaxS];          // shift still being updated
   int upd[kMaxS];             // shift updated in the current iteration
@@ -56,7 +57,7 @@ rhmc_status_t block_axpy(const C<TA> *A, const C<TY> *Cin, const C<TA> *M, C<TY>
 // compute_q: first form Q = W rho^-1 (and store it); otherwise read Q.
 template <typename T, typename TX>
 rhmc_status_t update_all(const C<T> *W, C<T> *Q, C<T> *P, C<TX> *X, const C<T> *coef, const int *upd, int s_begin,
-                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s);
+                         int s_end, int compute_q, long rows, int n, long fstride, cudaStream_t s, int acc = 0);
 rhmc_status_t flush(double2 *X64, float2 *X32, long len, cudaStream_t s);
 
 // update_tc.cu: shifted updates on the tensor cores (mixed path, n = 16)

@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
   if (c.t < nshift) {
     st->active[c.t] = 1;
     st->upd[c.t] = 0;
+    st->w1[c.t] = 1.0;
     for (int j = 0; j < n; ++j) st->res[c.t][j] = 1.0;
   }
   if (c.t == 0) {
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   mm(c, A1, Bi, Cp);
   mm(c, A2, A1, st->alpha_s[s]);
   // M1 = alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12)
-  store_coef<T>(c, coef + (1 + 2 * s) * nn, A2);
+  store_coef<T>(c, coef + (1 + 2 * s) * nn, A2, st->w1[s]);
   mm(c, A1, Bi, st->rho[cur], false, true);
   store_coef<T>(c, coef + (2 + 2 * s) * nn, A1);
   if (c.own) {

@@ -247,6 +247,8 @@ STANDARD = [
     (-1.0 / 32, 2e-3, 64.0, 12),   # batched ensemble, n_pf = 8
     (-1.0 / 48, 2e-3, 64.0, 12),   # batched ensemble, n_pf = 12
     (-1.0 / 64, 2e-3, 64.0, 12),   # batched ensemble, n_pf = 16
+    (1.0 / 16, 1e-3, 64.0, 8),     # heatbath x^(+1/(8 n_pf)), 4^4, n_pf = 2
+    (1.0 / 32, 2e-3, 64.0, 12),    # heatbath, 8^4, n_pf = 4
 ]
 
 
