@@ -302,6 +302,14 @@ enum {
   RHMC_TUNE_REFINE_LANES = 9
 };
 
+/* Self-test of the device-side timeout path used by kernels that wait on
+ * mbarriers (the tensor-core update): one warp on `device` waits for an
+ * mbarrier phase that nothing completes; the wait gives up after about
+ * `seconds` (0 < seconds <= 2) and the call returns RHMC_ERR_DEVICE_TIMEOUT
+ * with the context usable afterwards.  Any other status means the timeout
+ * path is broken. */
+rhmc_status_t rhmc_selftest_bounded_wait(int device, double seconds, rhmc_stream_t s);
+
 /* The same settings for one context only (they take precedence over the
  * process-wide ones in every call on ctx, including the concurrent solves of
  * rhmc_block_multishift_cg_batch, so each ensemble can run its own tuned

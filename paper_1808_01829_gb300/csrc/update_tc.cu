@@ -35,7 +35,6 @@ constexpr int kTcRows = 128;         // tile rows (MMA M)
 constexpr int kTcK = 32;             // reals per row (MMA K)
 constexpr int kTcN = 64;             // output reals per row (MMA N): M1 | M2
 constexpr int kTcCols = 64;          // tensor-memory columns allocated
-constexpr long kWaitLimit = 1L << 24;
 
 // Byte offset of (row, k) in a K-major tile of 32-bit elements with 128-byte
 // rows under the 128-byte swizzle: 16-byte chunk c of row r sits at chunk
@@ -86,6 +85,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+
+// Wait for phase `parity` of the mbarrier at addr for at most `cycles` SM
+// clocks; false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait_for(unsigned addr, unsigned parity, long long cycles) {
+  if (mbar_try_wait(addr, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(addr, parity))
+    if (clock64() - t0 > cycles) return false;
+  return true;
+}
+constexpr long long kWaitCycles = 2000000000LL;  // about a second at the GPU's 2 GHz
 
 #define RHMC_TMEM_LD64(taddr, v)                                                                                      \
   asm volatile(                                                                                                       \
@@ -224,17 +234,12 @@ __global__ void __launch_bounds__(kTcRows, 4) k_update_tc(const float2 *__restri
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
                      : "memory");
-        long it = 0;
-        while (!mbar_try_wait(mbar_addr, phase) && ++it < kWaitLimit) {
-        }
-        if (it >= kWaitLimit) {
+        if (!mbar_wait_for(mbar_addr, phase, kWaitCycles)) {
           ok_sh = 0;
           atomicExch(err, 1);
           // give the MMAs in flight one more bounded chance to land before the
           // tensor memory is released
-          it = 0;
-          while (!mbar_try_wait(mbar_addr, phase) && ++it < kWaitLimit) {
-          }
+          mbar_wait_for(mbar_addr, phase, kWaitCycles);
         }
       }
       __syncthreads();
@@ -298,4 +303,57 @@ rhmc_status_t update_shifts_tc(const float2 *Q, float2 *P, float2 *X, const floa
   return RHMC_OK;
 }
 
+
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives at; the wait must give up after `cycles` clocks and set *err.
+__global__ void k_wait_selftest(int *err, long long cycles) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned addr = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (!mbar_wait_for(addr, 0, cycles) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 }  // namespace rhmc
+
+extern "C" rhmc_status_t rhmc_selftest_bounded_wait(int device, double seconds, rhmc_stream_t sv) {
+  using namespace rhmc;
+  if (!(seconds > 0.0 && seconds <= 2.0)) {
+    set_error("rhmc_selftest_bounded_wait: seconds must be in (0, 2]");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) RHMC_CUDA_TRY(cudaSetDevice(device));
+  int khz = 0;
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+  const long long cycles = (long long)(seconds * (khz > 0 ? khz : 2000000) * 1e3);
+  int *flag = nullptr;
+  rhmc_status_t rc = RHMC_OK;
+  cudaStream_t s = (cudaStream_t)sv;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+    set_error("rhmc_selftest_bounded_wait: cudaMalloc failed");
+    rc = RHMC_ERR_CUDA;
+  } else {
+    int h = 0;
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    k_wait_selftest<<<1, 32, 0, s>>>(flag, cycles);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess) {
+      if (h) {
+        set_error("bounded device wait expired (self-test: nothing arrives at the barrier)");
+        rc = RHMC_ERR_DEVICE_TIMEOUT;
+      }
+    } else {
+      set_error("rhmc_selftest_bounded_wait: %s", cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
+      rc = RHMC_ERR_CUDA;
+    }
+    cudaFree(flag);
+  }
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return rc;
+}
