@@ -285,6 +285,10 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 thread; 4: two, even n); tiles staged in shared memory by
  *                                 cp.async, even n (1); register staged with one direction of
  *                                 prefetch (2)
+ *   RHMC_TUNE_LINKS12             1: the FP32 hop reads the first two rows of each link and
+ *                                 rebuilds the third (only when rhmc_set_gauge found every link
+ *                                 in SU(3) to FP32 accuracy); 0, 2: full records (built-in;
+ *                                 measured no faster at 24^4, n = 16)
  *   RHMC_TUNE_REFINE_LANES        defect corrections of different shifts run concurrently on
  *                                 up to this many streams, one host thread each (0: 4, the
  *                                 most; 1: in turn on the caller's stream)
@@ -299,7 +303,8 @@ enum {
   RHMC_TUNE_UPDATE_TENSOR = 6,
   RHMC_TUNE_GRAPHS = 7,
   RHMC_TUNE_HOP_STAGED = 8,
-  RHMC_TUNE_REFINE_LANES = 9
+  RHMC_TUNE_REFINE_LANES = 9,
+  RHMC_TUNE_LINKS12 = 10
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

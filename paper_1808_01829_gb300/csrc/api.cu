@@ -164,6 +164,8 @@ struct rhmc_ctx {
   double2 *l64[2] = {nullptr, nullptr};
   float2 *l32[2] = {nullptr, nullptr};
   float4 *ldf[2] = {nullptr, nullptr};  // double-float copy of the FP64 link records
+  float2 *l12[2] = {nullptr, nullptr};  // first two rows of the FP32 records (used when every link is SU(3))
+  bool rec12 = false;
   bool have_gauge = false;
   void *pool = nullptr;
   size_t pool_bytes = 0;
@@ -234,13 +236,25 @@ template <> struct LinksOf<float> {
 template <> struct LinksOf<double> {
   static const double2 *get(const rhmc_ctx *c, int p) { return c->l64[p]; }
 };
+template <typename T> struct Links12Of;
+template <> struct Links12Of<float> {
+  static const float2 *get(const rhmc_ctx *c, int p) {
+    // opt-in: at 24^4, n = 16 the rebuild costs what the 128 fewer bytes per site save
+    return (c->rec12 && tune_get(TUNE_LINKS12) == 1) ? c->l12[p] : nullptr;
+  }
+};
+template <> struct Links12Of<double> {
+  static const double2 *get(const rhmc_ctx *, int) { return nullptr; }
+};
 
 // Y = (A + sigma) X, tmp: odd-parity field of the same width.
 template <typename T>
 static rhmc_status_t apply_A(const rhmc_ctx *c, const C<T> *X, C<T> *Y, C<T> *tmp, int n, double sigma,
                              cudaStream_t s) {
-  RHMC_TRY(hop<T>(c->g, 1, LinksOf<T>::get(c, 1), X, tmp, nullptr, 0.0, n, 1, 0, s));
-  RHMC_TRY(hop<T>(c->g, 0, LinksOf<T>::get(c, 0), tmp, Y, X, 4.0 * c->mass * c->mass + sigma, n, 1, 0, s));
+  RHMC_TRY(hop<T>(c->g, 1, LinksOf<T>::get(c, 1), X, tmp, nullptr, 0.0, n, 1, 0, s, Links12Of<T>::get(c, 1),
+                  c->bc_t));
+  RHMC_TRY(hop<T>(c->g, 0, LinksOf<T>::get(c, 0), tmp, Y, X, 4.0 * c->mass * c->mass + sigma, n, 1, 0, s,
+                  Links12Of<T>::get(c, 0), c->bc_t));
   return RHMC_OK;
 }
 
@@ -962,7 +976,8 @@ rhmc_status_t rhmc_create(rhmc_ctx_t **out, const rhmc_lattice_t *lat, int devic
   for (int p = 0; p < 2; ++p) {
     if (cudaMalloc(&c->l64[p], sizeof(double2) * 72 * c->g.Vh) != cudaSuccess ||
         cudaMalloc(&c->l32[p], sizeof(float2) * 72 * c->g.Vh) != cudaSuccess ||
-        cudaMalloc(&c->ldf[p], sizeof(float4) * 72 * c->g.Vh) != cudaSuccess) {
+        cudaMalloc(&c->ldf[p], sizeof(float4) * 72 * c->g.Vh) != cudaSuccess ||
+        cudaMalloc(&c->l12[p], sizeof(float2) * 48 * c->g.Vh) != cudaSuccess) {
       set_error("rhmc_create: out of device memory for links");
       rhmc_destroy(c);
       return RHMC_ERR_CUDA;
@@ -997,6 +1012,7 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
     if (c->l64[p]) cudaFree(c->l64[p]);
     if (c->l32[p]) cudaFree(c->l32[p]);
     if (c->ldf[p]) cudaFree(c->ldf[p]);
+    if (c->l12[p]) cudaFree(c->l12[p]);
   }
   if (c->side) cudaStreamSynchronize(c->side);
   for (auto &l : c->lanes) {
@@ -1026,6 +1042,7 @@ rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *c, const void *U, rhmc_stream_t sv) {
   cudaStream_t s = (cudaStream_t)sv;
   RHMC_TRY(stage_links(c->g, (const double2 *)U, c->bc_t, c->l64, c->l32, s));
   for (int p = 0; p < 2; ++p) RHMC_TRY(stage_links_df(c->g, c->l64[p], c->ldf[p], s));
+  RHMC_TRY(stage_links12(c->g, c->bc_t, c->l32, c->l12, &c->rec12, s));
   RHMC_CUDA_TRY(cudaStreamSynchronize(s));
   c->have_gauge = true;
   return RHMC_OK;
@@ -1109,7 +1126,8 @@ rhmc_status_t rhmc_hop(rhmc_ctx_t *c, const void *X, void *Y, int n, int out_par
   Arena a(c->pool);
   float2 *x32 = a.take<float2>(len), *y32 = a.take<float2>(len);
   RHMC_TRY((convert<double, float>((const double2 *)X, x32, len, s)));
-  RHMC_TRY(hop<float>(c->g, out_par, c->l32[out_par], x32, y32, nullptr, 0, n, 1, 0, s));
+  RHMC_TRY(hop<float>(c->g, out_par, c->l32[out_par], x32, y32, nullptr, 0, n, 1, 0, s,
+                      Links12Of<float>::get(c, out_par), c->bc_t));
   RHMC_TRY((convert<float, double>(y32, (double2 *)Y, len, s)));
   return RHMC_OK;
 }

@@ -10,6 +10,7 @@
 // site needs are contiguous: a CTA stages the records of its site tile into
 // shared memory with coalesced 16-byte loads and every thread of the tile (one
 // per (site, right-hand side)) reads them from there.
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -63,6 +64,72 @@ rhmc_status_t stage_links(const Geom &g, const double2 *U, int bc_t, double2 *l6
     RHMC_LAUNCH_CHECK();
   }
   return RHMC_OK;
+}
+
+// Coordinates of the site with parity `par` and parity rank h, 32-bit
+// arithmetic (V/2 < 2^31): x = 2 xh + (parity of y + z + t xor par).
+__device__ __forceinline__ void site_coords32(const Geom &g, int par, int h, int &x0, int &x1, int &x2, int &x3) {
+  const int r = h / g.Lxh;
+  const int xh = h - r * g.Lxh;
+  const int r2 = r / g.L[1];
+  x1 = r - r2 * g.L[1];
+  x3 = r2 / g.L[2];
+  x2 = r2 - x3 * g.L[2];
+  x0 = 2 * xh + (((x1 + x2 + x3) & 1) ^ par);
+}
+
+// ------------------------------------------------------------ 12-real links
+// A link record L = f V with V in SU(3) and f = +-1 (f = eta b for the forward
+// links, f = -eta b for the daggered backward ones) is determined by its first
+// two rows: row 3 = f conj(row 1 x row 2).  The FP32 hop can therefore read 6
+// of the 9 complex entries (384 instead of 576 bytes per site) and rebuild the
+// third rows in shared memory.  The sign of record d of the site with parity
+// `par` and coordinates x:
+__device__ __forceinline__ float link_sign(const Geom &g, int bc_t, int d, int x0, int x1, int x2, int x3) {
+  const int mu = d & 3;
+  const int ps = mu == 0 ? 0 : mu == 1 ? x0 : mu == 2 ? x0 + x1 : x0 + x1 + x2;
+  float f = (ps & 1) ? -1.f : 1.f;  // eta_mu(x)
+  if (d < 4) {
+    if (mu == 3 && bc_t == -1 && x3 == g.L[3] - 1) f = -f;  // b_mu(x)
+  } else {
+    if (mu == 3 && bc_t == -1 && x3 == 0) f = -f;  // b_mu(x - mu)
+    f = -f;
+  }
+  return f;
+}
+
+__device__ __forceinline__ float2 cross_conj(float2 a1, float2 a2, float2 b1, float2 b2) {
+  // conj(a1 b2 - a2 b1)
+  const float re = a1.x * b2.x - a1.y * b2.y - (a2.x * b1.x - a2.y * b1.y);
+  const float im = a1.x * b2.y + a1.y * b2.x - (a2.x * b1.y + a2.y * b1.x);
+  return make_float2(re, -im);
+}
+
+// first two rows of every FP32 record; *dev_max = largest |row 3 - rebuilt row 3|
+__global__ void k_links12(Geom g, int par, int bc_t, const float2 *__restrict__ l32, float2 *__restrict__ l12,
+                          unsigned *dev_max) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;  // (site, d)
+  if (k >= g.Vh * 8) return;
+  const int h = (int)(k >> 3), d = (int)(k & 7);
+  const float2 *L = l32 + k * 9;
+  float2 r[6];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    r[e] = L[e];
+    l12[k * 6 + e] = r[e];
+  }
+  int x0, x1, x2, x3;
+  site_coords32(g, par, h, x0, x1, x2, x3);
+  const float f = link_sign(g, bc_t, d, x0, x1, x2, x3);
+  float dev = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    const float2 t = cross_conj(r[c1], r[c2], r[3 + c1], r[3 + c2]);
+    const float2 w = L[6 + c];
+    dev = fmaxf(dev, fmaxf(fabsf(w.x - f * t.x), fabsf(w.y - f * t.y)));
+  }
+  atomicMax(dev_max, __float_as_uint(dev));  // non-negative floats order as their bit patterns
 }
 
 // ------------------------------------------------------------ hop
@@ -254,33 +321,24 @@ static void launch_hop(const Geom &g, int par, const C<T> *links, const C<T> *in
 // 200 bytes per thread in flight) before it multiplies anything, so the
 // latency of the gathered reads is paid once per site instead of once per
 // direction.
-// Coordinates of the site with parity `par` and parity rank h, 32-bit
-// arithmetic (V/2 < 2^31): x = 2 xh + (parity of y + z + t xor par).
-__device__ __forceinline__ void site_coords32(const Geom &g, int par, int h, int &x0, int &x1, int &x2, int &x3) {
-  const int r = h / g.Lxh;
-  const int xh = h - r * g.Lxh;
-  const int r2 = r / g.L[1];
-  x1 = r - r2 * g.L[1];
-  x3 = r2 / g.L[2];
-  x2 = r2 - x3 * g.L[2];
-  x0 = 2 * xh + (((x1 + x2 + x3) & 1) ^ par);
-}
-
-template <int N, int R, bool SELF>
+template <int N, int R, bool SELF, bool REC>
 __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *__restrict__ links,
                                                 const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                const float2 *__restrict__ self, float a) {
+                                                const float2 *__restrict__ self, float a, int bc_t) {
   constexpr int TPS = N / R;                                 // threads per site
   constexpr int TILE = (128 / TPS) < 32 ? (128 / TPS) : 32;  // sites per CTA (static shared memory <= 20 KB)
+  constexpr int LR = REC ? 48 : 72;  // complex per site record as stored
   __shared__ __align__(16) float2 sl[TILE * 72];
+  __shared__ __align__(16) float2 sl12[REC ? TILE * 48 : 1];
+  __shared__ float sgn[REC ? TILE * 8 : 1];
   __shared__ int snb[TILE * 8];
   const int tid = threadIdx.x;
   const int h0 = blockIdx.x * TILE;
   const int nsites = min(TILE, (int)g.Vh - h0);
   {
-    const unsigned base = (unsigned)__cvta_generic_to_shared(sl);
-    const char *src = reinterpret_cast<const char *>(links + (long)h0 * 72);
-    for (int c = tid; c < nsites * 36; c += blockDim.x)
+    const unsigned base = (unsigned)__cvta_generic_to_shared(REC ? sl12 : sl);
+    const char *src = reinterpret_cast<const char *>(links + (long)h0 * LR);
+    for (int c = tid; c < nsites * (LR / 2); c += blockDim.x)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * c), "l"(src + 16L * c) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
@@ -288,6 +346,7 @@ __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *_
     const int site = k >> 3, d = k & 7;
     int y0, y1, y2, y3;
     site_coords32(g, par, h0 + site, y0, y1, y2, y3);
+    if (REC) sgn[k] = link_sign(g, bc_t, d, y0, y1, y2, y3);
     const int mu = d & 3;
     const bool fwd = d < 4;
     if (mu == 0) y0 = fwd ? (y0 + 1 == g.L[0] ? 0 : y0 + 1) : (y0 == 0 ? g.L[0] - 1 : y0 - 1);
@@ -311,6 +370,22 @@ __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *_
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
+  if (REC) {  // full records from the first two rows: row 3 = f conj(row 1 x row 2)
+    for (int e = tid; e < nsites * 8; e += blockDim.x) {
+      const float2 *r = sl12 + e * 6;
+      float2 *o = sl + (e >> 3) * 72 + (e & 7) * 9;
+      const float f = sgn[e];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) o[c] = r[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        const float2 t = cross_conj(r[c1], r[c2], r[3 + c1], r[3 + c2]);
+        o[6 + c] = make_float2(f * t.x, f * t.y);
+      }
+    }
+    __syncthreads();
+  }
   if (!live) return;
   float2 acc[3][R];
 #pragma unroll
@@ -345,19 +420,25 @@ __global__ void __launch_bounds__(128) k_hop_pf(Geom g, int par, const float2 *_
 
 template <int N, int R>
 static void launch_hop_pf_n(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
-                            const float2 *self, double a, cudaStream_t s) {
+                            const float2 *self, double a, const float2 *links12, int bc_t, cudaStream_t s) {
   constexpr int TPS = N / R;
   constexpr int TILE = (128 / TPS) < 32 ? (128 / TPS) : 32;
   const int threads = ((TILE * TPS + 31) / 32) * 32;
   const unsigned grid = (unsigned)((g.Vh + TILE - 1) / TILE);
-  if (self)
-    k_hop_pf<N, R, true><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
-  else
-    k_hop_pf<N, R, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a);
+  if (links12) {
+    if (self)
+      k_hop_pf<N, R, true, true><<<grid, threads, 0, s>>>(g, par, links12, in, out, self, (float)a, bc_t);
+    else
+      k_hop_pf<N, R, false, true><<<grid, threads, 0, s>>>(g, par, links12, in, out, self, (float)a, bc_t);
+  } else if (self) {
+    k_hop_pf<N, R, true, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a, bc_t);
+  } else {
+    k_hop_pf<N, R, false, false><<<grid, threads, 0, s>>>(g, par, links, in, out, self, (float)a, bc_t);
+  }
 }
 
 static bool launch_hop_pf(const Geom &g, int par, const float2 *links, const float2 *in, float2 *out,
-                          const float2 *self, double a, int n, cudaStream_t s) {
+                          const float2 *self, double a, int n, const float2 *links12, int bc_t, cudaStream_t s) {
   // two right-hand sides per thread (16-byte loads, half the load instructions): built-in
   // for even n >= 12 (measured at 24^4: n = 16 65 us against 71 us; n = 8 no gain)
   const int mode = tune_get(TUNE_HOP_STAGED);
@@ -367,11 +448,11 @@ static bool launch_hop_pf(const Geom &g, int par, const float2 *links, const flo
   case NN:                                                                         \
     if constexpr (NN % 2 == 0) {                                                   \
       if (r2) {                                                                    \
-        launch_hop_pf_n<NN, 2>(g, par, links, in, out, self, a, s);                \
+        launch_hop_pf_n<NN, 2>(g, par, links, in, out, self, a, links12, bc_t, s); \
         return true;                                                               \
       }                                                                            \
     }                                                                              \
-    launch_hop_pf_n<NN, 1>(g, par, links, in, out, self, a, s);                    \
+    launch_hop_pf_n<NN, 1>(g, par, links, in, out, self, a, links12, bc_t, s);     \
     return true;
     L_PF(1) L_PF(2) L_PF(3) L_PF(4) L_PF(5) L_PF(6) L_PF(7) L_PF(8)
     L_PF(9) L_PF(10) L_PF(11) L_PF(12) L_PF(13) L_PF(14) L_PF(15) L_PF(16)
@@ -590,7 +671,7 @@ static bool try_hop_staged(const Geom &g, int par, const C<T> *links, const C<T>
 
 template <typename T>
 rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
-                  int n, int nbatch, long bstride, cudaStream_t s) {
+                  int n, int nbatch, long bstride, cudaStream_t s, const C<T> *links12, int bc_t) {
   if (n < 1 || n > RHMC_MAX_NRHS || g.Vh * 3L * n > 0x7fffffffL) return RHMC_ERR_INVALID_ARG;
   prof_begin(sizeof(T) == 4 ? PROF_HOP32 : PROF_HOP64, s);
   int R = tune_get(TUNE_HOP_RHS_PER_THREAD);
@@ -599,7 +680,8 @@ rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T
   if (try_hop_staged<T>(g, par, links, in, out, self, a, n, nbatch, R, s)) {
   } else if (use_hop_pf<T>(links, in, nbatch)) {
     launch_hop_pf(g, par, reinterpret_cast<const float2 *>(links), reinterpret_cast<const float2 *>(in),
-                  reinterpret_cast<float2 *>(out), reinterpret_cast<const float2 *>(self), a, n, s);
+                  reinterpret_cast<float2 *>(out), reinterpret_cast<const float2 *>(self), a, n,
+                  reinterpret_cast<const float2 *>(links12), bc_t, s);
   } else if (R == 4)
     launch_hop<T, 4>(g, par, links, in, out, self, a, n, nbatch, bstride, s);
   else if (R == 2)
@@ -733,8 +815,30 @@ rhmc_status_t hop_df(const Geom &g, int par, const float4 *links, const float4 *
 }
 
 template rhmc_status_t hop<float>(const Geom &, int, const float2 *, const float2 *, float2 *, const float2 *, double,
-                                  int, int, long, cudaStream_t);
+                                  int, int, long, cudaStream_t, const float2 *, int);
 template rhmc_status_t hop<double>(const Geom &, int, const double2 *, const double2 *, double2 *, const double2 *,
-                                   double, int, int, long, cudaStream_t);
+                                   double, int, int, long, cudaStream_t, const double2 *, int);
+
+// 12-real copies of the FP32 records; returns through *ok whether every record
+// is f V with V in SU(3) to FP32 accuracy (then the hop may use the copies).
+rhmc_status_t stage_links12(const Geom &g, int bc_t, float2 *const l32[2], float2 *l12[2], bool *ok,
+                            cudaStream_t s) {
+  unsigned *dmax = nullptr;
+  RHMC_CUDA_TRY(cudaMallocAsync(&dmax, sizeof(unsigned), s));
+  RHMC_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned), s));
+  const long items = g.Vh * 8;
+  for (int p = 0; p < 2; ++p) {
+    k_links12<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(g, p, bc_t, l32[p], l12[p], dmax);
+    RHMC_LAUNCH_CHECK();
+  }
+  unsigned h = 0;
+  RHMC_CUDA_TRY(cudaMemcpyAsync(&h, dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+  RHMC_CUDA_TRY(cudaFreeAsync(dmax, s));
+  float dev = 0.f;
+  std::memcpy(&dev, &h, sizeof(float));
+  *ok = dev < 1e-5f;
+  return RHMC_OK;
+}
 
 }  // namespace rhmc

@@ -35,9 +35,12 @@ struct SolverState {
 // dslash.cu
 rhmc_status_t stage_links(const Geom &g, const double2 *U, int bc_t, double2 *l64[2], float2 *l32[2],
                           cudaStream_t s);
+// links12: optional 12-real copy of `links` (FP32 single-field hops use it), bc_t
+// its boundary condition (signs of the rebuilt third rows)
 template <typename T>
 rhmc_status_t hop(const Geom &g, int par, const C<T> *links, const C<T> *in, C<T> *out, const C<T> *self, double a,
-                  int n, int nbatch, long bstride, cudaStream_t s);
+                  int n, int nbatch, long bstride, cudaStream_t s, const C<T> *links12 = nullptr, int bc_t = -1);
+rhmc_status_t stage_links12(const Geom &g, int bc_t, float2 *const l32[2], float2 *l12[2], bool *ok, cudaStream_t s);
 
 // double-float (FP64-accurate, FP32 units) operator pieces
 rhmc_status_t stage_links_df(const Geom &g, const double2 *l64, float4 *ldf, cudaStream_t s);

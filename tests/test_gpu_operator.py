@@ -147,3 +147,28 @@ def test_errors_are_reported():
     with pytest.raises(ValueError):
         ctx.apply_mdagm_mrhs(X.to(torch.complex64))
     ctx.close()
+
+
+@pytest.mark.parametrize("bc", [-1, 1])
+def test_fp32_hop_12_real_links(bc):
+    """SU(3) links: the FP32 hop reading two rows per link and rebuilding the third
+    (with the staggered phase and boundary sign) agrees with the full records and the
+    oracle; links off SU(3) must not take that path."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n, sigma = (4, 6, 4, 8), 0.05, 16, 0.13
+    X = syn.gaussian_pseudofermions(dims, n, 2104)
+    for scale in (1.0, 1.05):
+        U = syn.random_links(dims, 0.5, 1104) * scale
+        ref = oracle.apply_A(dims, mass, U, X, sigma=sigma, bc_t=bc)
+        ctx = make_ctx(dims, mass, U, bc)
+        try:
+            for mode in (1, 0):
+                lib.rhmc_tune_set(10, mode)
+                got = ctx.apply_mdagm_mrhs(to_gpu(X), sigma, "fp32").cpu().numpy()
+                assert colrel(got, ref) <= 1e-6, (scale, mode)
+        finally:
+            lib.rhmc_tune_set(10, 0)
+        ctx.close()
