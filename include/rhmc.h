@@ -289,6 +289,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 rebuilds the third (only when rhmc_set_gauge found every link
  *                                 in SU(3) to FP32 accuracy); 0, 2: full records (built-in;
  *                                 measured no faster at 24^4, n = 16)
+ *   RHMC_TUNE_SHIFT_FREEZE_NANO   mixed precision: shifted systems stop being updated once their
+ *                                 recursive residuals are below max(tol, value x 1e-9)
+ *                                 (0: tol, built-in)
  *   RHMC_TUNE_REFINE_LANES        defect corrections of different shifts run concurrently on
  *                                 up to this many streams, one host thread each (0: 4, the
  *                                 most; 1: in turn on the caller's stream)
@@ -304,7 +307,8 @@ enum {
   RHMC_TUNE_GRAPHS = 7,
   RHMC_TUNE_HOP_STAGED = 8,
   RHMC_TUNE_REFINE_LANES = 9,
-  RHMC_TUNE_LINKS12 = 10
+  RHMC_TUNE_LINKS12 = 10,
+  RHMC_TUNE_SHIFT_FREEZE_NANO = 11
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

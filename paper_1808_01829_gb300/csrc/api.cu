@@ -107,6 +107,7 @@ constexpr int kCheckEvery = 6;        // iterations between host checks (a multi
                                       // k % 2 and k % 3 slot pattern of a captured chunk fixed)
 constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
+constexpr double kShiftFreezeMixed = 0.0;  // built-in freeze level of the shifted systems (mixed)
 constexpr int kRefineLanes = 4;       // concurrent defect corrections (built-in and most; 8 measured 2 % faster)
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
@@ -611,6 +612,14 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     return RHMC_ERR_BREAKDOWN;
   }
   const double target = prm.tol;
+  // Shifted systems freeze once their recursive residuals are below
+  // max(tol, RHMC_TUNE_SHIFT_FREEZE_NANO x 1e-9) in mixed precision.  Built-in:
+  // tol.  Freezing earlier (their true residuals stop near the FP32 drift level)
+  // shortens phase 1 but costs more in the corrections: at 24^4, n = 16, 1e-6
+  // gave 211 + 256 ms against 235 + 158 ms (the large shifts drift little when
+  // run to tol and then need almost no correction).
+  const int fz = tune_get(TUNE_SHIFT_FREEZE_NANO);
+  const double tol_shift = mixed ? std::max(target, fz > 0 ? 1e-9 * fz : kShiftFreezeMixed) : target;
   double res_at_reliable = 1.0;
   const int check_every = tune_get(TUNE_CHECK_EVERY) > 0 ? tune_get(TUNE_CHECK_EVERY) : kCheckEvery;
   const int flush_every = tune_get(TUNE_FLUSH_EVERY);
@@ -624,9 +633,9 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     const bool graph = use_graphs() && chunk == kCheckEvery && check_every == kCheckEvery && k > 0 &&
                        k % kCheckEvery == 0;
     if (graph)
-      RHMC_TRY(run_chunk_graph<T>(c, b, X, n, ns, sigma0, k, chunk, target, freeze, s));
+      RHMC_TRY(run_chunk_graph<T>(c, b, X, n, ns, sigma0, k, chunk, tol_shift, freeze, s));
     else
-      RHMC_TRY(run_chunk<T>(c, b, X, n, ns, sigma0, k, chunk, target, freeze, s));
+      RHMC_TRY(run_chunk<T>(c, b, X, n, ns, sigma0, k, chunk, tol_shift, freeze, s));
     k += chunk;
     stats.dirac += chunk;
     RHMC_TRY(read_state(c, b.st, v, s));

@@ -117,6 +117,7 @@ enum TuneKey {
   TUNE_HOP_STAGED,            // FP32 hop with cp.async-staged tiles: built-in (0), always (1), never (2)
   TUNE_REFINE_LANES,          // concurrent per-shift defect corrections (0: built-in 4)
   TUNE_LINKS12,               // FP32 hop reads 12-real links when all links are SU(3) (1); full records (0, 2)
+  TUNE_SHIFT_FREEZE_NANO,     // mixed: freeze shifted systems below this recursive residual (x 1e-9; 0: built-in)
   TUNE_NKEYS
 };
 int tune_get(int key);
