@@ -76,10 +76,9 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1808_01829_gb300 import replicas
+
+    return replicas.env()
 
 
 class ClockSampler:
@@ -263,12 +262,11 @@ def run_gpu(args):
     import numpy as np
     import torch
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1808_01829_gb300 import replicas
 
-        dist.init_process_group("nccl")
+    rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    replicas.init("nccl")
     dev = torch.device("cuda", local)
     from paper_1808_01829_gb300 import _build
     from paper_1808_01829_gb300.api import RhmcContext
@@ -300,8 +298,7 @@ def run_gpu(args):
     infos = []
     for _ in range(args.warmup):
         infos.append(step()[2])
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -316,11 +313,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = int(lib.rhmc_kernel_launches() - l0)
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    replicas.barrier()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     last = infos[-1]
 
     # ---- end to end: pinned host Phi -> device, force, G -> pinned host
@@ -385,6 +379,7 @@ def run_gpu(args):
         len_b = Phi.nbytes
         line = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "force_evals_per_s": world * 1000.0 / ms,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": cfg["workload"], "precision": cfg["precision"],
@@ -407,8 +402,7 @@ def run_gpu(args):
         }
         print(json.dumps(line))
     ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    replicas.finalize()
 
 
 if __name__ == "__main__":
