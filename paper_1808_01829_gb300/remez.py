@@ -249,6 +249,12 @@ STANDARD = [
     (-1.0 / 64, 2e-3, 64.0, 12),   # batched ensemble, n_pf = 16
     (1.0 / 16, 1e-3, 64.0, 8),     # heatbath x^(+1/(8 n_pf)), 4^4, n_pf = 2
     (1.0 / 32, 2e-3, 64.0, 12),    # heatbath, 8^4, n_pf = 4
+    # convergence study (studies.py): x^(-1/(4 n_pf)), n_pf = 1, 2, 4, 8, 16
+    (-1.0 / 4, 2e-3, 64.0, 12),
+    (-1.0 / 4, 4e-4, 64.0, 16),
+    (-1.0 / 8, 4e-4, 64.0, 16),
+    (-1.0 / 16, 4e-4, 64.0, 16),
+    (-1.0 / 32, 4e-4, 64.0, 16),
 ]
 
 
