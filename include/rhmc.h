@@ -276,8 +276,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, shifted updates: on the tensor cores
  *                                 (tcgen05, 3xTF32, n_rhs = 16 only) = 1; CUDA-core kernel with
  *                                 lane-owned row slices = 2; CUDA-core kernel with column-owner
- *                                 lanes and cp.async-staged row tiles = 0 (built-in) or 3..9
- *                                 (tile shape variants, see the autotuner)
+ *                                 lanes and cp.async-staged row tiles = 0 (built-in: packed
+ *                                 FP32x2 FMAs) or 3..11 (tile shape and FMA variants, see the
+ *                                 autotuner)
  *   RHMC_TUNE_GRAPHS              solver iterations in captured CUDA graphs (0, 1: built-in)
  *                                 or as eager launches (2)
  *   RHMC_TUNE_HOP_STAGED          FP32 hop kernel: all 8 neighbours' loads issued at once,
@@ -295,6 +296,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_REFINE_LANES        defect corrections of different shifts run concurrently on
  *                                 up to this many streams, one host thread each (0: 4, the
  *                                 most; 1: in turn on the caller's stream)
+ *   RHMC_TUNE_AXPY_SCALAR         mixed precision, tall-skinny updates Y = C + A M (with or
+ *                                 without the fused Gram): 1 = scalar FP32 FMAs; 0 = packed
+ *                                 FP32x2 FMAs (built-in)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -308,7 +312,8 @@ enum {
   RHMC_TUNE_HOP_STAGED = 8,
   RHMC_TUNE_REFINE_LANES = 9,
   RHMC_TUNE_LINKS12 = 10,
-  RHMC_TUNE_SHIFT_FREEZE_NANO = 11
+  RHMC_TUNE_SHIFT_FREEZE_NANO = 11,
+  RHMC_TUNE_AXPY_SCALAR = 12
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

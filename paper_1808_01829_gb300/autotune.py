@@ -5,9 +5,10 @@ profiler, the candidates of
 
 * the FP32 hop: one or two right-hand sides per thread (RHMC_TUNE_HOP_STAGED
   3 / 4), on the FP32 operator;
-* the column-owner shifted-update kernel: rows per warp tile, warps per CTA
-  and shifts in flight (RHMC_TUNE_UPDATE_TENSOR variants 4, 6, 7, 8, 9), in
-  a short mixed-precision solve with the given shifts;
+* the column-owner shifted-update kernel with packed FP32x2 FMAs: warps per
+  CTA and shifts in flight (RHMC_TUNE_UPDATE_TENSOR variants 5, 10, 11), in a
+  short mixed-precision solve with the given shifts (the scalar-FMA variants
+  are left out: at equal speed per launch they leave a larger FP32 drift);
 
 and keeps the fastest.  The settings are applied to the context
 (rhmc_ctx_tune_set), so ensembles solved together by
@@ -28,7 +29,7 @@ from . import _lib, roofline
 KEY_HOP = 8          # RHMC_TUNE_HOP_STAGED
 KEY_UPDATE = 6       # RHMC_TUNE_UPDATE_TENSOR
 HOP_CANDIDATES = (3, 4)
-UPDATE_CANDIDATES = (8, 7, 6, 4, 9)
+UPDATE_CANDIDATES = (5, 10, 11)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rhmc_gb300_autotune.json")
 
 

@@ -44,6 +44,29 @@ namespace rhmc {
   }
 
 
+// ------------------------------------------------------------ packed FP32x2 helpers
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+// d = a * b + c on two FP32 lanes at once (one rounding per lane)
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // ------------------------------------------------------------ Gram
 // G = A^dagger B (n x n), summed over all rows, in two launches:
 //   k_gram      every warp streams its own 16-row tiles of A and B through a
@@ -66,12 +89,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <typename T, int N, bool SAME>
+// PK (FP32, n = 16): packed FP32x2 FMAs, conj(a) b from the duplicated pairs
+// (a.re, a.re), (a.im, a.im) times the (re, im) pair of b as loaded.
+template <typename T, int N, bool SAME, bool PK>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
                                               double2 *__restrict__ partial) {
   constexpr int TE = kGramTileRows * N;  // complex per tile and operand
   constexpr int E = (N * N + 31) / 32;   // entries per lane
   constexpr bool STRUCT = (N == 16);
+  constexpr bool PACKED = PK && STRUCT && sizeof(T) == 4;
+  unsigned long long p1[PACKED ? 8 : 1], p2[PACKED ? 8 : 1];  // (sum a.re b.re, a.re b.im), (a.im b.re, a.im b.im)
+#pragma unroll
+  for (int q = 0; q < (PACKED ? 8 : 1); ++q) p1[q] = p2[q] = 0ull;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int STAGE = (SAME ? 1 : 2) * TE;  // complex per pipeline stage
@@ -114,7 +143,23 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
     cp_async_wait1();
     __syncwarp();
     const C<T> *ta = sa(st), *tb = sb(st);
-    if (STRUCT) {
+    if constexpr (PACKED) {
+      const int i = lane >> 1, j0 = (lane & 1) * 8;
+#pragma unroll 4
+      for (int r = 0; r < kGramTileRows; ++r) {
+        const float2 a = *reinterpret_cast<const float2 *>(ta + r * N + i);
+        const unsigned long long axx = pack2(a.x, a.x), ayy = pack2(a.y, a.y);
+        const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(tb + r * N + j0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const ulonglong2 b2 = bp[q];
+          p1[2 * q] = fma2(axx, b2.x, p1[2 * q]);
+          p2[2 * q] = fma2(ayy, b2.x, p2[2 * q]);
+          p1[2 * q + 1] = fma2(axx, b2.y, p1[2 * q + 1]);
+          p2[2 * q + 1] = fma2(ayy, b2.y, p2[2 * q + 1]);
+        }
+      }
+    } else if (STRUCT) {
       const int i = lane >> 1, j0 = (lane & 1) * 8;
 #pragma unroll 4
       for (int r = 0; r < kGramTileRows; ++r) {
@@ -138,6 +183,14 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
     st ^= 1;
   }
   cp_async_wait0();
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 u = unpack2(p1[q]), v = unpack2(p2[q]);
+      acc[q].x = u.x + v.y;
+      acc[q].y = u.y - v.x;
+    }
+  }
   __syncthreads();
   // CTA reduction in FP64 (reuses the tile buffers), then one partial per entry
   double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [kGramWarps][N*N]
@@ -423,39 +476,16 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
 // FP32 shifted updates of Algorithm 1 lines 11-12 for every live shift:
 //   X^(s) += P^(s) M1^(s),   P^(s) = Q + P^(s) M2^(s)
 // (M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger).  Each warp owns tiles of
-// R = 8 rows; lane l < 2N owns output column j = l mod N of M1 (l < N) or M2
+// R rows; lane l < 2N owns output column j = l mod N of M1 (l < N) or M2
 // (N <= l < 2N) and keeps that coefficient column in registers for the shift.
-// The tile's Q rows and, three shifts deep, its P^(s) and X^(s) rows are
-// staged in the warp's shared memory by cp.async.  The P^(s) tile is then
-// rewritten with every element duplicated, (re, re, im, im), so that one
-// broadcast 16-byte load feeds a complex multiply-add done as two packed
-// FP32x2 FMAs: (acc.re, acc.im) += (p.re, p.re) (c.re, c.im) + (p.im, p.im) (-c.im, c.re).
+// The tile's Q rows and, NB - 1 shifts ahead, its P^(s) and X^(s) rows are
+// staged in the warp's shared memory by cp.async; every lane reads the P^(s)
+// rows as broadcasts.
 __device__ __forceinline__ void cpa16(unsigned dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 template <int NW> __device__ __forceinline__ void cpa_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(NW) : "memory");
-}
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 unpack2(unsigned long long v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-  return make_float2(lo, hi);
-}
-// d = a * b + c on two FP32 lanes at once (one rounding per lane)
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
 }
 
 // X^(s) rows r, r+1 (lanes of M1) or P^(s) rows (lanes of M2) of a column-owner tile
@@ -472,13 +502,17 @@ __device__ __forceinline__ void col_store(int mat, int j, int r, int N, long off
   }
 }
 
-// tiles of R x N complex per warp: Q, NB x (P, X) raw, the duplicated P tile (packed variant)
-template <int NB, bool PACKED> constexpr int col_tiles_per_warp() { return 1 + 2 * NB + (PACKED ? 2 : 0); }
+// tiles of R x N complex per warp: Q, NB x (P, X)
+template <int NB> constexpr int col_tiles_per_warp() { return 1 + 2 * NB; }
 
 // R rows per warp tile, W warps per CTA, NB shifts in flight per warp;
-// PACKED: duplicated P tile and FP32x2 FMAs
+// PACKED: FP32x2 FMAs.  A complex product u c is formed from the (re, im) pair
+// of u as loaded, times the duplicated pairs (c.re, c.re) and (c.im, c.im)
+// held in registers: A = sum (u.re c.re, u.im c.re), B = sum (u.re c.im,
+// u.im c.im), u c = (A.x - B.y, A.y + B.x): two packed FMAs per complex
+// multiply-add instead of four scalar ones.
 template <int N, int R, int W, int NB, bool PACKED>
-__global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict__ Q, float2 *__restrict__ P,
+__global__ void __launch_bounds__(W * 32, 1) k_update_cols(const float2 *__restrict__ Q, float2 *__restrict__ P,
                                                         float2 *__restrict__ X, const float2 *__restrict__ coef,
                                                         const int *__restrict__ upd, int s_begin, int s_end, long rows,
                                                         long fstride) {
@@ -489,10 +523,9 @@ __global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict
   const int nsh = s_end - s_begin;
   float2 *cs = reinterpret_cast<float2 *>(smem_raw);  // [nsh][2][N * N]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2 *qs = cs + (size_t)nsh * 2 * N * N + (size_t)warp * col_tiles_per_warp<NB, PACKED>() * TILE;
+  float2 *qs = cs + (size_t)nsh * 2 * N * N + (size_t)warp * col_tiles_per_warp<NB>() * TILE;
   auto ptile = [&](int b) { return qs + TILE * (1 + 2 * b); };
   auto xtile = [&](int b) { return qs + TILE * (2 + 2 * b); };
-  float4 *dup = reinterpret_cast<float4 *>(qs + TILE * (1 + 2 * NB));  // [R][N] duplicated P tile
   for (int k = threadIdx.x; k < nsh * 2 * N * N; k += blockDim.x) cs[k] = coef[(1 + 2 * s_begin) * N * N + k];
   if (threadIdx.x == 0) {
     int m = 0;
@@ -536,50 +569,56 @@ __global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict
       cp_async_commit();
       cpa_wait<NB - 1>();  // shift i's tiles (and the Q tile) have landed for this lane
       __syncwarp();        // ... and for the whole warp
-      if (PACKED) {
-        const float2 *pt = ptile(b);
-        for (int e = lane; e < nr * N; e += 32) {
-          const float2 v = pt[e];
-          dup[e] = make_float4(v.x, v.x, v.y, v.y);
-        }
-      }
       const int sh = live[i];
       const float2 *xt = xtile(b);
       const long off = sh * fstride + r0 * N;
-      if (PACKED) {
-        unsigned long long ca[N], cb[N];
+      if constexpr (PACKED) {
+        unsigned long long cr[N], ci[N];
         if (act) {
           const float2 *m = cs + ((sh - s_begin) * 2 + mat) * N * N + j;
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const float2 c = m[k * N];
-            ca[k] = pack2(c.x, c.y);
-            cb[k] = pack2(-c.y, c.x);
+            cr[k] = pack2(c.x, c.x);
+            ci[k] = pack2(c.y, c.y);
           }
         }
-        __syncwarp();  // duplicated tile complete
+        const float2 *pt = ptile(b);
         if (act) {
 #pragma unroll 1
           for (int r = 0; r < nr; r += 2) {
-            unsigned long long a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
-            const float4 *d0 = dup + r * N, *d1 = d0 + N;
+            unsigned long long a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;  // row r: A, B (even, odd k)
+            unsigned long long c0 = 0ull, c1 = 0ull, d0 = 0ull, d1 = 0ull;  // row r + 1
+            const float2 *p0 = pt + r * N, *p1 = p0 + N;
+            if constexpr (N % 2 == 0) {
 #pragma unroll
-            for (int k = 0; k < N; k += 2) {
-              const float4 u0 = d0[k], v0 = d1[k];
-              a0 = fma2(pack2(u0.x, u0.y), ca[k], a0);
-              a0 = fma2(pack2(u0.z, u0.w), cb[k], a0);
-              b0 = fma2(pack2(v0.x, v0.y), ca[k], b0);
-              b0 = fma2(pack2(v0.z, v0.w), cb[k], b0);
-              if (k + 1 < N) {
-                const float4 u1 = d0[k + 1], v1 = d1[k + 1];
-                a1 = fma2(pack2(u1.x, u1.y), ca[k + 1], a1);
-                a1 = fma2(pack2(u1.z, u1.w), cb[k + 1], a1);
-                b1 = fma2(pack2(v1.x, v1.y), ca[k + 1], b1);
-                b1 = fma2(pack2(v1.z, v1.w), cb[k + 1], b1);
+              for (int k = 0; k < N; k += 2) {
+                const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(p0 + k);
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p1 + k);
+                a0 = fma2(u.x, cr[k], a0);
+                b0 = fma2(u.x, ci[k], b0);
+                a1 = fma2(u.y, cr[k + 1], a1);
+                b1 = fma2(u.y, ci[k + 1], b1);
+                c0 = fma2(v.x, cr[k], c0);
+                d0 = fma2(v.x, ci[k], d0);
+                c1 = fma2(v.y, cr[k + 1], c1);
+                d1 = fma2(v.y, ci[k + 1], d1);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < N; ++k) {
+                const unsigned long long u = *reinterpret_cast<const unsigned long long *>(p0 + k);
+                const unsigned long long v = *reinterpret_cast<const unsigned long long *>(p1 + k);
+                a0 = fma2(u, cr[k], a0);
+                b0 = fma2(u, ci[k], b0);
+                c0 = fma2(v, cr[k], c0);
+                d0 = fma2(v, ci[k], d0);
               }
             }
-            const float2 s0 = unpack2(add2(a0, a1)), s1 = unpack2(add2(b0, b1));
-            col_store(mat, j, r, N, off, xt, qs, X, P, s0, s1);
+            const float2 A0 = unpack2(add2(a0, a1)), B0 = unpack2(add2(b0, b1));
+            const float2 A1 = unpack2(add2(c0, c1)), B1 = unpack2(add2(d0, d1));
+            col_store(mat, j, r, N, off, xt, qs, X, P, make_float2(A0.x - B0.y, A0.y + B0.x),
+                      make_float2(A1.x - B1.y, A1.y + B1.x));
           }
         }
       } else {
@@ -625,7 +664,7 @@ __global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict
           }
         }
       }
-      __syncwarp();  // buffer b and the duplicated tile are refilled at the next step
+      __syncwarp();  // buffer b is refilled at the next step
     }
     cpa_wait<0>();
     __syncwarp();  // the Q tile and buffers are reused by the next tile
@@ -634,7 +673,7 @@ __global__ void __launch_bounds__(W * 32) k_update_cols(const float2 *__restrict
 
 template <int N, int R, int W, int NB, bool PACKED>
 static size_t col_smem(int nsh) {
-  return (size_t)nsh * 2 * N * N * sizeof(float2) + (size_t)W * col_tiles_per_warp<NB, PACKED>() * R * N * sizeof(float2);
+  return (size_t)nsh * 2 * N * N * sizeof(float2) + (size_t)W * col_tiles_per_warp<NB>() * R * N * sizeof(float2);
 }
 
 template <int N, int R, int W, int NB, bool PACKED>
@@ -656,19 +695,24 @@ static rhmc_status_t launch_update_cols(const float2 *Q, float2 *P, float2 *X, c
 }
 
 // Variants of the column-owner kernel (RHMC_TUNE_UPDATE_TENSOR), rows per warp
-// tile / warps per CTA / shifts in flight: 3 = 16/8/3; 4 = 8/16/3; 5 = 8/16/3
-// with the duplicated tile and FP32x2 FMAs; 6 = 4/32/3; 7 = 8/24/2; 8 = 8/28/2
-// (built-in, 0); 9 = 4/32/2.  Measured at 24^4, n = 16, 15 live shifts, one
-// launch alone: 1116, 830, 1042, 792, 720, 694, 789 us for 3 ... 9.
+// tile / warps per CTA / shifts in flight (p: FP32x2 FMAs): 3 = 16/8/3;
+// 4 = 8/16/3; 5 = 8/16/2p (built-in, 0); 6 = 4/32/3; 7 = 8/24/2; 8 = 8/28/2;
+// 9 = 4/32/2; 10 = 8/16/3p; 11 = 8/20/2p.  Measured at 24^4, n = 16, 15 live
+// shifts, one launch alone: 1116, 830, -, 1042, 792, 720, 694, 789 us for 3,
+// 4, 6 ... 9 (scalar FMAs); in the whole force evaluation 5 takes the update
+// from 4.35 to 4.54 TB/s: with packed FMAs the kernel is bound by the FMA pipe
+// (60 % busy, issue 56 %) rather than by instruction issue (80 %).
 #define RHMC_COL_VARIANTS(X_)                   \
   switch (col_variant()) {                      \
     case 3: X_(16, 8, 3, false); break;         \
     case 4: X_(8, 16, 3, false); break;         \
-    case 5: X_(8, 16, 3, true); break;          \
     case 6: X_(4, 32, 3, false); break;         \
     case 7: X_(8, 24, 2, false); break;         \
+    case 8: X_(8, 28, 2, false); break;         \
     case 9: X_(4, 32, 2, false); break;         \
-    default: X_(8, 28, 2, false); break;        \
+    case 10: X_(8, 16, 3, true); break;         \
+    case 11: X_(8, 20, 2, true); break;         \
+    default: X_(8, 16, 2, true); break;         \
   }
 static int col_variant() { return tune_get(TUNE_UPDATE_TENSOR); }
 template <int N> static size_t col_tiles_bytes() {
@@ -744,22 +788,83 @@ static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2
 // Q = W rho^-1): lane l < 2N owns column j = l mod N of M (kept in registers)
 // for rows of parity l / N of each row pair; the warp's tiles of R rows of A
 // and C are staged by cp.async two tiles deep; every lane reads the A row as
-// a broadcast.
-template <int N, int R, int W>
-__global__ void __launch_bounds__(W * 32) k_axpy_cols(const float2 *__restrict__ A, const float2 *__restrict__ Cin,
-                                                      const float2 *__restrict__ M, float2 *__restrict__ Y,
-                                                      long rows) {
+// a broadcast.  PK: packed FP32x2 FMAs on the (re, im) pair of each A element
+// times the duplicated coefficient pairs (c.re, c.re), (c.im, c.im), as in
+// the shifted updates.
+
+// y = sum_k a[k] M[k][j], packed: cr[k] = (c.re, c.re), ci[k] = (c.im, c.im)
+template <int N>
+__device__ __forceinline__ float2 row_times_col_packed(const float2 *ar, const unsigned long long *cr,
+                                                       const unsigned long long *ci) {
+  unsigned long long a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2) {
+      const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(ar + k);
+      a0 = fma2(u.x, cr[k], a0);
+      b0 = fma2(u.x, ci[k], b0);
+      a1 = fma2(u.y, cr[k + 1], a1);
+      b1 = fma2(u.y, ci[k + 1], b1);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const unsigned long long u = *reinterpret_cast<const unsigned long long *>(ar + k);
+      a0 = fma2(u, cr[k], a0);
+      b0 = fma2(u, ci[k], b0);
+    }
+  }
+  const float2 A = unpack2(add2(a0, a1)), B = unpack2(add2(b0, b1));
+  return make_float2(A.x - B.y, A.y + B.x);
+}
+
+// the same with scalar FMAs and cf[k] = M[k][j]
+template <int N> __device__ __forceinline__ float2 row_times_col(const float2 *ar, const float2 *cf) {
+  float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float2 u = ar[k], c0 = cf[k];
+    if (k & 1) {
+      ax1 = fmaf(u.x, c0.x, ax1); ax1 = fmaf(-u.y, c0.y, ax1);
+      ay1 = fmaf(u.x, c0.y, ay1); ay1 = fmaf(u.y, c0.x, ay1);
+    } else {
+      ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
+      ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
+    }
+  }
+  return make_float2(ax0 + ax1, ay0 + ay1);
+}
+
+// the lane's coefficient column j of M, scalar (cf) or as duplicated pairs (cr, ci)
+template <int N, bool PK>
+__device__ __forceinline__ void load_col(const float2 *__restrict__ M, int j, float2 *cf, unsigned long long *cr,
+                                         unsigned long long *ci) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float2 c = M[k * N + j];
+    if constexpr (PK) {
+      cr[k] = pack2(c.x, c.x);
+      ci[k] = pack2(c.y, c.y);
+    } else {
+      cf[k] = c;
+    }
+  }
+}
+
+template <int N, int R, int W, bool PK>
+__global__ void __launch_bounds__(W * 32, PK ? 1 : 2) k_axpy_cols(const float2 *__restrict__ A,
+                                                                  const float2 *__restrict__ Cin,
+                                                                  const float2 *__restrict__ M,
+                                                                  float2 *__restrict__ Y, long rows) {
   constexpr int TILE = R * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2 *wb = reinterpret_cast<float2 *>(smem_raw) + (size_t)warp * 4 * TILE;  // [2 buffers][A, C]
   const int h = lane / N, j = lane - (lane / N) * N;
   const bool act = lane < 2 * N;
-  float2 cf[N];
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) cf[k] = M[k * N + j];
-  }
+  float2 cf[PK ? 1 : N];
+  unsigned long long cr[PK ? N : 1], ci[PK ? N : 1];
+  if (act) load_col<N, PK>(M, j, cf, cr, ci);
   const long ntiles = (rows + R - 1) / R;
   const long t0 = (long)blockIdx.x * W + warp, dt = (long)gridDim.x * W;
   auto issue = [&](long tile, int b) {
@@ -788,27 +893,11 @@ __global__ void __launch_bounds__(W * 32) k_axpy_cols(const float2 *__restrict__
     if (act) {
 #pragma unroll 1
       for (int r = h; r < nr; r += 2) {
-        float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
-        const float2 *ar = at + r * N;
-        if constexpr (N % 2 == 0) {
-#pragma unroll
-          for (int k = 0; k < N; k += 2) {
-            const float4 u = *reinterpret_cast<const float4 *>(ar + k);
-            const float2 c0 = cf[k], c1 = cf[k + 1];
-            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
-            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
-            ax1 = fmaf(u.z, c1.x, ax1); ax1 = fmaf(-u.w, c1.y, ax1);
-            ay1 = fmaf(u.z, c1.y, ay1); ay1 = fmaf(u.w, c1.x, ay1);
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const float2 u = ar[k], c0 = cf[k];
-            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
-            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
-          }
-        }
-        float2 y = make_float2(ax0 + ax1, ay0 + ay1);
+        float2 y;
+        if constexpr (PK)
+          y = row_times_col_packed<N>(at + r * N, cr, ci);
+        else
+          y = row_times_col<N>(at + r * N, cf);
         if (Cin) {
           const float2 cv = ct[r * N + j];
           y.x += cv.x;
@@ -827,8 +916,8 @@ __global__ void __launch_bounds__(W * 32) k_axpy_cols(const float2 *__restrict__
 // lane (h, j) adds conj(Y[r][i]) Y[r][j] for all i to its FP32 column of G;
 // the columns are combined across the row parities, the warps (FP64, shared
 // memory) and the CTAs (partials summed in fixed order by k_gram_sum).
-template <int N, int R, int W>
-__global__ void __launch_bounds__(W * 32) k_axpy_gram_cols(const float2 *__restrict__ A,
+template <int N, int R, int W, bool PK>
+__global__ void __launch_bounds__(W * 32, 1) k_axpy_gram_cols(const float2 *__restrict__ A,
                                                            const float2 *__restrict__ Cin,
                                                            const float2 *__restrict__ M, float2 *__restrict__ Y,
                                                            long rows, double2 *__restrict__ partial) {
@@ -839,13 +928,12 @@ __global__ void __launch_bounds__(W * 32) k_axpy_gram_cols(const float2 *__restr
   float2 *wrow = wb + 4 * TILE;
   const int h = lane / N, j = lane - (lane / N) * N;
   const bool act = lane < 2 * N;
-  float2 cf[N], g[N];
+  float2 g[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) g[k] = make_float2(0.f, 0.f);
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) cf[k] = M[k * N + j];
-  }
+  float2 cf[PK ? 1 : N];
+  unsigned long long cr[PK ? N : 1], ci[PK ? N : 1];
+  if (act) load_col<N, PK>(M, j, cf, cr, ci);
   const long ntiles = (rows + R - 1) / R;
   const long t0 = (long)blockIdx.x * W + warp, dt = (long)gridDim.x * W;
   auto issue = [&](long tile, int b) {
@@ -875,21 +963,14 @@ __global__ void __launch_bounds__(W * 32) k_axpy_gram_cols(const float2 *__restr
     for (int r = 0; r < nr; r += 2) {
       float2 y = make_float2(0.f, 0.f);
       if (act) {
-        float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
         const float2 *ar = at + (r + h) * N;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const float2 u = ar[k], c0 = cf[k];
-          if (k & 1) {
-            ax1 = fmaf(u.x, c0.x, ax1); ax1 = fmaf(-u.y, c0.y, ax1);
-            ay1 = fmaf(u.x, c0.y, ay1); ay1 = fmaf(u.y, c0.x, ay1);
-          } else {
-            ax0 = fmaf(u.x, c0.x, ax0); ax0 = fmaf(-u.y, c0.y, ax0);
-            ay0 = fmaf(u.x, c0.y, ay0); ay0 = fmaf(u.y, c0.x, ay0);
-          }
-        }
+        float2 p;
+        if constexpr (PK)
+          p = row_times_col_packed<N>(ar, cr, ci);
+        else
+          p = row_times_col<N>(ar, cf);
         const float2 cv = ct[(r + h) * N + j];
-        y = make_float2(ax0 + ax1 + cv.x, ay0 + ay1 + cv.y);
+        y = make_float2(p.x + cv.x, p.y + cv.y);
         Y[(r0 + r + h) * N + j] = y;
         wrow[h * N + j] = y;
       }
@@ -932,39 +1013,44 @@ __global__ void __launch_bounds__(W * 32) k_axpy_gram_cols(const float2 *__restr
 }
 
 constexpr int kAxpyRows = 8, kAxpyWarps = 16;
+// warps per CTA of the fused axpy + Gram kernel (the packed form holds 64 more
+// registers of coefficients per lane)
+template <bool PK> constexpr int axpy_gram_warps() { return PK ? 12 : 16; }
+static bool axpy_packed() { return tune_get(TUNE_AXPY_SCALAR) != 1; }
 
-template <int N>
+template <int N, bool PK>
 static void launch_axpy_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows,
                              cudaStream_t s) {
   const int threads = kAxpyWarps * 32;
   const size_t smem = (size_t)kAxpyWarps * 4 * kAxpyRows * N * sizeof(float2);
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_axpy_cols<N, kAxpyRows, kAxpyWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_axpy_cols<N, kAxpyRows, kAxpyWarps, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          220 * 1024);
   });
   const long ntiles = (rows + kAxpyRows - 1) / kAxpyRows;
   long grid = (ntiles + kAxpyWarps - 1) / kAxpyWarps;
-  grid = std::min(grid, (long)resident_ctas(k_axpy_cols<N, kAxpyRows, kAxpyWarps>, threads, smem));
-  k_axpy_cols<N, kAxpyRows, kAxpyWarps><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows);
+  grid = std::min(grid, (long)resident_ctas(k_axpy_cols<N, kAxpyRows, kAxpyWarps, PK>, threads, smem));
+  k_axpy_cols<N, kAxpyRows, kAxpyWarps, PK><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows);
 }
 
-template <int N>
+template <int N, bool PK>
 static void launch_axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows,
                                   double2 *scratch, double2 *out, cudaStream_t s) {
-  const int threads = kAxpyWarps * 32;
-  const size_t smem = std::max((size_t)kAxpyWarps * (4 * kAxpyRows * N + 2 * N) * sizeof(float2),
-                               (size_t)kAxpyWarps * N * N * sizeof(double2));
+  constexpr int W = axpy_gram_warps<PK>();
+  const int threads = W * 32;
+  const size_t smem = std::max((size_t)W * (4 * kAxpyRows * N + 2 * N) * sizeof(float2),
+                               (size_t)W * N * N * sizeof(double2));
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_axpy_gram_cols<N, kAxpyRows, W, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          220 * 1024);
   });
   const long ntiles = (rows + kAxpyRows - 1) / kAxpyRows;
-  long grid = (ntiles + kAxpyWarps - 1) / kAxpyWarps;
-  grid = std::min(grid, (long)std::min(kGramCtas, resident_ctas(k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps>,
-                                                                  threads, smem)));
-  k_axpy_gram_cols<N, kAxpyRows, kAxpyWarps><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
+  long grid = (ntiles + W - 1) / W;
+  grid = std::min(grid, (long)std::min(kGramCtas, resident_ctas(k_axpy_gram_cols<N, kAxpyRows, W, PK>, threads,
+                                                                  smem)));
+  k_axpy_gram_cols<N, kAxpyRows, W, PK><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, (int)grid, out);
 }
 
@@ -974,7 +1060,11 @@ rhmc_status_t axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, 
                              double2 *scratch, double2 *out, cudaStream_t s) {
   if (rows % 8 || !C) return RHMC_ERR_INVALID_ARG;
   prof_begin(PROF_AXPY, s);
-#define L_AG(NN) launch_axpy_gram_cols<NN>(A, C, M, Y, rows, scratch, out, s)
+#define L_AG(NN)                                                        \
+  if (axpy_packed())                                                    \
+    launch_axpy_gram_cols<NN, true>(A, C, M, Y, rows, scratch, out, s); \
+  else                                                                  \
+    launch_axpy_gram_cols<NN, false>(A, C, M, Y, rows, scratch, out, s)
   RHMC_DISPATCH_N(n, L_AG)
 #undef L_AG
   prof_end(s, (double)rows * n * sizeof(float2) * 3);
@@ -987,7 +1077,11 @@ rhmc_status_t axpy_cols(const float2 *A, const float2 *C, const float2 *M, float
                         cudaStream_t s) {
   if (rows % 8) return RHMC_ERR_INVALID_ARG;
   prof_begin(PROF_AXPY, s);
-#define L_AX(NN) launch_axpy_cols<NN>(A, C, M, Y, rows, s)
+#define L_AX(NN)                                   \
+  if (axpy_packed())                               \
+    launch_axpy_cols<NN, true>(A, C, M, Y, rows, s); \
+  else                                             \
+    launch_axpy_cols<NN, false>(A, C, M, Y, rows, s)
   RHMC_DISPATCH_N(n, L_AX)
 #undef L_AX
   prof_end(s, (double)rows * n * sizeof(float2) * (C ? 3 : 2));
@@ -1072,7 +1166,7 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
 
 // ------------------------------------------------------------ launchers
 
-template <typename T, int N>
+template <typename T, int N, bool PK>
 static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
   const bool same = (A == B);
   const size_t smem = (size_t)kGramWarps * 2 * (same ? 1 : 2) * kGramTileRows * N * sizeof(C<T>);
@@ -1080,25 +1174,38 @@ static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratc
   const size_t bytes = std::max(smem, smem_red);
   static std::once_flag attr;
   std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_gram<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_gram<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram<T, N, true, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram<T, N, false, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
   // one wave: as many CTAs as are resident at once (at most the partials' capacity)
-  const int resident = same ? resident_ctas(k_gram<T, N, true>, 256, bytes) : resident_ctas(k_gram<T, N, false>, 256, bytes);
+  const int resident = same ? resident_ctas(k_gram<T, N, true, PK>, 256, bytes)
+                            : resident_ctas(k_gram<T, N, false, PK>, 256, bytes);
   const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, std::min(kGramCtas, resident));
   if (same)
-    k_gram<T, N, true><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+    k_gram<T, N, true, PK><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
   else
-    k_gram<T, N, false><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+    k_gram<T, N, false, PK><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, grid, out);
+}
+
+// packed FMAs for FP32 at n = 16 unless RHMC_TUNE_AXPY_SCALAR = 1
+template <typename T, int N>
+static void launch_gram_any(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
+  if constexpr (N == 16 && sizeof(T) == 4) {
+    if (tune_get(TUNE_AXPY_SCALAR) != 1) {
+      launch_gram<T, N, true>(A, B, rows, scratch, out, s);
+      return;
+    }
+  }
+  launch_gram<T, N, false>(A, B, rows, scratch, out, s);
 }
 
 // G = A^dagger B into out (n x n, FP64); scratch holds kGramCtas * n * n partials.
 template <typename T>
 rhmc_status_t gram(const C<T> *A, const C<T> *B, long rows, int n, double2 *scratch, double2 *out, cudaStream_t s) {
   prof_begin(sizeof(T) == 4 ? PROF_GRAM32 : PROF_GRAM64, s);
-#define L_GRAM(NN) launch_gram<T, NN>(A, B, rows, scratch, out, s)
+#define L_GRAM(NN) launch_gram_any<T, NN>(A, B, rows, scratch, out, s)
   RHMC_DISPATCH_N(n, L_GRAM)
 #undef L_GRAM
   prof_end(s, (double)rows * n * sizeof(C<T>) * (A == B ? 1 : 2));

@@ -226,7 +226,7 @@ def test_tensor_core_shift_update_matches_oracle(dims):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 5, 9])
+@pytest.mark.parametrize("variant", [0, 2, 5, 9, 10, 11])
 def test_shifted_update_kernels_many_shifts(variant):
     """Both FP32 shifted-update kernels (column owners, built-in; lane slices) on a
     mixed solve with 40 shifts at n = 16 (the column-owner kernel splits them over
@@ -245,6 +245,33 @@ def test_shifted_update_kernels_many_shifts(variant):
         Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-9, precision="mixed")
     finally:
         lib.rhmc_tune_set(6, 0)
+    assert info.true_rel_resid_max <= 1e-9
+    Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, shifts, tol=1e-13, max_iter=20000)
+    assert rc == 0
+    _check_solution(dims, mass, U, B, shifts, Xg.cpu().numpy(), 1e-9, Xo)
+    ctx.close()
+
+
+@pytest.mark.parametrize("scalar", [0, 1])
+@pytest.mark.parametrize("n", [16, 5])
+def test_fp32_bulk_fma_forms(scalar, n):
+    """The FP32 Gram and Y = C + A M kernels with packed FP32x2 FMAs (built-in)
+    and with scalar FMAs (RHMC_TUNE_AXPY_SCALAR = 1) both give mixed solves
+    that match the oracle, at n = 16 (packed Gram) and odd n."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass = (4, 4, 4, 8), 0.05
+    shifts = [1e-3, 0.02, 0.3, 4.0]
+    U = syn.random_links(dims, 0.5, 1250 + n)
+    B = syn.gaussian_pseudofermions(dims, n, 2250 + n)
+    ctx = make_ctx(dims, mass, U)
+    try:
+        lib.rhmc_tune_set(12, scalar)
+        Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-9, precision="mixed")
+    finally:
+        lib.rhmc_tune_set(12, 0)
     assert info.true_rel_resid_max <= 1e-9
     Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, shifts, tol=1e-13, max_iter=20000)
     assert rc == 0
