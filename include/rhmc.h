@@ -206,6 +206,23 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double 
                          const void *X_in_dev, void *G_dev, double *S_out, void *workspace, rhmc_info_t *info,
                          rhmc_stream_t s);
 
+/* Lie-algebra force and its norm (Sec. II, Eqs. (force), (force_norm)).
+ * Per link, F_mu(x) = TA(U_mu(x) G_mu(x)^dagger) with
+ * TA(M) = (M - M^dagger)/2 - tr(M - M^dagger)/6 (traceless anti-Hermitian);
+ * with generators T^a = i lambda^a / 2 (Gell-Mann lambda^a) the derivative of
+ * S along U -> exp(w T^a) U is F^a = Re tr(G^dagger T^a U) = tr(F T^a), i.e.
+ * F = -2 sum_a F^a T^a.
+ *   U         complex128 [V][4][3][3], the links given to rhmc_set_gauge
+ *   G         complex128 [V][4][3][3], rhmc_force's output
+ *   F         complex128 [V][4][3][3] output, or NULL; may alias G
+ *   norm2_out optional host double: sum over links of sum_a (F^a)^2 / 2
+ *             (= |F|_F^2 / 4), summed in a fixed order (deterministic)
+ * FP64.  With norm2_out the call synchronises stream s; otherwise it is
+ * asynchronous.  INVALID_ARG for null U or G, or when neither F nor norm2_out
+ * is given. */
+rhmc_status_t rhmc_force_lie(rhmc_ctx_t *ctx, const void *U_dev, const void *G_dev, void *F_dev, double *norm2_out,
+                             rhmc_stream_t s);
+
 /* R(A) Phi of Eq. (RA) by the block multishift solve, without storing the
  * shifted solutions (pseudofermion heatbath and action evaluation, where only
  * the rational sum is needed):
@@ -299,6 +316,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_AXPY_SCALAR         mixed precision, tall-skinny updates Y = C + A M (with or
  *                                 without the fused Gram): 1 = scalar FP32 FMAs; 0 = packed
  *                                 FP32x2 FMAs (built-in)
+ *   RHMC_TUNE_NO_DEFECT_CORRECTION  1: no defect corrections after the multishift phase; the
+ *                                 FP64 true residuals it left are reported (info) and shifts
+ *                                 above tol give NOT_CONVERGED (for convergence studies)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -313,7 +333,8 @@ enum {
   RHMC_TUNE_REFINE_LANES = 9,
   RHMC_TUNE_LINKS12 = 10,
   RHMC_TUNE_SHIFT_FREEZE_NANO = 11,
-  RHMC_TUNE_AXPY_SCALAR = 12
+  RHMC_TUNE_AXPY_SCALAR = 12,
+  RHMC_TUNE_NO_DEFECT_CORRECTION = 13
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

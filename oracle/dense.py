@@ -161,3 +161,43 @@ def matrix_power_apply(dims, mass, U, Phi, r, bc_t=-1):
     w, v = np.linalg.eigh(A)
     B = field_to_vec(Phi)
     return vec_to_field(v @ ((w ** r)[:, None] * (v.conj().T @ B)), Phi.shape[-1])
+
+
+# ---------------------------------------------------------------- Lie-algebra force (Sec. II)
+def gell_mann_matrices():
+    """The eight Gell-Mann matrices lambda^a (Hermitian, traceless, tr(l^a l^b) = 2 delta_ab)."""
+    L = np.zeros((8, 3, 3), dtype=np.complex128)
+    L[0][0, 1] = L[0][1, 0] = 1
+    L[1][0, 1], L[1][1, 0] = -1j, 1j
+    L[2][0, 0], L[2][1, 1] = 1, -1
+    L[3][0, 2] = L[3][2, 0] = 1
+    L[4][0, 2], L[4][2, 0] = -1j, 1j
+    L[5][1, 2] = L[5][2, 1] = 1
+    L[6][1, 2], L[6][2, 1] = -1j, 1j
+    L[7] = np.diag([1, 1, -2]) / np.sqrt(3)
+    return L
+
+
+def lie_components(U, G):
+    """F^a = d S / d w along U -> exp(w T^a) U at every link, T^a = i lambda^a / 2.
+    With G = dS/dRe U + i dS/dIm U, dS = Re tr(G^dagger dU), so F^a = Re tr(G^dagger T^a U).
+    U, G (..., 3, 3); returns (..., 8)."""
+    T = 0.5j * gell_mann_matrices()
+    return np.einsum("...ji,ajk,...ki->...a", G.conj(), T, U).real
+
+
+def force_norm2(U, G):
+    """sum over links and a of (F^a)^2 / 2 (the summand of the force norm F^2, Sec. II)."""
+    return float(0.5 * np.sum(lie_components(U, G) ** 2))
+
+
+def ta_project(M):
+    """Traceless anti-Hermitian part: (M - M^dagger)/2 - tr(M - M^dagger)/6."""
+    A = 0.5 * (M - np.swapaxes(M.conj(), -1, -2))
+    tr = np.trace(A, axis1=-2, axis2=-1)
+    return A - (tr / 3.0)[..., None, None] * np.eye(3)
+
+
+def force_lie(U, G):
+    """F = TA(U G^dagger) per link."""
+    return ta_project(U @ np.swapaxes(G.conj(), -1, -2))

@@ -18,6 +18,10 @@ RHMC_MIXED_FP32 = 1
 RHMC_DF64 = 2
 RHMC_MAX_NRHS = 16
 RHMC_MAX_SHIFTS = 64
+# launch-setting keys (rhmc_tune_set / rhmc_ctx_tune_set) used from Python
+RHMC_TUNE_UPDATE_TENSOR = 6
+RHMC_TUNE_AXPY_SCALAR = 12
+RHMC_TUNE_NO_DEFECT_CORRECTION = 13
 
 STATUS = {
     0: "OK",
@@ -113,6 +117,8 @@ def load():
         lib.rhmc_multishift_cg_pervector.argtypes = [P, P, I, I, PD, P, D, I, P, ctypes.POINTER(Info), P]
         lib.rhmc_force.argtypes = [P, P, I, D, PD, PD, I, D, I, I, P, P, PD, P, ctypes.POINTER(Info), P]
         lib.rhmc_rational_apply.argtypes = [P, P, I, D, PD, I, P, P, P]
+        lib.rhmc_force_lie.argtypes = [P, P, P, P, PD, P]
+        lib.rhmc_force_lie.restype = I
         lib.rhmc_rational_apply.restype = I
         lib.rhmc_last_error.restype = ctypes.c_char_p
         lib.rhmc_kernel_launches.restype = ctypes.c_longlong
@@ -145,5 +151,5 @@ def exported_symbols():
         "rhmc_hop", "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force", "rhmc_last_error", "rhmc_kernel_launches",
         "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
         "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply", "rhmc_block_multishift_cg_batch", "rhmc_ctx_tune_set", "rhmc_ctx_tune_get",
-        "rhmc_rational_solve", "rhmc_rational_solve_bytes", "rhmc_selftest_bounded_wait",
+        "rhmc_rational_solve", "rhmc_rational_solve_bytes", "rhmc_selftest_bounded_wait", "rhmc_force_lie",
     ]

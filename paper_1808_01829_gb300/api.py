@@ -212,6 +212,22 @@ class RhmcContext:
         _lib.check(rc, "rhmc_force")
         return G, S.value, self._info(info, buf, ns, n)
 
+    # -- rhmc_force_lie (Lie-algebra force F = TA(U G^dagger) and the force norm)
+    def force_lie(self, U: torch.Tensor, G: torch.Tensor, out=None, want_F: bool = True):
+        """F_mu(x) = TA(U_mu(x) G_mu(x)^dagger) and sum_{x,mu,a} (F^a)^2 / 2 with
+        F^a = Re tr(G^dagger T^a U), T^a = i lambda^a / 2.  Returns (F or None, norm2)."""
+        for t, name in ((U, "U"), (G, "G")):
+            _check_field(t, name, (self.V, 4, 3, 3))
+        F = None
+        if want_F:
+            F = torch.empty_like(G) if out is None else out
+            _check_field(F, "F", (self.V, 4, 3, 3))
+        nrm = ctypes.c_double(0.0)
+        rc = self.lib.rhmc_force_lie(self._h, _ptr(U), _ptr(G), _ptr(F) if F is not None else None,
+                                     ctypes.byref(nrm), _stream(G))
+        _lib.check(rc, "rhmc_force_lie")
+        return F, nrm.value
+
 
 def block_multishift_cg_batch(items, tol: float, max_iter: int = 0, precision: str = "mixed"):
     """Batched SBCGrQ over independent ensembles (rhmc_block_multishift_cg_batch).

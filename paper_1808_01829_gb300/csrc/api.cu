@@ -177,6 +177,7 @@ struct rhmc_ctx {
   SolverLane main;                 // the caller's stream
   int tune[TUNE_NKEYS] = {};       // per-context launch settings (0: the process-wide value)
   std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
+  double *d_parts = nullptr;       // partial sums of rhmc_force_lie's norm (kParts)
 };
 
 namespace rhmc {
@@ -774,7 +775,7 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
         if (r > 0) ratio_min = std::min(ratio_min, prm.tol / r);
       }
       if (round == 0) w.worst1 = std::max(w.worst1, mx);
-      if (mx <= prm.tol || prm.fixed_iters > 0 || round >= kMaxRefine) {
+      if (mx <= prm.tol || prm.fixed_iters > 0 || round >= kMaxRefine || tune_get(TUNE_NO_DEFECT_CORRECTION) == 1) {
         w.worst = std::max(w.worst, mx);
         return RHMC_OK;
       }
@@ -1031,6 +1032,7 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
   c->lanes.clear();
   c->main.release();
   if (c->pool) cudaFree(c->pool);
+  if (c->d_parts) cudaFree(c->d_parts);
   for (int q = 0; q < 3; ++q) {
     if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);
@@ -1537,6 +1539,27 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
       S += alpha[q] * t;
     }
     *S_out = S;
+  }
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_force_lie(rhmc_ctx_t *c, const void *U, const void *G, void *F, double *norm2_out,
+                             rhmc_stream_t sv) {
+  if (!c || !U || !G || (!F && !norm2_out)) {
+    set_error("rhmc_force_lie: null context, U or G, or neither F nor norm2_out requested");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = (cudaStream_t)sv;
+  if (!c->d_parts) RHMC_CUDA_TRY(cudaMalloc(&c->d_parts, sizeof(double) * kParts));
+  RHMC_TRY(force_lie(c->g, (const double2 *)U, (const double2 *)G, (double2 *)F, c->d_parts, kParts, s));
+  if (norm2_out) {
+    RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts));
+    RHMC_CUDA_TRY(cudaMemcpyAsync(lane(c).h_pin, c->d_parts, sizeof(double) * kParts, cudaMemcpyDeviceToHost, s));
+    RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+    double sum = 0.0;
+    for (int q = 0; q < kParts; ++q) sum += lane(c).h_pin[q];
+    *norm2_out = sum;
   }
   return RHMC_OK;
 }

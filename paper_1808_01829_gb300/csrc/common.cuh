@@ -119,6 +119,7 @@ enum TuneKey {
   TUNE_LINKS12,               // FP32 hop reads 12-real links when all links are SU(3) (1); full records (0, 2)
   TUNE_SHIFT_FREEZE_NANO,     // mixed: freeze shifted systems below this recursive residual (x 1e-9; 0: built-in)
   TUNE_AXPY_SCALAR,           // mixed: scalar FP32 FMAs in the Y = C + A M kernels (1); packed FP32x2 (0)
+  TUNE_NO_DEFECT_CORRECTION,  // 1: report the true residuals after the multishift phase, no corrections
   TUNE_NKEYS
 };
 int tune_get(int key);

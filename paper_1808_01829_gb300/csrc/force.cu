@@ -232,4 +232,70 @@ rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int
   return RHMC_OK;
 }
 
+// ------------------------------------------------------------ Lie-algebra force
+// F_mu(x) = TA(U_mu(x) G_mu(x)^dagger), TA(M) = (M - M^dagger)/2 - tr(M - M^dagger)/6,
+// the traceless anti-Hermitian projection: with generators T^a = i lambda^a / 2,
+// the derivative of S along U -> exp(w T^a) U is F^a = Re tr(G^dagger T^a U)
+// = tr(F T^a), so F = -2 sum_a F^a T^a and sum_a (F^a)^2 / 2 = |F|_F^2 / 4, the
+// summand of the force norm F^2 (Sec. II).  FP64, one thread per link; each
+// CTA writes the sum of its links' |F|_F^2 / 4 to partial[blockIdx.x].
+__global__ void __launch_bounds__(256) k_force_lie(const double2 *__restrict__ U, const double2 *G,
+                                                   double2 *F, long nlinks, double *__restrict__ partial) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (long)gridDim.x * blockDim.x) {
+    double2 u[9], g[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      u[e] = U[l * 9 + e];
+      g[e] = G[l * 9 + e];
+    }
+    double2 m[9];  // M = U G^dagger
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double2 a = u[i * 3 + k], b = g[j * 3 + k];  // a conj(b)
+          re = fma(a.x, b.x, fma(a.y, b.y, re));
+          im = fma(a.y, b.x, fma(-a.x, b.y, im));
+        }
+        m[i * 3 + j] = make_double2(re, im);
+      }
+    // (M - M^dagger)/2 has a purely imaginary diagonal; its trace / 3 is removed
+    const double t = (m[0].y + m[4].y + m[8].y) / 3.0;
+    double nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double2 a = m[i * 3 + j], b = m[j * 3 + i];
+        double2 f = make_double2(0.5 * (a.x - b.x), 0.5 * (a.y + b.y));
+        if (i == j) f.y -= t;
+        nrm += f.x * f.x + f.y * f.y;
+        if (F) F[l * 9 + i * 3 + j] = f;
+      }
+    acc += 0.25 * nrm;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+rhmc_status_t force_lie(const Geom &g, const double2 *U, const double2 *G, double2 *F, double *partial, int nparts,
+                        cudaStream_t s) {
+  prof_begin(PROF_FORCE, s);
+  const long nlinks = g.V * 4;
+  k_force_lie<<<nparts, 256, 0, s>>>(U, G, F, nlinks, partial);
+  prof_end(s, (double)nlinks * 9 * sizeof(double2) * (F ? 3 : 2));
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
 }  // namespace rhmc

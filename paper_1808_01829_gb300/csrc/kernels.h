@@ -107,6 +107,9 @@ rhmc_status_t force_links_df(const Geom &g, const float4 *X, const float4 *Y, in
                              const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
 rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int n, int nshift, long fstride,
                           const double *alpha_dev, int bc_t, double2 *G, cudaStream_t s);
+// F = TA(U G^dagger) per link (F may be null or alias G); partial[nparts]: per-CTA sums of |F|_F^2 / 4
+rhmc_status_t force_lie(const Geom &g, const double2 *U, const double2 *G, double2 *F, double *partial, int nparts,
+                        cudaStream_t s);
 
 // api.cu: read-only view of a context (device, geometry, mass, staged FP64
 // links of the two output parities); NO_GAUGE before rhmc_set_gauge.

@@ -255,6 +255,11 @@ STANDARD = [
     (-1.0 / 8, 4e-4, 64.0, 16),
     (-1.0 / 16, 4e-4, 64.0, 16),
     (-1.0 / 32, 4e-4, 64.0, 16),
+    # force-norm study (studies.py): heatbath x^(+1/(8 n_pf)) on [2e-3, 64], n_pf = 1, 2, 8, 16
+    (1.0 / 8, 2e-3, 64.0, 12),
+    (1.0 / 16, 2e-3, 64.0, 12),
+    (1.0 / 64, 2e-3, 64.0, 12),
+    (1.0 / 128, 2e-3, 64.0, 12),
 ]
 
 

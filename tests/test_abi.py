@@ -46,3 +46,22 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.rhmc_create(None, ctypes.byref(lat), 0) == 1
     assert lib.rhmc_workspace_bytes(None, 2, 4, 0) == 0
     assert lib.rhmc_destroy(None) == 0
+
+
+def test_python_constants_match_header():
+    """The tune keys and precision codes the binding names equal the header's enums,
+    and the library's key count covers every key the header declares."""
+    from paper_1808_01829_gb300 import _lib
+
+    with open(os.path.join(ROOT, "include", "rhmc.h")) as f:
+        src = f.read()
+    enums = {k: int(v) for k, v in re.findall(r"^\s*(RHMC_[A-Z0-9_]+)\s*=\s*(\d+)", src, re.M)}
+    for name in dir(_lib):
+        if name.startswith("RHMC_TUNE_") or name in ("RHMC_FP64", "RHMC_MIXED_FP32"):
+            assert enums[name] == getattr(_lib, name), name
+    with open(os.path.join(ROOT, "paper_1808_01829_gb300", "csrc", "common.cuh")) as f:
+        cuh = f.read()
+    body = cuh[cuh.index("TUNE_HOP_RHS_PER_THREAD = 0"):cuh.index("TUNE_NKEYS")]
+    internal = re.findall(r"^\s*(TUNE_[A-Z0-9_]+)", body, re.M)
+    header = sorted(((v, k) for k, v in enums.items() if k.startswith("RHMC_TUNE_")))
+    assert [k[len("RHMC_"):] for _, k in header] == internal

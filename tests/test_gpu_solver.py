@@ -279,6 +279,35 @@ def test_fp32_bulk_fma_forms(scalar, n):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_no_defect_correction_reports_true_residuals(precision):
+    """RHMC_TUNE_NO_DEFECT_CORRECTION = 1 with an iteration cap: NOT_CONVERGED, no
+    corrections, and the reported per-(shift, column) residuals are the true
+    relative residuals of the returned solutions (oracle operator)."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    dims, mass, n = (4, 4, 4, 8), 0.02, 4
+    shifts = [2e-3, 0.05, 1.0]
+    U = syn.random_links(dims, 0.5, 1260)
+    B = syn.gaussian_pseudofermions(dims, n, 2260)
+    ctx = make_ctx(dims, mass, U)
+    ctx.tune_set(_lib.RHMC_TUNE_NO_DEFECT_CORRECTION, 1)
+    Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-12, max_iter=18, precision=precision,
+                                       allow_not_converged=True)
+    ctx.tune_set(_lib.RHMC_TUNE_NO_DEFECT_CORRECTION, 0)
+    assert info.refinements == 0 and info.iters == 18
+    X = Xg.cpu().numpy()
+    bn = np.linalg.norm(B.reshape(-1, n), axis=0)
+    got = np.asarray(info.per_shift_resid).reshape(len(shifts), n)
+    for s, sig in enumerate(shifts):
+        R = B - oracle.apply_A(dims, mass, U, X[s], sigma=sig)
+        want = np.linalg.norm(R.reshape(-1, n), axis=0) / bn
+        assert np.allclose(got[s], want, rtol=1e-6, atol=0), (s, got[s], want)
+    assert got.max() > 1e-12  # 18 iterations do not reach the tolerance
+    ctx.close()
+
+
 def test_force_double_float_matches_native_fp64():
     """The double-float force path (built-in) and the native FP64 one
     (RHMC_TUNE_NATIVE_FP64_RESIDUALS) agree to 1e-12 from the same solutions,

@@ -6,7 +6,11 @@
 * the action against the dense eigendecomposition form phi^dagger R(A) phi;
 * gauge covariance G[U^g, g Phi] = g(x) G[U, Phi] g(x+mu)^dagger;
 * linearity in the rational coefficients alpha_s;
-* the sampled-link evaluation agrees with the full one.
+* the sampled-link evaluation agrees with the full one;
+* the Lie-algebra components F^a = Re tr(G^dagger T^a U) are the derivatives of
+  the action along U -> exp(w T^a) U, link by link (finite differences), and the
+  projection TA(U G^dagger) carries the same information: F = -2 sum_a F^a T^a,
+  sum_a (F^a)^2 / 2 = |F|_F^2 / 4.
 """
 import numpy as np
 import pytest
@@ -109,3 +113,49 @@ def test_force_at_matches_full():
     Gs = oracle.force_at(dims, U, X, [0.4, 1.3], links)
     for k, (lex, mu) in enumerate(links):
         np.testing.assert_allclose(Gs[k], G[lex, mu], atol=1e-13)
+
+
+def test_lie_components_are_single_link_derivatives():
+    """F^a at one link and generator = (S(exp(wT^a)U) - S(exp(-wT^a)U)) / 2w with only
+    that link rotated (dense solves), for several links and all eight generators."""
+    dims, mass = (2, 2, 2, 2), 0.1
+    U = syn.random_links(dims, 0.5, 1031)
+    Phi = syn.gaussian_pseudofermions(dims, 2, 2031)
+    G = oracle.force(dims, U, _solve(dims, mass, U, Phi), ALPHA).reshape(U.shape)
+    Fa = dense.lie_components(U, G)
+    lam = dense.gell_mann_matrices()
+    h = 1e-5
+    for (t, z, y, x, mu) in [(0, 0, 0, 0, 0), (1, 0, 1, 0, 3), (0, 1, 1, 1, 2)]:
+        for a in range(8):
+            w, v = np.linalg.eigh(lam[a] / 2)  # exp(i h lambda/2) = v exp(i h w) v^dagger
+
+            def S_at(hh):
+                Up = U.copy()
+                E = (v * np.exp(1j * hh * w)) @ v.conj().T
+                Up[t, z, y, x, mu] = E @ U[t, z, y, x, mu]
+                return dense.action(dims, mass, Up, Phi, ALPHA0, ALPHA, BETA)
+
+            fd = (S_at(h) - S_at(-h)) / (2 * h)
+            an = Fa[t, z, y, x, mu, a]
+            assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (t, z, y, x, mu, a, fd, an)
+
+
+def test_ta_projection_matches_components():
+    """TA(U G^dagger) = -2 sum_a F^a T^a, traceless and anti-Hermitian, and the norm
+    from the eight components equals |TA(U G^dagger)|_F^2 / 4 (random links, random G)."""
+    rng = np.random.default_rng(33)
+    U = syn.random_links((2, 2, 2, 4), 0.7, 1032)
+    G = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    F = dense.force_lie(U, G)
+    Fa = dense.lie_components(U, G)
+    T = 0.5j * dense.gell_mann_matrices()
+    assert np.allclose(F, -2 * np.einsum("...a,aij->...ij", Fa, T), atol=1e-13, rtol=0)
+    assert np.allclose(np.trace(F, axis1=-2, axis2=-1), 0, atol=1e-13)
+    assert np.allclose(F, -np.swapaxes(F.conj(), -1, -2), atol=1e-13)
+    assert abs(dense.force_norm2(U, G) - 0.25 * np.sum(np.abs(F) ** 2)) <= 1e-12 * dense.force_norm2(U, G)
+    # the Gell-Mann matrices: Hermitian, traceless, tr(l^a l^b) = 2 delta_ab, closed under [.,.] with f^123 = 1
+    lam = dense.gell_mann_matrices()
+    assert np.allclose(np.einsum("aij,bji->ab", lam, lam), 2 * np.eye(8), atol=1e-14)
+    assert np.allclose(lam, np.swapaxes(lam.conj(), -1, -2))
+    assert np.allclose(np.trace(lam, axis1=-2, axis2=-1), 0)
+    assert np.allclose(lam[0] @ lam[1] - lam[1] @ lam[0], 2j * lam[2])
