@@ -291,7 +291,7 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_NATIVE_FP64_RESIDUALS  mixed precision: compute the reliable-update and
  *                                 true residuals with native FP64 instead of RHMC_DF64
  *   RHMC_TUNE_UPDATE_TENSOR       mixed precision, shifted updates: on the tensor cores
- *                                 (tcgen05, 3xTF32, n_rhs = 16 only) = 1; CUDA-core kernel with
+ *                                 (tcgen05, three-piece TF32 split, n_rhs = 16 only) = 1; CUDA-core kernel with
  *                                 lane-owned row slices = 2; CUDA-core kernel with column-owner
  *                                 lanes and cp.async-staged row tiles = 0 (built-in: packed
  *                                 FP32x2 FMAs) or 3..11 (tile shape and FMA variants, see the

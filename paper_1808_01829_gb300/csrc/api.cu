@@ -314,7 +314,7 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   b.T64 = a.take<double2>(len);
   b.AP64 = a.take<double2>(len);
   b.rinv64 = a.take<double2>((size_t)n * n);
-  b.btiles = a.take<float>((size_t)ns * 2 * 64 * 32);
+  b.btiles = a.take<float>((size_t)ns * 3 * 64 * 32);
   b.partial = a.take<double2>((size_t)n * n);
   b.gscratch = a.take<double2>((size_t)kGramCtas * n * n);
   b.npart = a.take<double>((size_t)kParts * kMaxN);
@@ -399,10 +399,10 @@ static bool use_graphs() { return !prof_on() && tune_get(TUNE_GRAPHS) != 2; }
 // Tensor-core shifted updates: FP32 fields, 16 right-hand sides.
 template <typename T> static bool use_tensor_update(int n) {
   if (sizeof(T) != 4 || n != 16) return false;
-  // Built-in choice: CUDA cores.  Measured at 24^4: the tcgen05 (3xTF32) path
-  // leaves a larger FP32 drift in the shifted systems (phase-1 true residual
-  // 5.2e-6 against 4.4e-6), which costs more defect-correction iterations than
-  // the update saves.
+  // Built-in choice: CUDA cores.  Measured at 24^4: the tcgen05 kernel (one
+  // CTA per row tile, three-piece TF32 split) moves 2.1 TB/s against 4.5 for
+  // the packed CUDA-core kernel and its drift costs more defect correction
+  // (510 against 324 iterations).
   return tune_get(TUNE_UPDATE_TENSOR) == 1;
 }
 // Column-owner shifted updates (FP32): the built-in choice; RHMC_TUNE_UPDATE_TENSOR = 2

@@ -9,18 +9,25 @@
 //   B[2k+0][2j+1] = Im M_kj,  B[2k+1][2j+1] =  Re M_kj,
 // so that row (p_0re, p_0im, p_1re, ...) * B gives (y_0re, y_0im, ...) = p M.
 //
-// FP32 accuracy from TF32 inputs ("3xTF32"): every operand is split into a
-// TF32 head and a TF32 tail, a = ah + al with ah = rna_tf32(a), al =
-// rna_tf32(a - ah), and D = Ah Bh + Ah Bl + Al Bh accumulates in FP32 in tensor
-// memory (the Al Bl term is below FP32 rounding).
+// FP32 accuracy from TF32 inputs: every operand is split exactly into three
+// TF32 pieces, a = a0 + a1 + a2 with a0 = rna_tf32(a), a1 = rna_tf32(a - a0),
+// a2 = rna_tf32(a - a0 - a1) (each difference is exact in FP32 and the pieces
+// carry 11 + 11 + 2 significant bits), and D accumulates the six products
+// whose order is above 2^-33 of the result, smallest first:
+//   A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0,
+// in FP32 in tensor memory.  (A head + tail split keeps only about 22 of
+// FP32's 24 bits and shows up as a larger drift of the shifted systems.)
 //
-// Per CTA (128 threads, one row per thread): the threads write the split P
-// tile to shared memory in the 128-byte-swizzled K-major layout, copy the
-// (pre-laid-out) B tiles, one elected thread issues the 12 tcgen05.mma
-// (K = 32 in steps of 8, three products) and commits them to an mbarrier;
-// after a bounded wait the threads read their row of D with tcgen05.ld and
-// update X^(s) and P^(s).  A wait that does not finish within its iteration
-// limit sets an error flag; the kernel then frees its tensor memory and
+// Per CTA (128 threads, one row per thread, three CTAs per SM): the threads
+// load their rows of P^(s) and X^(s), write the split P tile to shared memory
+// in the 128-byte-swizzled K-major layout; the B pieces of the shift (laid out
+// once per iteration by k_tc_prepare_b) arrive by one bulk copy on an
+// mbarrier; one thread issues the 24 tcgen05.mma (K = 32 in steps of 8, six
+// products), commits them to a second mbarrier and, once they are done,
+// starts the bulk copy of the next shift's B pieces; the threads then read
+// their row of D with tcgen05.ld and write X^(s) and P^(s).  Every mbarrier
+// wait is bounded: one that gives up sets an error flag, the kernel waits
+// (bounded) for its copies and MMAs in flight, frees its tensor memory and
 // returns.
 #include <mutex>
 
@@ -114,7 +121,11 @@ constexpr long long kWaitCycles = 2000000000LL;  // about a second at the GPU's 
 
 }  // namespace
 
-// B tiles for every shift in [s_begin, s_end): [s][head, tail][64 x 32 floats,
+constexpr int kPieces = 3;
+constexpr int kBTile = kTcN * kTcK;                               // floats per B piece
+constexpr unsigned kBBytes = (unsigned)(kPieces * kBTile * sizeof(float));  // one shift's B pieces
+
+// B pieces for every shift in [s_begin, s_end): [s][piece][64 x 32 floats,
 // swizzled K-major, row n = output real index, k = input real index].
 __global__ void __launch_bounds__(256) k_tc_prepare_b(const float2 *__restrict__ coef, int s_begin, int s_end,
                                                       float *__restrict__ btiles) {
@@ -123,138 +134,169 @@ __global__ void __launch_bounds__(256) k_tc_prepare_b(const float2 *__restrict__
   constexpr int N = 16;
   const float2 *m1 = coef + (1 + 2 * s) * N * N;
   const float2 *m2 = m1 + N * N;
-  float *hi = btiles + (size_t)s * 2 * kTcN * kTcK;
-  float *lo = hi + kTcN * kTcK;
-  for (int e = threadIdx.x; e < kTcN * kTcK; e += blockDim.x) {
+  float *b0 = btiles + (size_t)s * kPieces * kBTile;
+  for (int e = threadIdx.x; e < kBTile; e += blockDim.x) {
     const int n = e / kTcK, k = e % kTcK;  // B[k][n]
     const float2 *M = n < 32 ? m1 : m2;
     const int j = (n & 31) >> 1, b = n & 1, kc = k >> 1, a = k & 1;
     const float2 z = M[kc * N + j];
     // (a, b): (re, re) -> Re, (im, re) -> -Im, (re, im) -> Im, (im, im) -> Re
     const float v = (a == b) ? z.x : (a == 1 ? -z.y : z.y);
-    const float h = tf32_rna(v);
+    const float p0 = tf32_rna(v);
+    const float r1 = v - p0;
+    const float p1 = tf32_rna(r1);
     const unsigned off = sw128(n, k) / 4;
-    hi[off] = h;
-    lo[off] = tf32_rna(v - h);
+    b0[off] = p0;
+    b0[kBTile + off] = p1;
+    b0[2 * kBTile + off] = tf32_rna(r1 - p1);
   }
 }
 
-__global__ void __launch_bounds__(kTcRows, 4) k_update_tc(const float2 *__restrict__ Q, float2 *__restrict__ P,
+__device__ __forceinline__ void mbar_expect_bulk(unsigned mbar, unsigned dst, const void *src, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kTcRows, 3) k_update_tc(const float2 *__restrict__ Q, float2 *__restrict__ P,
                                                        float2 *__restrict__ X, const float *__restrict__ btiles,
                                                        const int *__restrict__ upd, int s_begin, int s_end, long rows,
                                                        long fstride, int *__restrict__ err) {
-  // shared: A head/tail (16 KB each), B head/tail (8 KB each), all 1024-aligned
+  // shared: A pieces (3 x 16 KB), B pieces (3 x 8 KB, one bulk-copy target), all 1024-aligned
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *base = smem_raw;
   {  // align to 1024 bytes for the swizzle pattern
     const unsigned a = smem_u32(smem_raw);
     base += (1024 - (a & 1023)) & 1023;
   }
-  float *Ah = reinterpret_cast<float *>(base);
-  float *Al = Ah + kTcRows * kTcK;
-  float *Bh = Al + kTcRows * kTcK;
-  float *Bl = Bh + kTcN * kTcK;
-  __shared__ __align__(8) unsigned long long mbar;
+  float *As = reinterpret_cast<float *>(base);  // [3][128 x 32]
+  float *Bs = As + kPieces * kTcRows * kTcK;    // [3][64 x 32]
+  __shared__ __align__(8) unsigned long long mbar_mma, mbar_b;
   __shared__ unsigned tmem_base_sh;
-  __shared__ int ok_sh;
-  __shared__ int supd[kMaxS];
+  __shared__ int ok_sh, b_pending;
+  __shared__ int live[kMaxS];
+  __shared__ int nlive;
   const int tid = threadIdx.x, warp = tid >> 5;
-  for (int k = tid; k < s_end; k += blockDim.x) supd[k] = upd[k];
+  if (tid == 0) {
+    int m = 0;
+    for (int q = s_begin; q < s_end; ++q)
+      if (upd[q]) live[m++] = q;
+    nlive = m;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  const unsigned amma = smem_u32(&mbar_mma), ab = smem_u32(&mbar_b);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(amma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ab));
     asm volatile("fence.mbarrier_init.release.cluster;");
     ok_sh = 1;
+    b_pending = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const unsigned tmem = tmem_base_sh;
-  const unsigned mbar_addr = smem_u32(&mbar);
-  unsigned phase = 0;
-  const unsigned sAh = smem_u32(Ah), sAl = smem_u32(Al), sBh = smem_u32(Bh), sBl = smem_u32(Bl);
-  for (long tile = blockIdx.x; tile * kTcRows < rows && ok_sh; tile += gridDim.x) {
+  const int nl = nlive;
+  const unsigned sA = smem_u32(As), sB = smem_u32(Bs);
+  unsigned ph_mma = 0, ph_b = 0;
+  const long ntiles = (rows + kTcRows - 1) / kTcRows;
+  // the first work item's B pieces
+  if (tid == 0 && nl > 0 && blockIdx.x < ntiles) {
+    mbar_expect_bulk(ab, sB, btiles + (size_t)live[0] * kPieces * kBTile, kBBytes);
+    b_pending = 1;
+  }
+  for (long tile = blockIdx.x; tile < ntiles && nl > 0; tile += gridDim.x) {
     const long r = tile * kTcRows + tid;
-    const bool live = r < rows;
+    const bool rlive = r < rows;
     float q[kTcK];
-    if (live) {
+    {
       const float4 *src = reinterpret_cast<const float4 *>(Q + r * 16);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float4 v = src[c];
+        const float4 v = rlive ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         q[4 * c] = v.x, q[4 * c + 1] = v.y, q[4 * c + 2] = v.z, q[4 * c + 3] = v.w;
       }
     }
-    for (int s = s_begin; s < s_end; ++s) {
-      if (!supd[s]) continue;
+    int i = 0;
+    for (; i < nl; ++i) {
+      const int s = live[i];
       float2 *Ps = P + s * fstride;
-      // A tile: this thread's row, head and tail, swizzled
-      {
-        float4 pv[8];
-        if (live) {
-          const float4 *src = reinterpret_cast<const float4 *>(Ps + r * 16);
+      float2 *Xs = X + s * fstride;
+      float4 xv[8];
+      {  // this thread's rows of X^(s) and P^(s); P split into the three pieces, swizzled
+        const float4 *xsrc = reinterpret_cast<const float4 *>(Xs + r * 16);
+        const float4 *psrc = reinterpret_cast<const float4 *>(Ps + r * 16);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) pv[c] = src[c];
-        } else {
-#pragma unroll
-          for (int c = 0; c < 8; ++c) pv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int c = 0; c < 8; ++c) xv[c] = rlive ? xsrc[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const float4 v = pv[c];
-          const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-          const float4 l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z),
-                                       tf32_rna(v.w - h.w));
-          const unsigned off = sw128(tid, 4 * c);
-          *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(Ah) + off) = h;
-          *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(Al) + off) = l;
+          const float4 v = rlive ? psrc[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 p0 = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+          const float4 r1 = make_float4(v.x - p0.x, v.y - p0.y, v.z - p0.z, v.w - p0.w);
+          const float4 p1 = make_float4(tf32_rna(r1.x), tf32_rna(r1.y), tf32_rna(r1.z), tf32_rna(r1.w));
+          const float4 p2 = make_float4(tf32_rna(r1.x - p1.x), tf32_rna(r1.y - p1.y), tf32_rna(r1.z - p1.z),
+                                        tf32_rna(r1.w - p1.w));
+          unsigned char *a0 = reinterpret_cast<unsigned char *>(As) + sw128(tid, 4 * c);
+          *reinterpret_cast<float4 *>(a0) = p0;
+          *reinterpret_cast<float4 *>(a0 + kTcRows * kTcK * 4) = p1;
+          *reinterpret_cast<float4 *>(a0 + 2 * kTcRows * kTcK * 4) = p2;
         }
-      }
-      // B tiles (already in the swizzled layout): 16 KB copied by the CTA
-      {
-        const float4 *src = reinterpret_cast<const float4 *>(btiles + (size_t)s * 2 * kTcN * kTcK);
-        float4 *dst = reinterpret_cast<float4 *>(Bh);
-        for (int k = tid; k < 2 * kTcN * kTcK / 4; k += blockDim.x) dst[k] = src[k];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // K = 32 reals = 4 steps of 8 (32 bytes) inside the 128-byte swizzle atom
+        bool ok = mbar_wait_for(ab, ph_b, kWaitCycles);  // this shift's B pieces
+        b_pending = ok ? 0 : 1;
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          // products (A piece, B piece), smallest first
+          const int pa[6] = {2, 0, 1, 1, 0, 0}, pb[6] = {0, 2, 1, 0, 1, 0};
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const unsigned off = kk * 32;
-          mma_tf32(tmem, make_desc(sAh + off), make_desc(sBh + off), kk > 0);
-          mma_tf32(tmem, make_desc(sAh + off), make_desc(sBl + off), 1);
-          mma_tf32(tmem, make_desc(sAl + off), make_desc(sBh + off), 1);
+          for (int t = 0; t < 6; ++t)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {  // K = 32 reals = 4 steps of 8 (32 bytes) inside the swizzle atom
+              const unsigned aoff = sA + pa[t] * (kTcRows * kTcK * 4) + kk * 32;
+              const unsigned boff = sB + pb[t] * (kBTile * 4) + kk * 32;
+              mma_tf32(tmem, make_desc(aoff), make_desc(boff), (t > 0 || kk > 0) ? 1 : 0);
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(amma)
+                       : "memory");
+          ok = mbar_wait_for(amma, ph_mma, kWaitCycles);
+          if (!ok) mbar_wait_for(amma, ph_mma, kWaitCycles);  // one more bounded chance before memory is reused
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
-                     : "memory");
-        if (!mbar_wait_for(mbar_addr, phase, kWaitCycles)) {
+        if (!ok) {
           ok_sh = 0;
           atomicExch(err, 1);
-          // give the MMAs in flight one more bounded chance to land before the
-          // tensor memory is released
-          mbar_wait_for(mbar_addr, phase, kWaitCycles);
+        } else {
+          // the next work item's B pieces (the MMAs reading Bs are done)
+          const bool next_in_tile = i + 1 < nl;
+          const bool next_tile = tile + gridDim.x < ntiles;
+          if (next_in_tile || next_tile) {
+            const int sn = next_in_tile ? live[i + 1] : live[0];
+            mbar_expect_bulk(ab, sB, btiles + (size_t)sn * kPieces * kBTile, kBBytes);
+            b_pending = 1;
+          }
         }
       }
       __syncthreads();
-      phase ^= 1;
+      ph_b ^= 1;
+      ph_mma ^= 1;
       if (!ok_sh) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned d[64];
       RHMC_TMEM_LD64(tmem + ((unsigned)(warp * 32) << 16), d);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (live) {
-        float4 *xs = reinterpret_cast<float4 *>(X + s * fstride + r * 16);
+      if (rlive) {
+        float4 *xs = reinterpret_cast<float4 *>(Xs + r * 16);
         float4 *ps = reinterpret_cast<float4 *>(Ps + r * 16);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          float4 x = xs[c];
+          float4 x = xv[c];
           x.x += __uint_as_float(d[4 * c]);
           x.y += __uint_as_float(d[4 * c + 1]);
           x.z += __uint_as_float(d[4 * c + 2]);
@@ -266,28 +308,33 @@ __global__ void __launch_bounds__(kTcRows, 4) k_update_tc(const float2 *__restri
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
+      __syncthreads();  // tensor memory and the A pieces are rewritten by the next item
     }
+    if (!ok_sh) break;
   }
+  __syncthreads();
+  // a bulk copy still in flight (only after a failed wait) lands before the CTA's memory is released
+  if (tid == 0 && b_pending) mbar_wait_for(ab, ph_b, kWaitCycles);
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
 // Shifts [s_begin, s_end) with the tensor cores (mixed path, n = 16).
-// btiles: 2 * 64 * 32 floats per shift of scratch; err: device flag.
+// btiles: 3 * 64 * 32 floats per shift of scratch; err: device flag.
 rhmc_status_t update_shifts_tc(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
                                int s_begin, int s_end, long rows, long fstride, float *btiles, int *err,
                                cudaStream_t s) {
   if (s_end <= s_begin) return RHMC_OK;
+  if (((uintptr_t)btiles & 15) != 0) return RHMC_ERR_INVALID_ARG;  // bulk-copy source alignment
   k_tc_prepare_b<<<s_end - s_begin, 256, 0, s>>>(coef, s_begin, s_end, btiles);
   RHMC_LAUNCH_CHECK();
-  const size_t smem = 1024 + (size_t)(2 * kTcRows * kTcK + 2 * kTcN * kTcK) * sizeof(float);
+  const size_t smem = 1024 + (size_t)kPieces * (kTcRows * kTcK + kBTile) * sizeof(float);
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   const long tiles = (rows + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::min<long>(tiles, 4 * 152);
+  const int grid = (int)std::min<long>(tiles, resident_ctas(k_update_tc, kTcRows, smem));
   int nupd = s_end - s_begin;
   if (prof_on()) {
     int h[kMaxS];

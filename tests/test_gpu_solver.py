@@ -203,7 +203,7 @@ def test_mixed_residuals_native_fp64_and_double_float_agree():
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 4, 10)])
 def test_tensor_core_shift_update_matches_oracle(dims):
-    """Mixed solve at n_pf = 16 with the shifted updates on tcgen05 (3xTF32): same
+    """Mixed solve at n_pf = 16 with the shifted updates on tcgen05 (three-piece TF32 split): same
     oracle criteria as the CUDA-core path; both paths reach the tolerance."""
     need_gpu()
     from paper_1808_01829_gb300 import _lib
