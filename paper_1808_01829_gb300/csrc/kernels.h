@@ -19,7 +19,7 @@ struct SolverState {
   double2 G1[kSlots][kMaxN * kMaxN];
   double2 rho[kSlots][kMaxN * kMaxN];
   double2 delta[kSlots][kMaxN * kMaxN];
-  double2 beta_s[kMaxS][kMaxN * kMaxN];
+  double2 m2_s[kMaxS][kMaxN * kMaxN];   // beta^(s)_k rho_k^dagger of the last update of shift s
   double2 alpha_s[kMaxS][kMaxN * kMaxN];
   double sigma[kMaxS];        // shifts, ascending
   double d0[kMaxN];           // ||B e_j||

@@ -175,58 +175,62 @@ __device__ void inv_upper(const Cta &c, double2 *Ri, const double2 *R) {
 }
 
 // General inverse by Gauss-Jordan with partial pivoting.  A is destroyed.
+// Ai = A^-1 by Gauss-Jordan elimination with partial pivoting (A is destroyed).
+// Per pivot step: warp 0 finds the pivot row by a shuffle reduction, forms the
+// pivot reciprocal and the column of elimination factors; the rows are swapped
+// and the pivot row scaled; every other row is then updated from the factor
+// column and the pivot row.  Three barriers per step.
 __device__ bool inv_general(const Cta &c, double2 *Ai, double2 *A, int *piv, int *flag) {
   const int n = c.n;
+  __shared__ double2 fcol[kMaxN];
+  __shared__ double2 dinv;
   set_eye(c, Ai);
   for (int k = 0; k < n; ++k) {
-    if (c.t == 0) {
-      int p = k;
-      double best = A[k * n + k].x * A[k * n + k].x + A[k * n + k].y * A[k * n + k].y;
-      for (int r = k + 1; r < n; ++r) {
-        const double v = A[r * n + k].x * A[r * n + k].x + A[r * n + k].y * A[r * n + k].y;
-        if (v > best) {
-          best = v;
-          p = r;
+    if (c.t < 32) {
+      const int r = c.t;
+      const double2 a = (r < n) ? A[r * n + k] : make_double2(0.0, 0.0);
+      double v = (r >= k && r < n) ? a.x * a.x + a.y * a.y : -1.0;
+      int idx = r;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
         }
       }
-      *piv = p;
-      if (!(best > 0.0) || !isfinite(best)) *flag = 1;
+      const int p = __shfl_sync(0xffffffffu, idx, 0);
+      const double best = __shfl_sync(0xffffffffu, v, 0);
+      // elimination factor of row r after the swap: row p holds the old row k
+      const double2 akk = make_double2(__shfl_sync(0xffffffffu, a.x, k), __shfl_sync(0xffffffffu, a.y, k));
+      if (r < n) fcol[r] = (r == k) ? make_double2(0.0, 0.0) : (r == p ? akk : a);
+      if (r == 0) {
+        *piv = p;
+        if (!(best > 0.0) || !isfinite(best)) {
+          *flag = 1;
+        } else {
+          const double2 d = (p == k) ? akk : A[p * n + k];
+          const double rr = frcp(best);
+          dinv = make_double2(d.x * rr, -d.y * rr);
+        }
+      }
     }
     __syncthreads();
     if (*flag) return false;
     const int p = *piv;
-    if (p != k && c.t < 2 * n) {
+    if (c.t < 2 * n) {  // swap rows k and p, scale the new row k
       const int col = c.t % n;
       double2 *M = (c.t < n) ? A : Ai;
-      const double2 tmp = M[k * n + col];
-      M[k * n + col] = M[p * n + col];
-      M[p * n + col] = tmp;
-    }
-    __syncthreads();
-    __shared__ double2 dinv;
-    if (c.t == 0) {
-      const double2 d = A[k * n + k];
-      const double r = frcp(d.x * d.x + d.y * d.y);
-      dinv = make_double2(d.x * r, -d.y * r);
-    }
-    __syncthreads();
-    if (c.t < 2 * n) {
-      const int col = c.t % n;
-      double2 *M = (c.t < n) ? A : Ai;
-      M[k * n + col] = cmulz(M[k * n + col], dinv);
-    }
-    __syncthreads();
-    // eliminate column k from the other rows; factors read before any write
-    double2 fa = make_double2(0, 0), va = make_double2(0, 0), vi = make_double2(0, 0);
-    if (c.own && c.i != k) {
-      fa = A[c.i * n + k];
-      va = A[k * n + c.j];
-      vi = Ai[k * n + c.j];
+      const double2 rk = M[k * n + col], rp = M[p * n + col];
+      if (p != k) M[p * n + col] = rk;
+      M[k * n + col] = cmulz(rp, dinv);
     }
     __syncthreads();
     if (c.own && c.i != k) {
-      A[c.t] = csub(A[c.t], cmulz(fa, va));
-      Ai[c.t] = csub(Ai[c.t], cmulz(fa, vi));
+      const double2 f = fcol[c.i];
+      A[c.t] = csub(A[c.t], cmulz(f, A[k * n + c.j]));
+      Ai[c.t] = csub(Ai[c.t], cmulz(f, Ai[k * n + c.j]));
     }
     __syncthreads();
   }
@@ -435,8 +439,9 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
     const double2 e = make_double2(c.i == c.j ? 1.0 : 0.0, 0.0);
     st->alpha[0][c.t] = e;
     st->G1[0][c.t] = e;
+    const double2 rh = R[c.j * n + c.i];  // beta^(s)_0 rho_0^dagger = delta_0^dagger (beta^(s)_0 = 1)
     for (int s = 0; s < nshift; ++s) {
-      st->beta_s[s][c.t] = e;
+      st->m2_s[s][c.t] = make_double2(rh.x, -rh.y);
       st->alpha_s[s][c.t] = e;
     }
   }
@@ -562,11 +567,18 @@ __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int npa
   colnorms_upper(n, Dk, st->res[0], st->inv_d0, nullptr);
   if (t == 0) st->upd[0] = 1;
 }
-// lines 9-12 for shift s = blockIdx.x + 1.
+// lines 9-12 for shift s = blockIdx.x + 1.  With C = alpha_k rho_{k-1} alpha_{k-1}^-1
+// and M2_prev = beta^(s)_{k-1} rho_{k-1}^dagger (kept in FP64 from the last update):
+//   T = 1 + dsig alpha_k + C (1 - beta^(s)_{k-1}) rho_{k-1}^dagger
+//     = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,      beta^(s)_k = T^-1   (line 9)
+//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                                      (line 10)
+//   M1 = alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12),
+//   delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (the shifted residual).
+// Nine n x n products and one inverse per shift.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef,
                                                     double tol_shift, int freeze) {
-  __shared__ double2 Cp[NN], A1[NN], A2[NN], B[NN], Bi[NN];
+  __shared__ double2 Cs[NN], A1[NN], A2[NN], B[NN], Bi[NN];
   __shared__ int flag, piv;
   Cta c(n);
   const int s = blockIdx.x + 1;
@@ -579,40 +591,31 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   }
   if (c.t == 0) flag = 0;
   const double dsig = st->sigma[s] - st->sigma[0];
-  // coupling C = alpha_k rho_{k-1} alpha_{k-1}^-1, with alpha_{k-1}^-1 = Gram1_{k-1}
   mm(c, A1, st->alpha[cur], st->rho[prev]);
-  mm(c, Cp, A1, st->G1[prev]);
-  // T = 1 + dsig alpha_k + C (1 - beta_{k-1}) rho_{k-1}^dagger      (line 9)
-  if (c.own) {
-    const double2 b = st->beta_s[s][c.t];
-    A1[c.t] = make_double2((c.i == c.j ? 1.0 : 0.0) - b.x, -b.y);
-  }
-  __syncthreads();
-  mm(c, A2, Cp, A1);
-  mm(c, A1, A2, st->rho[prev], false, true);
+  mm(c, Cs, A1, st->G1[prev]);                        // C
+  mm(c, A2, Cs, st->rho[prev], false, true);          // C rho_{k-1}^dagger
+  mm(c, A1, Cs, st->m2_s[s]);                         // C M2_prev
   if (c.own) {
     const double2 a = st->alpha[cur][c.t];
-    B[c.t] = make_double2((c.i == c.j ? 1.0 : 0.0) + dsig * a.x + A1[c.t].x, dsig * a.y + A1[c.t].y);
+    B[c.t] = make_double2((c.i == c.j ? 1.0 : 0.0) + dsig * a.x + A2[c.t].x - A1[c.t].x,
+                          dsig * a.y + A2[c.t].y - A1[c.t].y);
   }
   __syncthreads();
   if (!inv_general(c, Bi, B, &piv, &flag)) {
     if (c.t == 0) st->breakdown = 4;
     return;
   }
-  // alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                        (line 10)
-  mm(c, A1, Bi, Cp);
-  mm(c, A2, A1, st->alpha_s[s]);
-  // M1 = alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12)
-  store_coef<T>(c, coef + (1 + 2 * s) * nn, A2, st->w1[s]);
-  mm(c, A1, Bi, st->rho[cur], false, true);
-  store_coef<T>(c, coef + (2 + 2 * s) * nn, A1);
+  mm(c, A2, Cs, st->alpha_s[s]);
+  mm(c, A1, Bi, A2);  // alpha^(s)_k
+  store_coef<T>(c, coef + (1 + 2 * s) * nn, A1, st->w1[s]);
+  mm(c, A2, Bi, st->rho[cur], false, true);  // beta^(s)_k rho_k^dagger
+  store_coef<T>(c, coef + (2 + 2 * s) * nn, A2);
   if (c.own) {
-    st->beta_s[s][c.t] = Bi[c.t];
-    st->alpha_s[s][c.t] = A2[c.t];
+    st->m2_s[s][c.t] = A2[c.t];
+    st->alpha_s[s][c.t] = A1[c.t];
   }
-  // shifted residual delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k = rho_k Gram1_k alpha^(s)_k
-  mm(c, A1, st->rho[cur], st->G1[cur]);
-  mm(c, B, A1, A2);
+  mm(c, Cs, st->rho[cur], st->G1[cur]);
+  mm(c, B, Cs, A1);  // delta^(s)_k
   __shared__ double colres[kMaxN];
   if (c.t < n) {
     const double r = colnorm(c, B, c.t) * st->inv_d0[c.t];
