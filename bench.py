@@ -52,6 +52,7 @@ WORKLOAD = {
 # by the units processed.  A kernel changed since its capture has no entry.
 TRAFFIC_RATIO = {
     "update_shifts_fp32": (0.960, "profiles/k_update_cols_16x16x16x32_n16.md (16^3x32, 15 shifts; scaled by bytes moved)"),
+    "hop_fp32": (0.942, "profiles/k_hop_pf_traffic_24x24x24x24_n16.md (24^4, both hop kinds; scaled by bytes moved)"),
 }
 # SBCGrQ iterations of the bench workload (24^4, 16 x 16, tol 1e-8) measured with
 # the library's FP64 path; the oracle runs the same recursion
@@ -348,6 +349,10 @@ def run_gpu(args):
         roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
         roof["traffic_source"] = src
     roof_dslash = roofline.entry(stats, "hop_fp32") if "hop_fp32" in stats else None
+    if roof_dslash and "hop_fp32" in TRAFFIC_RATIO:
+        ratio, src = TRAFFIC_RATIO["hop_fp32"]
+        roof_dslash["traffic"] = ratio * roof_dslash["algorithmic_bytes_per_launch"]
+        roof_dslash["traffic_source"] = src
 
     # ---- comparison: per-vector FP64 multishift CG + force (Fig. 9 analogue)
     base = None
