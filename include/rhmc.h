@@ -319,6 +319,18 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_NO_DEFECT_CORRECTION  1: no defect corrections after the multishift phase; the
  *                                 FP64 true residuals it left are reported (info) and shifts
  *                                 above tol give NOT_CONVERGED (for convergence studies)
+ *   RHMC_TUNE_BASIS_ITERS         mixed precision, several shifts: the block basis Q_k is kept for
+ *                                 up to this many iterations (V/2 * 3 * n_rhs * 8 bytes each,
+ *                                 counted by rhmc_workspace_bytes) and the shifted solutions are
+ *                                 assembled from it at the end of the multishift phase instead of
+ *                                 updating P^(s), X^(s) every iteration; a solve that runs longer
+ *                                 switches to the updates at that point.  0 = built-in (up to 384
+ *                                 iterations within a quarter of the device memory, off below
+ *                                 24), 1 = off, >= 2 = that capacity
+ *   RHMC_TUNE_BASIS_GEMM          the assembly's GEMM: 0 = FP32-accurate tensor-core emulation
+ *                                 (BF16x9), 1 = FP32 on the CUDA cores
+ *   RHMC_TUNE_BASIS_CHUNK         the assembly sums FP32 partial products over this many basis
+ *                                 blocks and adds them in FP64 (0: one GEMM)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -334,7 +346,10 @@ enum {
   RHMC_TUNE_LINKS12 = 10,
   RHMC_TUNE_SHIFT_FREEZE_NANO = 11,
   RHMC_TUNE_AXPY_SCALAR = 12,
-  RHMC_TUNE_NO_DEFECT_CORRECTION = 13
+  RHMC_TUNE_NO_DEFECT_CORRECTION = 13,
+  RHMC_TUNE_BASIS_ITERS = 14,
+  RHMC_TUNE_BASIS_GEMM = 15,
+  RHMC_TUNE_BASIS_CHUNK = 16
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

@@ -22,6 +22,9 @@ RHMC_MAX_SHIFTS = 64
 RHMC_TUNE_UPDATE_TENSOR = 6
 RHMC_TUNE_AXPY_SCALAR = 12
 RHMC_TUNE_NO_DEFECT_CORRECTION = 13
+RHMC_TUNE_BASIS_ITERS = 14
+RHMC_TUNE_BASIS_GEMM = 15
+RHMC_TUNE_BASIS_CHUNK = 16
 
 STATUS = {
     0: "OK",

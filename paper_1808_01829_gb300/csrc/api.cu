@@ -178,6 +178,7 @@ struct rhmc_ctx {
   int tune[TUNE_NKEYS] = {};       // per-context launch settings (0: the process-wide value)
   std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
   double *d_parts = nullptr;       // partial sums of rhmc_force_lie's norm (kParts)
+  void *cublas = nullptr;          // library GEMM handle of the stored-basis assembly
 };
 
 namespace rhmc {
@@ -295,7 +296,44 @@ struct SolveBufs {
   double *npart;
   SolverState *st;
   int accumulate = 0;  // shifts s >= 1 add w_s X^(s) into one field after X^(0) (FP64)
+  // stored-basis mode (mixed, several shifts): the block basis Q_0 .. Q_{cap-1}
+  // (rows x cap*n, row-major), the per-iteration shift coefficients and the
+  // real-embedded assembly matrix; basis == nullptr: shifted updates in HBM
+  float2 *basis = nullptr;
+  double2 *hist = nullptr;
+  float *ccat = nullptr;
+  int cap = 0;
 };
+
+// Iterations the stored basis holds (RHMC_TUNE_BASIS_ITERS; 0: off).
+// Stored-basis capacity.  RHMC_TUNE_BASIS_ITERS: 0 = built-in, 1 = off, >= 2 = that
+// many iterations.  Built-in: up to kBasisCapMax blocks within a quarter of the
+// device's memory, off when fewer than kBasisCapMin would fit.  The base update of
+// the column-owner path stores the blocks, so the lane-slice kernel turns it off.
+constexpr int kBasisCapMax = 384, kBasisCapMin = 24;
+static size_t device_total_memory() {
+  static std::mutex mu;
+  static std::map<int, size_t> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  cudaDeviceProp p{};
+  const size_t total = cudaGetDeviceProperties(&p, dev) == cudaSuccess ? p.totalGlobalMem : 0;
+  cache[dev] = total;
+  return total;
+}
+static int basis_cap(const Geom &g, int n, int ns, bool mixed) {
+  if (!mixed || ns < 2 || tune_get(TUNE_UPDATE_TENSOR) == 2) return 0;
+  const int v = tune_get(TUNE_BASIS_ITERS);
+  if (v == 1) return 0;
+  if (v >= 2) return v;
+  const size_t block = (size_t)g.Vh * 3 * n * sizeof(float2);
+  const size_t fit = (device_total_memory() / 4) / std::max<size_t>(block, 1);
+  const int cap = (int)std::min<size_t>(fit, kBasisCapMax);
+  return cap >= kBasisCapMin ? cap : 0;
+}
 
 static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, SolveBufs &b) {
   const size_t len = (size_t)g.Vh * 3 * n;
@@ -319,6 +357,13 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
   b.gscratch = a.take<double2>((size_t)kGramCtas * n * n);
   b.npart = a.take<double>((size_t)kParts * kMaxN);
   b.st = a.take<SolverState>(1);
+  const int cap = basis_cap(g, n, ns, mixed);
+  if (cap > 0) {
+    b.cap = cap;
+    b.basis = a.take<float2>((size_t)g.Vh * 3 * cap * n);
+    b.hist = a.take<double2>((size_t)cap * ns * 2 * n * n);
+    b.ccat = a.take<float>((size_t)(cap + 1) * 2 * n * (ns - 1) * 2 * n);
+  }
 }
 
 // Phase-2 buffers live above the (dead) phase-1 buffers of the top-level solve.
@@ -447,6 +492,8 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
   if (cols) {
     RHMC_TRY(axpy_cols((const float2 *)W, nullptr, (const float2 *)b.coef, (float2 *)Qcur, rows, n, s));
+    if (b.basis)  // block k of the stored basis (k from the device counter: graph replays)
+      RHMC_TRY(basis_store_dev((const float2 *)Qcur, b.basis, rows, n, b.cap, &b.st->kabs[k % kSlots], s));
     RHMC_TRY(update_shifts_cols((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                 b.st->upd, 0, 1, rows, n, len, s));
   } else {
@@ -457,8 +504,10 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
       RHMC_CUDA_TRY(cudaEventRecord(c->ev_base[k % 3], s));
       RHMC_CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_base[k % 3], 0));
     }
-    RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, ss));
-    if (use_tensor_update<T>(n))
+    RHMC_TRY(nxn_shifts<T>(n, ns, b.st, k, (C<T> *)b.coef, tol_shift, freeze, b.hist, b.cap, ss));
+    if (b.basis) {
+      // stored-basis mode: the shifted solutions are assembled at the end
+    } else if (use_tensor_update<T>(n))
       RHMC_TRY(update_shifts_tc((const float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
                                 b.st->upd, 1, ns, rows, len, b.btiles, &b.st->device_timeout, ss));
     else if (cols)
@@ -582,11 +631,48 @@ struct PhaseTimer {
 // Returns OK when the recursive residuals reached the target (phase 1 only).
 template <typename T>
 static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, const double *shifts, double2 *X,
-                                  const SolveParams &prm, const SolveBufs &b, SolveStats &stats, cudaStream_t s) {
+                                  const SolveParams &prm, const SolveBufs &b0, SolveStats &stats, cudaStream_t s) {
   const bool mixed = std::is_same<T, float>::value;
   const long rows = c->g.Vh * 3;
   const long len = rows * n;
   const double sigma0 = shifts[0];
+  // stored-basis mode (mixed, several shifts, not accumulating): b.basis set
+  SolveBufs b = b0;
+  if (!mixed || ns < 2 || b.accumulate) b.basis = nullptr, b.hist = nullptr, b.cap = 0;
+  // X^(s) += sum_i Q_i C_i (want_p = 0), or P^(s) = sum_{i <= K} Q_i D_i (want_p = 1),
+  // for s >= 1 from the stored basis; the unused FP32 increments of s >= 1 are the
+  // GEMM's output and are zero again afterwards
+  auto assemble = [&](int K, int want_p) -> rhmc_status_t {
+    if (K <= 0 && !want_p) return RHMC_OK;
+    if (!c->cublas) RHMC_TRY(basis_handle_create(&c->cublas));
+    float2 *tmp = (float2 *)b.Xinc + len;
+    RHMC_TRY(basis_coefficients(n, ns, b.st, b.hist, K, want_p, b.ccat, s));
+    const int emul = tune_get(TUNE_BASIS_GEMM) != 1;
+    if (want_p) {
+      RHMC_TRY(basis_gemm(c->cublas, b.basis, b.ccat, tmp, rows, n, b.cap, K + 1, ns, emul, s));
+      RHMC_TRY(basis_scatter(tmp, nullptr, (float2 *)b.P, rows, n, ns, len, s));
+    } else {
+      // X^(s) from one GEMM, or in FP64 from FP32 partial sums over RHMC_TUNE_BASIS_CHUNK
+      // blocks each (smaller FP32 rounding of long sums, at one more pass over X per chunk)
+      const long m = (long)(ns - 1) * 2 * n;
+      const int chunk = tune_get(TUNE_BASIS_CHUNK) > 0 ? tune_get(TUNE_BASIS_CHUNK) : K;
+      for (int c0 = 0; c0 < K; c0 += chunk) {
+        const int nb = std::min(chunk, K - c0);
+        RHMC_TRY(basis_gemm(c->cublas, b.basis + (size_t)c0 * n, b.ccat + (size_t)c0 * 2 * n * m, tmp, rows, n,
+                            b.cap, nb, ns, emul, s));
+        RHMC_TRY(basis_scatter(tmp, X, nullptr, rows, n, ns, len, s));
+      }
+    }
+    RHMC_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(float2) * len * (ns - 1), s));
+    return RHMC_OK;
+  };
+  // end of the stored-basis mode at iteration K: the shifted solutions so far into X
+  auto finish_basis = [&](int K) -> rhmc_status_t {
+    if (!b.basis) return RHMC_OK;
+    RHMC_TRY(assemble(K, 0));
+    b.basis = nullptr, b.hist = nullptr, b.cap = 0;
+    return RHMC_OK;
+  };
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   // accumulating solve: X^(0) and one field for sum_{s>=1} w_s X^(s)
   RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * (b.accumulate ? std::min(ns, 2) : ns), s));
@@ -605,6 +691,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   for (int q = 0; q < ns; ++q)
     RHMC_CUDA_TRY(cudaMemcpyAsync((C<T> *)b.P + q * len, b.Qb[0], sizeof(C<T>) * len, cudaMemcpyDeviceToDevice, s));
   if (mixed) RHMC_CUDA_TRY(cudaMemsetAsync(b.Xinc, 0, sizeof(float2) * len * ns, s));
+  if (b.basis) RHMC_TRY(basis_store((const float2 *)b.Qb[0], b.basis, rows, n, b.cap, 0, s));
   if (prm.acc_w) RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->w1, prm.acc_w, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   StateView v;
   RHMC_TRY(read_state(c, b.st, v, s));
@@ -631,6 +718,12 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   while (k < kmax) {
     const int chunk = prm.fixed_iters > 0 ? kmax : std::min(check_every, kmax - k);
     const int freeze = prm.fixed_iters > 0 ? 0 : 1;
+    if (b.basis && k + chunk > b.cap - 1) {
+      // the basis is full: X^(s) and P^(s) from it, then the shifted updates in HBM
+      RHMC_TRY(assemble(k, 0));
+      RHMC_TRY(assemble(k, 1));
+      b.basis = nullptr, b.hist = nullptr, b.cap = 0;
+    }
     const bool graph = use_graphs() && chunk == kCheckEvery && check_every == kCheckEvery && k > 0 &&
                        k % kCheckEvery == 0;
     if (graph)
@@ -667,6 +760,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     }
     if (mixed && converged && !prm.verify_at_convergence) {
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      RHMC_TRY(finish_basis(k));
       stats.iters = k;
       return RHMC_OK;
     }
@@ -679,12 +773,15 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       RHMC_TRY((convert<double, float>(b.R64, (float2 *)b.W, len, s)));
       RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.gscratch, b.partial, s));
       RHMC_TRY(nxn_reliable<float>(b.partial, kGramParts, n, b.st, k, (float2 *)b.mw, s));
+      // (the stored basis keeps the replaced block: P^(s)_k was formed from it, and the
+      // new Q_k enters the shifted systems only through the base recursion from k + 1 on)
       RHMC_TRY((block_axpy<float, float>((float2 *)b.W, nullptr, (float2 *)b.mw, (float2 *)b.Qb[k & 1], rows, n, s)));
       stats.dirac++;
       stats.reliable++;
       RHMC_TRY(read_state(c, b.st, v, s));
       if (v.breakdown) {
         // the true residual is numerically zero: every column has converged
+        RHMC_TRY(finish_basis(k));
         stats.iters = k;
         return RHMC_OK;
       }
@@ -692,18 +789,21 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       for (int j = 0; j < n; ++j) base = std::max(base, v.res[0][j]);
       res_at_reliable = base;
       if (base < target && shifts_done) {
+        RHMC_TRY(finish_basis(k));
         stats.iters = k;
         return RHMC_OK;
       }
       continue;
     }
     if (converged) {
+      RHMC_TRY(finish_basis(k));
       stats.iters = k;
       return RHMC_OK;
     }
   }
   if (mixed)
     for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+  RHMC_TRY(finish_basis(k));
   stats.iters = k;
   if (prm.fixed_iters > 0) return RHMC_OK;
   set_error("not converged after %d iterations", k);
@@ -1033,6 +1133,7 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
   c->main.release();
   if (c->pool) cudaFree(c->pool);
   if (c->d_parts) cudaFree(c->d_parts);
+  basis_handle_destroy(c->cublas);
   for (int q = 0; q < 3; ++q) {
     if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);

@@ -120,6 +120,9 @@ enum TuneKey {
   TUNE_SHIFT_FREEZE_NANO,     // mixed: freeze shifted systems below this recursive residual (x 1e-9; 0: built-in)
   TUNE_AXPY_SCALAR,           // mixed: scalar FP32 FMAs in the Y = C + A M kernels (1); packed FP32x2 (0)
   TUNE_NO_DEFECT_CORRECTION,  // 1: report the true residuals after the multishift phase, no corrections
+  TUNE_BASIS_ITERS,           // mixed: stored-basis capacity in iterations (0: built-in, 1: off)
+  TUNE_BASIS_GEMM,            // stored-basis assembly GEMM: FP32-accurate tensor-core emulation (0) or FP32 (1)
+  TUNE_BASIS_CHUNK,           // stored-basis assembly: blocks per FP32 partial sum (0: one GEMM)
   TUNE_NKEYS
 };
 int tune_get(int key);

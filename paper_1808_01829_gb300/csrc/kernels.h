@@ -28,6 +28,8 @@ struct SolverState {
   double res[kMaxS][kMaxN];   // recursive relative residual per shift and column (s = 0: base)
   int active[kMaxS];          // shift still being updated
   int upd[kMaxS];             // shift updated in the current iteration
+  int last_k[kMaxS];          // last iteration that updated shift s (stored-basis mode)
+  int kabs[kSlots];           // absolute iteration number of slot k % kSlots (graph replays reuse k's slot)
   int breakdown;              // nonzero: which coefficient step failed
   int device_timeout;         // a bounded device-side wait expired
 };
@@ -92,9 +94,33 @@ template <typename T>
 rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *mw, cudaStream_t s);
 template <typename T>
 rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef, cudaStream_t s);
+// hist (nullable, stored-basis mode): [cap][nshift][2][n*n] FP64, alpha^(s)_k and
+// beta^(s)_k rho_k^dagger recorded at iteration k < cap
 template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
-                         cudaStream_t s);
+                         double2 *hist, int cap, cudaStream_t s);
+// Stored-basis mode: coefficient matrices of the basis expansion of X^(s)
+// (want_p = 0: X^(s) = sum_{i < last_s} Q_i C_i, C_i = alpha_{i+1} + M2_{i+1} C_{i+1})
+// or of P^(s)_K (want_p = 1: P^(s)_K = sum_{i <= K} Q_i D_i, D_K = 1,
+// D_i = M2_{i+1} D_{i+1}), written FP32 real-embedded into Ccat
+// [(K + 1) * 2n rows][(nshift - 1) * 2n columns] (row-major).
+rhmc_status_t basis_coefficients(int n, int nshift, const SolverState *st, const double2 *hist, int K, int want_p,
+                                 float *Ccat, cudaStream_t s);
+// Q (rows x n) into column block k of the basis (rows x cap*n, row-major)
+rhmc_status_t basis_store(const float2 *Q, float2 *basis, long rows, int n, int cap, int k, cudaStream_t s);
+// the same with the block index read from *kdev (an iteration counter in device memory)
+rhmc_status_t basis_store_dev(const float2 *Q, float2 *basis, long rows, int n, int cap, const int *kdev,
+                              cudaStream_t s);
+// tmp (rows x (nshift - 1) n complex) = basis blocks 0 .. nblk-1 times Ccat (library GEMM;
+// emulated: FP32-accurate BF16x9 tensor-core emulation, else FP32 CUDA cores)
+rhmc_status_t basis_gemm(void *handle, const float2 *basis, const float *Ccat, float2 *tmp, long rows, int n,
+                         int cap, int nblk, int nshift, int emulated, cudaStream_t s);
+rhmc_status_t basis_handle_create(void **handle);
+void basis_handle_destroy(void *handle);
+// X^(s) (FP64, [nshift][rows*n]) += / P^(s) (FP32) = the assembled block of shift s
+// from tmp (rows x (nshift - 1) * n complex, row-major), shifts 1 .. nshift - 1
+rhmc_status_t basis_scatter(const float2 *tmp, double2 *X, float2 *P, long rows, int n, int nshift, long fstride,
+                            cudaStream_t s);
 template <typename T>
 rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *rinv,
                            cudaStream_t s);

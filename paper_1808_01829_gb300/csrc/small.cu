@@ -449,7 +449,9 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
     st->d0[c.t] = nrm[c.t];
     st->inv_d0[c.t] = frcp_fast(nrm[c.t] > 0.0 ? nrm[c.t] : 1.0);
   }
+  if (c.t < kSlots) st->kabs[c.t] = 0;
   if (c.t < nshift) {
+    st->last_k[c.t] = 0;
     st->active[c.t] = 1;
     st->upd[c.t] = 0;
     st->w1[c.t] = 1.0;
@@ -474,6 +476,7 @@ __global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int n
   const int cur = k % kSlots;
   const int t = c.t, nt = blockDim.x, nn = n * n;
   reduce_partials(c, A, partial, nparts);
+  if (t == 0) st->kabs[cur] = st->kabs[(k - 1) % kSlots] + 1;
   // Gram1_k (Hermitian part) for the shifted step
   if (c.own) {
     const double2 a = A[t], b = A[c.j * n + c.i];
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int npa
 // Nine n x n products and one inverse per shift.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef,
-                                                    double tol_shift, int freeze) {
+                                                    double tol_shift, int freeze, double2 *hist, int cap) {
   __shared__ double2 Cs[NN], A1[NN], A2[NN], B[NN], Bi[NN];
   __shared__ int flag, piv;
   Cta c(n);
@@ -590,6 +593,7 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
     return;
   }
   if (c.t == 0) flag = 0;
+  const int kabs = st->kabs[cur];
   const double dsig = st->sigma[s] - st->sigma[0];
   mm(c, A1, st->alpha[cur], st->rho[prev]);
   mm(c, Cs, A1, st->G1[prev]);                        // C
@@ -613,7 +617,13 @@ __global__ void __launch_bounds__(256) k_nxn_shifts(int n, int nshift, SolverSta
   if (c.own) {
     st->m2_s[s][c.t] = A2[c.t];
     st->alpha_s[s][c.t] = A1[c.t];
+    if (hist && kabs < cap) {
+      double2 *h = hist + ((size_t)kabs * nshift + s) * 2 * nn;
+      h[c.t] = A1[c.t];
+      h[nn + c.t] = A2[c.t];
+    }
   }
+  if (c.t == 0) st->last_k[s] = kabs;
   mm(c, Cs, st->rho[cur], st->G1[cur]);
   mm(c, B, Cs, A1);  // delta^(s)_k
   __shared__ double colres[kMaxN];
@@ -681,10 +691,10 @@ rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st
 }
 template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
-                         cudaStream_t s) {
+                         double2 *hist, int cap, cudaStream_t s) {
   if (nshift > 1) {
     prof_begin(PROF_NXN_SHIFTS, s);
-    k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze);
+    k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze, hist, cap);
     prof_end(s, 0.0);
     RHMC_LAUNCH_CHECK();
   }
@@ -704,7 +714,8 @@ rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverStat
   template rhmc_status_t nxn_qr_init<T>(const double2 *, int, int, int, SolverState *, C<T> *, cudaStream_t); \
   template rhmc_status_t nxn_alpha<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);   \
   template rhmc_status_t nxn_rho<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);     \
-  template rhmc_status_t nxn_shifts<T>(int, int, SolverState *, int, C<T> *, double, int, cudaStream_t);      \
+  template rhmc_status_t nxn_shifts<T>(int, int, SolverState *, int, C<T> *, double, int, double2 *, int,     \
+                                       cudaStream_t);                                                            \
   template rhmc_status_t nxn_reliable<T>(const double2 *, int, int, SolverState *, int, C<T> *, cudaStream_t);
 RHMC_INST_NXN(float)
 RHMC_INST_NXN(double)

@@ -216,6 +216,7 @@ def test_tensor_core_shift_update_matches_oracle(dims):
     ctx = make_ctx(dims, mass, U)
     Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
     try:
+        lib.rhmc_tune_set(14, 1)  # shifted updates in HBM (no stored basis)
         for mode in (1, 2):
             lib.rhmc_tune_set(6, mode)
             Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-8, precision="mixed")
@@ -223,6 +224,7 @@ def test_tensor_core_shift_update_matches_oracle(dims):
             _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-8, Xo)
     finally:
         lib.rhmc_tune_set(6, 0)
+        lib.rhmc_tune_set(14, 0)
     ctx.close()
 
 
@@ -242,9 +244,11 @@ def test_shifted_update_kernels_many_shifts(variant):
     ctx = make_ctx(dims, mass, U)
     try:
         lib.rhmc_tune_set(6, variant)
+        lib.rhmc_tune_set(14, 1)  # shifted updates in HBM (no stored basis)
         Xg, info = ctx.block_multishift_cg(to_gpu(B), shifts, 1e-9, precision="mixed")
     finally:
         lib.rhmc_tune_set(6, 0)
+        lib.rhmc_tune_set(14, 0)
     assert info.true_rel_resid_max <= 1e-9
     Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, shifts, tol=1e-13, max_iter=20000)
     assert rc == 0
@@ -305,6 +309,37 @@ def test_no_defect_correction_reports_true_residuals(precision):
         want = np.linalg.norm(R.reshape(-1, n), axis=0) / bn
         assert np.allclose(got[s], want, rtol=1e-6, atol=0), (s, got[s], want)
     assert got.max() > 1e-12  # 18 iterations do not reach the tolerance
+    ctx.close()
+
+
+@pytest.mark.parametrize("cap,gemm,chunk", [(256, 0, 0), (256, 1, 0), (256, 0, 5), (14, 0, 0), (1, 0, 0)])
+def test_stored_basis_assembly_matches_oracle(cap, gemm, chunk):
+    """Mixed solve with the shifted solutions assembled from the stored block basis
+    (RHMC_TUNE_BASIS_ITERS): both assembly GEMMs, FP64 sums of 5-block partial
+    products, a capacity of 14 iterations (the solve switches to the shifted
+    updates part way) and the mode off (1); every shift matches the oracle."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    dims, mass, n = (4, 4, 4, 8), 0.03, 16
+    ra = rational_approx(-1.0 / 64, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1270)
+    B = syn.gaussian_pseudofermions(dims, n, 2270)
+    ctx = make_ctx(dims, mass, U)
+    ctx.tune_set(_lib.RHMC_TUNE_BASIS_ITERS, cap)
+    ctx.tune_set(_lib.RHMC_TUNE_BASIS_GEMM, gemm)
+    ctx.tune_set(_lib.RHMC_TUNE_BASIS_CHUNK, chunk)
+    try:
+        Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-9, precision="mixed")
+    finally:
+        for key in (_lib.RHMC_TUNE_BASIS_ITERS, _lib.RHMC_TUNE_BASIS_GEMM, _lib.RHMC_TUNE_BASIS_CHUNK):
+            ctx.tune_set(key, 0)
+    assert info.true_rel_resid_max <= 1e-9
+    if cap == 14:
+        assert info.iters > 14
+    Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13, max_iter=20000)
+    assert rc == 0
+    _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-9, Xo)
     ctx.close()
 
 
