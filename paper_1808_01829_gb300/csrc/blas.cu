@@ -1052,6 +1052,7 @@ static void launch_axpy_gram_cols(const float2 *A, const float2 *C, const float2
                                                                   smem)));
   k_axpy_gram_cols<N, kAxpyRows, W, PK><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, (int)grid, out);
+  count_launch();  // the second kernel of this launcher (the caller counts the first)
 }
 
 // Y = C + A M and out = Y^dagger Y (FP64 sums of FP32 products) in one pass over
@@ -1187,6 +1188,7 @@ static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratc
   else
     k_gram<T, N, false, PK><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, grid, out);
+  count_launch();  // the second kernel of this launcher (the caller counts the first)
 }
 
 // packed FMAs for FP32 at n = 16 unless RHMC_TUNE_AXPY_SCALAR = 1
