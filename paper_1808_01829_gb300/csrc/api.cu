@@ -1162,6 +1162,9 @@ rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *c, const void *U, rhmc_stream_t sv) {
 
 size_t rhmc_workspace_bytes(const rhmc_ctx_t *c, int n, int ns, rhmc_precision_t p) {
   if (!c || n < 1 || n > RHMC_MAX_NRHS || ns < 1 || ns > RHMC_MAX_SHIFTS) return 0;
+  // sized under the context's own settings and device, as its solves lay it out
+  DeviceGuard dg(c->device);
+  TuneScope tscope(c);
   const bool mixed = p == RHMC_MIXED_FP32;
   // solve with an internal X (unsorted shifts or force) + force's Y fields
   const size_t len = (size_t)c->g.Vh * 3 * n;
