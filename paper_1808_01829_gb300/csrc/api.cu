@@ -553,7 +553,9 @@ static rhmc_status_t run_chunk(rhmc_ctx *c, const SolveBufs &b, double2 *X, int 
 template <typename T>
 static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X, int n, int ns, double sigma0,
                                      int chunk_start, int len, double target, int freeze, cudaStream_t s) {
-  std::vector<double> key = {(double)(uintptr_t)b.P, (double)(uintptr_t)X, (double)b.accumulate, (double)n,
+  // (b.basis: chunks with and without the stored basis record different kernels)
+  std::vector<double> key = {(double)(uintptr_t)b.P, (double)(uintptr_t)X, (double)(uintptr_t)b.basis,
+                             (double)b.accumulate, (double)n,
                              (double)ns, sigma0, target, (double)freeze, (double)sizeof(T), (double)len,
                              (double)(chunk_start % kCheckEvery)};
   for (int t = 0; t < TUNE_NKEYS; ++t) key.push_back((double)tune_get(t));

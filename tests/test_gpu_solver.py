@@ -335,6 +335,9 @@ def test_stored_basis_assembly_matches_oracle(cap, gemm, chunk):
         for key in (_lib.RHMC_TUNE_BASIS_ITERS, _lib.RHMC_TUNE_BASIS_GEMM, _lib.RHMC_TUNE_BASIS_CHUNK):
             ctx.tune_set(key, 0)
     assert info.true_rel_resid_max <= 1e-9
+    # every shift kept being updated to the end of the multishift phase (after a switch
+    # from the stored basis too): what is left for the corrections is FP32 drift
+    assert info.phase1_rel_resid_max <= 1e-4
     if cap == 14:
         assert info.iters > 14
     Xo, _, rc = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13, max_iter=20000)
