@@ -4,6 +4,8 @@ Hot path of de Forcrand & Keegan, arXiv:1808.01829, as hand-written CUDA for
 sm_103a behind the C ABI in include/rhmc.h (librhmc.so).  Submodules:
 
 * ``api``        torch-facing binding of the C ABI (RhmcContext)
+* ``functional`` the same entry points as functions of the link tensor
+                 (apply_mdagm, block_multishift_cg, force, PseudofermionAction.apply)
 * ``action``     torch.autograd.Function for the pseudofermion action / force
 * ``remez``      rational approximation coefficients of Eq. (RA) (host set-up)
 * ``synthetic``  seeded synthetic gauge fields and pseudofermions
