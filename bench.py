@@ -258,6 +258,28 @@ def run_batch(dev, reps=3):
     return res
 
 
+# ------------------------------------------------------------------ hop widths
+def dslash_widths(ctx, dev, widths=(1, 2, 4, 8, 16), reps=10):
+    """FP32 hop at several right-hand-side widths on the bench lattice (the width-1
+    against width-n comparison of Sec. IV.B, Fig. 8): microseconds and algorithmic
+    GB/s per launch from the library's event profiler.  The launches alternate
+    between the two parities, so the two link sets (2 x 96 MB at 24^4) exceed L2."""
+    import torch
+
+    from paper_1808_01829_gb300 import roofline
+
+    out = []
+    for n in widths:
+        X = torch.randn(ctx.Vh, 3, n, dtype=torch.complex128, device=dev)
+        ctx.hop(X, 1, precision="fp32")
+        stats = roofline.profile(lambda: [ctx.hop(X, r & 1, precision="fp32") for r in range(reps)])
+        e = roofline.entry(stats, "hop_fp32")
+        out.append({"n_rhs": n, "us_per_launch": round(e["us_per_launch"], 2), "GB/s": round(e["achieved"], 1),
+                    "frac": round(e["frac"], 3)})
+        del X
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -372,6 +394,13 @@ def run_gpu(args):
     if not args.no_batch and not args.small:
         batch = run_batch(dev)
 
+    widths = None
+    if rank == 0 and not args.small:
+        try:
+            widths = dslash_widths(ctx, dev)
+        except Exception as e:  # a measurement beside the bench line: it never fails the line
+            widths = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         t_iter, t_force, threads = cpu_sample(cfg, U, Phi, ra)
@@ -394,6 +423,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "roofline": roof,
             "roofline_dslash": roof_dslash,
+            "dslash_widths": widths,
             "kernel_table": kt,
             "clocks": clk,
             "solver": {"iters": last.iters, "dirac_calls": last.dirac_calls, "reliable_updates": last.reliable_updates,
