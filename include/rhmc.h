@@ -109,7 +109,11 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *ctx);
 rhmc_status_t rhmc_set_gauge(rhmc_ctx_t *ctx, const void *U_dev, rhmc_stream_t s);
 
 /* Bytes of device workspace that rhmc_block_multishift_cg / rhmc_force need
- * for this problem size; 0 on invalid arguments. */
+ * for this problem size, under the context's launch settings; 0 on invalid
+ * arguments.  In mixed precision with several shifts this includes the stored
+ * block basis (RHMC_TUNE_BASIS_ITERS: built in, up to 384 blocks of
+ * V/2 * 3 * n_rhs * 8 bytes within a quarter of the device memory, e.g.
+ * 24.5 GB at 24^4, n_rhs = 16); RHMC_TUNE_BASIS_ITERS = 1 sizes without it. */
 size_t rhmc_workspace_bytes(const rhmc_ctx_t *ctx, int n_rhs, int n_shifts, rhmc_precision_t p);
 
 /* Y = (A + sigma) X for an n_rhs-wide block (multi-RHS operator, each link
