@@ -305,7 +305,6 @@ struct SolveBufs {
   int cap = 0;
 };
 
-// Iterations the stored basis holds (RHMC_TUNE_BASIS_ITERS; 0: off).
 // Stored-basis capacity.  RHMC_TUNE_BASIS_ITERS: 0 = built-in, 1 = off, >= 2 = that
 // many iterations.  Built-in: up to kBasisCapMax blocks within a quarter of the
 // device's memory, off when fewer than kBasisCapMin would fit.  The base update of
