@@ -5,7 +5,9 @@ operator is written here on the *full* lattice with ``np.roll`` shifts,
 M = 2m + D is formed as a dense matrix, and the even-odd operator is read off
 as the even-even block of M^dagger M (the even-odd preconditioning of Sec. IV),
 instead of being composed from two hops.  Solves are dense LU, spectra dense
-eigendecompositions, and derivatives central finite differences.
+eigendecompositions, and derivatives central finite differences.  The
+Lie-algebra components of the force, F^a = Re tr(G^dagger T^a U) with the
+Gell-Mann generators written out here, give the force norm of Sec. II.
 
 Normalisation (the paper fixes none; this is the reading used throughout):
 (D psi)(x) = sum_mu eta_mu(x) [b_mu(x) U_mu(x) psi(x+mu) - b_mu(x-mu) U_mu(x-mu)^dagger psi(x-mu)],
