@@ -7,6 +7,8 @@
   minimiser of Tr[E^dagger (A + sigma_s) E] over the block Krylov space
   {B, A B, ..., A^(k-1) B} (Sec. III: BCG minimises this trace; the Krylov
   space is shift invariant), computed by explicit projection;
+* one shift (N_s = 1) is BCGrQ: the smallest shift's iterates do not depend on the
+  other shifts;
 * a duplicated shift gives identical solutions; the true residual is below the
   tolerance; the rigorous bound ||X - X*|| <= ||R|| / (lambda_min + sigma);
 * breakdown and non-convergence are reported, not crashed on.
@@ -145,3 +147,17 @@ def test_thin_qr():
     Qn, Rn = np.linalg.qr(B)
     ph = np.diag(Rn) / np.abs(np.diag(Rn))
     np.testing.assert_allclose(Q, Qn * ph[None, :], atol=1e-12)
+
+
+def test_single_shift_is_bcgrq():
+    """N_s = 1 reduces SBCGrQ to BCGrQ: the smallest shift's iterates do not depend on
+    the other shifts (the base recursion never reads them), so a fixed number of
+    iterations gives the same X^(0) with or without them, to rounding of the same
+    operations."""
+    dims, mass, n = (4, 4, 4, 4), 0.05, 3
+    U, B = _setup(dims, n, seed=7)
+    for iters in (1, 7, 20):
+        X1, _, rc1 = oracle.sbcgrq(dims, mass, U, B, [SHIFTS[0]], fixed_iters=iters)
+        Xm, _, rcm = oracle.sbcgrq(dims, mass, U, B, SHIFTS, fixed_iters=iters)
+        assert rc1 == 0 and rcm == 0
+        assert np.linalg.norm(X1[0] - Xm[0]) <= 1e-14 * np.linalg.norm(Xm[0])
