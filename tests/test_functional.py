@@ -68,3 +68,23 @@ def test_calls_forward_to_the_context(fake):
 def test_rejects_bad_link_shape(fake):
     with pytest.raises(ValueError):
         functional.context_for(torch.zeros(16, 4, 3, 3, dtype=torch.complex128), 0.1)
+
+
+def test_binding_argument_checks():
+    """The binding rejects host tensors, wrong dtypes, non-contiguous and misshaped
+    fields before any library call."""
+    from paper_1808_01829_gb300 import api
+
+    X = torch.zeros(8, 3, 2, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="CUDA"):
+        api._check_field(X, "X", (8, 3, 2))  # a host tensor
+    if torch.cuda.is_available():  # pragma: no cover - the GPU box
+        Xd = X.cuda()
+        api._check_field(Xd, "X", (8, 3, 2))
+        with pytest.raises(ValueError, match="complex128"):
+            api._check_field(Xd.to(torch.complex64), "X")
+        with pytest.raises(ValueError, match="contiguous"):
+            api._check_field(Xd.transpose(0, 1), "X")
+        with pytest.raises(ValueError, match="shape"):
+            api._check_field(Xd, "X", (8, 3, 3))
+    assert list(api.PRECISION) == ["fp64", "mixed", "fp32", "df64"]
