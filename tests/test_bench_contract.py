@@ -27,3 +27,5 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["e2e"]["d2h_bytes_per_step"] == 0 and d["config"]["workload"]
+    one = d["cpu_baseline"]["one_thread"]
+    assert one["value"] > 0 and "1 thread" in one["sample"]
