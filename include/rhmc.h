@@ -364,6 +364,17 @@ enum {
  * path is broken. */
 rhmc_status_t rhmc_selftest_bounded_wait(int device, double seconds, rhmc_stream_t s);
 
+/* Measurement helper (no counterpart in the paper): the arithmetic peaks of
+ * the CUDA cores of `device`, in TFLOP/s, for scalar FP32 FMA, packed FP32x2
+ * FMA (fma.rn.f32x2, two lanes per instruction) and FP64 FMA.  Each is the
+ * best of five launches of independent FMA chains filling every SM (2 flops
+ * per FMA lane), timed with CUDA events on stream s after one warm-up launch;
+ * about 50 ms in all.  They are the denominators of the FP32 and FP64 roofline
+ * fractions (double-float operator, n x n coefficient chain, FP64 baseline).
+ * The call synchronises s.  INVALID_ARG for a null output pointer. */
+rhmc_status_t rhmc_probe_alu_peaks(int device, double *fp32_tflops, double *fp32x2_tflops, double *fp64_tflops,
+                                   rhmc_stream_t s);
+
 /* The same settings for one context only (they take precedence over the
  * process-wide ones in every call on ctx, including the concurrent solves of
  * rhmc_block_multishift_cg_batch, so each ensemble can run its own tuned

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import colrel, make_ctx, need_gpu, to_gpu
+from gpu_util import check_solution, colrel, make_ctx, need_gpu, to_gpu
 from paper_1808_01829_gb300 import synthetic as syn
 from paper_1808_01829_gb300.remez import rational_approx
 
@@ -19,15 +19,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _check_solution(dims, mass, U, B, shifts, Xg, tol, Xo):
-    bn = np.linalg.norm(B.reshape(-1, B.shape[-1]), axis=0)
-    for s, sig in enumerate(shifts):
-        R = B - oracle.apply_A(dims, mass, U, Xg[s], sigma=sig)
-        rn = np.linalg.norm(R.reshape(-1, B.shape[-1]), axis=0) / bn
-        assert np.all(rn <= tol), (s, sig, rn)
-        err = np.linalg.norm((Xg[s] - Xo[s]).reshape(-1, B.shape[-1]), axis=0)
-        xn = np.linalg.norm(Xo[s].reshape(-1, B.shape[-1]), axis=0)
-        bound = tol * bn / (4 * mass ** 2 + sig) + 1e-10 * xn
-        assert np.all(err <= bound), (s, sig, err / bound)
+    check_solution(dims, mass, U, B, shifts, Xg, tol, Xo)
 
 
 CONFIGS = [
