@@ -277,7 +277,8 @@ long long rhmc_kernel_launches(void);
 enum {
   RHMC_PROF_HOP_FP32 = 0, RHMC_PROF_HOP_FP64, RHMC_PROF_GRAM_FP32, RHMC_PROF_GRAM_FP64, RHMC_PROF_BLOCK_AXPY,
   RHMC_PROF_UPDATE_FP32, RHMC_PROF_UPDATE_FP64, RHMC_PROF_NXN, RHMC_PROF_FORCE, RHMC_PROF_OTHER,
-  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_UPDATE_TC, RHMC_PROF_UPDATE_SHIFTS32, RHMC_PROF_NCAT
+  RHMC_PROF_HOP_DF, RHMC_PROF_NXN_SHIFTS, RHMC_PROF_UPDATE_TC, RHMC_PROF_UPDATE_SHIFTS32,
+  RHMC_PROF_BASIS_TC, RHMC_PROF_NCAT
 };
 rhmc_status_t rhmc_profile_enable(int on);
 
@@ -331,8 +332,11 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 switches to the updates at that point.  0 = built-in (up to 384
  *                                 iterations within a quarter of the device memory, off below
  *                                 24), 1 = off, >= 2 = that capacity
- *   RHMC_TUNE_BASIS_GEMM          the assembly's GEMM: 0 = FP32-accurate tensor-core emulation
- *                                 (BF16x9), 1 = FP32 on the CUDA cores
+ *   RHMC_TUNE_BASIS_GEMM          the assembly's contraction: 0 = tcgen05 tensor-core kernel (FP16
+ *                                 pieces of the scaled FP32 operands, three products, FP32
+ *                                 accumulation moved to a correctly rounded running sum every 48
+ *                                 MMAs, written into the FP64 solutions), 1 = CUDA-core kernel
+ *                                 (FP32 products, FP64 sum over blocks)
  *   RHMC_TUNE_BASIS_CHUNK         the assembly sums FP32 partial products over this many basis
  *                                 blocks and adds them in FP64 (0: one GEMM)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */

@@ -38,7 +38,8 @@ STATUS = {
 
 
 PROF_CATEGORIES = ["hop_fp32", "hop_fp64", "gram_fp32", "gram_fp64", "block_axpy", "update_fp32", "update_fp64",
-                   "nxn", "force", "other", "hop_df", "nxn_shifts", "update_tc", "update_shifts_fp32"]
+                   "nxn", "force", "other", "hop_df", "nxn_shifts", "update_tc", "update_shifts_fp32",
+                   "basis_tc"]
 
 
 class RhmcError(RuntimeError):

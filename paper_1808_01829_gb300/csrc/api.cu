@@ -178,7 +178,6 @@ struct rhmc_ctx {
   int tune[TUNE_NKEYS] = {};       // per-context launch settings (0: the process-wide value)
   std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
   double *d_parts = nullptr;       // partial sums of rhmc_force_lie's norm (kParts)
-  void *cublas = nullptr;          // library GEMM handle of the stored-basis assembly
 };
 
 namespace rhmc {
@@ -298,10 +297,10 @@ struct SolveBufs {
   int accumulate = 0;  // shifts s >= 1 add w_s X^(s) into one field after X^(0) (FP64)
   // stored-basis mode (mixed, several shifts): the block basis Q_0 .. Q_{cap-1}
   // (rows x cap*n, row-major), the per-iteration shift coefficients and the
-  // real-embedded assembly matrix; basis == nullptr: shifted updates in HBM
+  // assembly's operands; basis == nullptr: shifted updates in HBM
   float2 *basis = nullptr;
   double2 *hist = nullptr;
-  float *ccat = nullptr;
+  BasisBufs asmb;
   int cap = 0;
 };
 
@@ -327,10 +326,11 @@ static int basis_cap(const Geom &g, int n, int ns, bool mixed) {
   if (!mixed || ns < 2 || tune_get(TUNE_UPDATE_TENSOR) == 2) return 0;
   const int v = tune_get(TUNE_BASIS_ITERS);
   if (v == 1) return 0;
-  if (v >= 2) return v;
+  // even, so that every basis row (cap * 2n floats) starts on a 16-byte boundary
+  if (v >= 2) return v & ~1;
   const size_t block = (size_t)g.Vh * 3 * n * sizeof(float2);
   const size_t fit = (device_total_memory() / 4) / std::max<size_t>(block, 1);
-  const int cap = (int)std::min<size_t>(fit, kBasisCapMax);
+  const int cap = (int)std::min<size_t>(fit, kBasisCapMax) & ~1;
   return cap >= kBasisCapMin ? cap : 0;
 }
 
@@ -361,7 +361,13 @@ static void layout_solve(Arena &a, const Geom &g, int n, int ns, bool mixed, Sol
     b.cap = cap;
     b.basis = a.take<float2>((size_t)g.Vh * 3 * cap * n);
     b.hist = a.take<double2>((size_t)cap * ns * 2 * n * n);
-    b.ccat = a.take<float>((size_t)(cap + 1) * 2 * n * (ns - 1) * 2 * n);
+    b.asmb.basis = b.basis;
+    b.asmb.hist = b.hist;
+    b.asmb.cap = cap;
+    b.asmb.cf = a.take<double2>((size_t)(ns - 1) * (cap + 1) * n * n);
+    b.asmb.bpack = a.take<unsigned char>(basis_pack_bytes(n, ns, cap));
+    b.asmb.bscale = a.take<double>((size_t)ns);
+    b.asmb.tile_nkt = a.take<int>((size_t)ns);
   }
 }
 
@@ -640,38 +646,26 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   // stored-basis mode (mixed, several shifts, not accumulating): b.basis set
   SolveBufs b = b0;
   if (!mixed || ns < 2 || b.accumulate) b.basis = nullptr, b.hist = nullptr, b.cap = 0;
-  // X^(s) += sum_i Q_i C_i (want_p = 0), or P^(s) = sum_{i <= K} Q_i D_i (want_p = 1),
-  // for s >= 1 from the stored basis; the unused FP32 increments of s >= 1 are the
-  // GEMM's output and are zero again afterwards
+  // X^(s) = sum_i Q_i C_i (want_p = 0), or P^(s) = sum_{i <= K} Q_i D_i (want_p = 1),
+  // for s >= 1 from the stored basis (tcgen05 kernel whose epilogue writes the FP64
+  // solutions; RHMC_TUNE_BASIS_CHUNK: FP32 partial sums over that many blocks).  X^(s),
+  // s >= 1, is zero until then: the shifted increments are not updated in this mode.
   auto assemble = [&](int K, int want_p) -> rhmc_status_t {
     if (K <= 0 && !want_p) return RHMC_OK;
-    if (!c->cublas) RHMC_TRY(basis_handle_create(&c->cublas));
-    float2 *tmp = (float2 *)b.Xinc + len;
-    RHMC_TRY(basis_coefficients(n, ns, b.st, b.hist, K, want_p, b.ccat, s));
-    const int emul = tune_get(TUNE_BASIS_GEMM) != 1;
-    if (want_p) {
-      RHMC_TRY(basis_gemm(c->cublas, b.basis, b.ccat, tmp, rows, n, b.cap, K + 1, ns, emul, s));
-      RHMC_TRY(basis_scatter(tmp, nullptr, (float2 *)b.P, rows, n, ns, len, s));
-    } else {
-      // X^(s) from one GEMM, or in FP64 from FP32 partial sums over RHMC_TUNE_BASIS_CHUNK
-      // blocks each (smaller FP32 rounding of long sums, at one more pass over X per chunk)
-      const long m = (long)(ns - 1) * 2 * n;
-      const int chunk = tune_get(TUNE_BASIS_CHUNK) > 0 ? tune_get(TUNE_BASIS_CHUNK) : K;
-      for (int c0 = 0; c0 < K; c0 += chunk) {
-        const int nb = std::min(chunk, K - c0);
-        RHMC_TRY(basis_gemm(c->cublas, b.basis + (size_t)c0 * n, b.ccat + (size_t)c0 * 2 * n * m, tmp, rows, n,
-                            b.cap, nb, ns, emul, s));
-        RHMC_TRY(basis_scatter(tmp, X, nullptr, rows, n, ns, len, s));
-      }
-    }
-    RHMC_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(float2) * len * (ns - 1), s));
-    return RHMC_OK;
+    return basis_assemble(b.asmb, n, ns, b.st, rows, K, want_p, X, (float2 *)b.P, len, tune_get(TUNE_BASIS_CHUNK),
+                          tune_get(TUNE_BASIS_GEMM) == 1, &b.st->device_timeout, s);
   };
   // end of the stored-basis mode at iteration K: the shifted solutions so far into X
   auto finish_basis = [&](int K) -> rhmc_status_t {
     if (!b.basis) return RHMC_OK;
     RHMC_TRY(assemble(K, 0));
     b.basis = nullptr, b.hist = nullptr, b.cap = 0;
+    StateView vf;
+    RHMC_TRY(read_state(c, b.st, vf, s));
+    if (vf.device_timeout) {
+      set_error("a bounded device-side wait expired in the stored-basis assembly");
+      return RHMC_ERR_DEVICE_TIMEOUT;
+    }
     return RHMC_OK;
   };
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
@@ -1134,7 +1128,6 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
   c->main.release();
   if (c->pool) cudaFree(c->pool);
   if (c->d_parts) cudaFree(c->d_parts);
-  basis_handle_destroy(c->cublas);
   for (int q = 0; q < 3; ++q) {
     if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);

@@ -1,6 +1,7 @@
 // Internal definitions shared by the library's translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,7 +101,8 @@ void count_launch();
 // algorithmic bytes.  No-ops when profiling is off.
 enum ProfCat {
   PROF_HOP32 = 0, PROF_HOP64, PROF_GRAM32, PROF_GRAM64, PROF_AXPY, PROF_UPDATE32, PROF_UPDATE64,
-  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_UPDATE_TC, PROF_UPDATE_SHIFTS32, PROF_NCAT
+  PROF_NXN, PROF_FORCE, PROF_OTHER, PROF_HOP_DF, PROF_NXN_SHIFTS, PROF_UPDATE_TC, PROF_UPDATE_SHIFTS32,
+  PROF_BASIS_TC, PROF_NCAT
 };
 bool prof_on();
 
@@ -121,7 +123,7 @@ enum TuneKey {
   TUNE_AXPY_SCALAR,           // mixed: scalar FP32 FMAs in the Y = C + A M kernels (1); packed FP32x2 (0)
   TUNE_NO_DEFECT_CORRECTION,  // 1: report the true residuals after the multishift phase, no corrections
   TUNE_BASIS_ITERS,           // mixed: stored-basis capacity in iterations (0: built-in, 1: off)
-  TUNE_BASIS_GEMM,            // stored-basis assembly GEMM: FP32-accurate tensor-core emulation (0) or FP32 (1)
+  TUNE_BASIS_GEMM,            // stored-basis assembly: FP32-accurate tcgen05 kernel (0) or CUDA-core kernel (1)
   TUNE_BASIS_CHUNK,           // stored-basis assembly: blocks per FP32 partial sum (0: one GEMM)
   TUNE_NKEYS
 };

@@ -99,28 +99,36 @@ rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st
 template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
                          double2 *hist, int cap, cudaStream_t s);
-// Stored-basis mode: coefficient matrices of the basis expansion of X^(s)
-// (want_p = 0: X^(s) = sum_{i < last_s} Q_i C_i, C_i = alpha_{i+1} + M2_{i+1} C_{i+1})
-// or of P^(s)_K (want_p = 1: P^(s)_K = sum_{i <= K} Q_i D_i, D_K = 1,
-// D_i = M2_{i+1} D_{i+1}), written FP32 real-embedded into Ccat
-// [(K + 1) * 2n rows][(nshift - 1) * 2n columns] (row-major).
-rhmc_status_t basis_coefficients(int n, int nshift, const SolverState *st, const double2 *hist, int K, int want_p,
-                                 float *Ccat, cudaStream_t s);
+// Stored-basis mode (basis.cu).  Buffers of the assembly: the block basis
+// (rows x cap*n FP32 complex, row-major), the recorded per-iteration shift
+// coefficients hist [cap][nshift][2][n*n] (alpha^(s)_k, beta^(s)_k rho_k^dagger),
+// FP64 expansion coefficients cf [nshift-1][cap+1][n*n], the packed FP16 operand
+// tiles of the tensor-core kernel (basis_pack_bytes), per-shift scales and per-tile
+// K extents.
+struct BasisBufs {
+  float2 *basis = nullptr;
+  double2 *hist = nullptr;
+  double2 *cf = nullptr;
+  unsigned char *bpack = nullptr;
+  double *bscale = nullptr;  // [nshift]
+  int *tile_nkt = nullptr;   // [nshift]
+  int cap = 0;
+};
+size_t basis_pack_bytes(int n, int nshift, int cap);
+// want_p = 0: X^(s) = sum_{i < last_s} Q_i C_i for s = 1 .. nshift-1 (FP64, C_i = alpha_{i+1}
+// + M2_{i+1} C_{i+1}; X^(s), s >= 1, is overwritten: it is zero before the one assembly of a
+// solve); want_p = 1: P^(s) = sum_{i <= K} Q_i D_i (FP32, D_K = 1, D_i = M2_{i+1} D_{i+1}),
+// active shifts only.  chunk_blocks > 0 (X only): FP32 partial sums over about that many
+// blocks, added in FP64.  simt: CUDA-core kernel instead of tcgen05.  err: device flag set
+// when a bounded wait of the tensor-core kernel gave up.
+rhmc_status_t basis_assemble(const BasisBufs &bb, int n, int nshift, const SolverState *st, long rows, int K,
+                             int want_p, double2 *X, float2 *P, long fstride, int chunk_blocks, int simt, int *err,
+                             cudaStream_t s);
 // Q (rows x n) into column block k of the basis (rows x cap*n, row-major)
 rhmc_status_t basis_store(const float2 *Q, float2 *basis, long rows, int n, int cap, int k, cudaStream_t s);
 // the same with the block index read from *kdev (an iteration counter in device memory)
 rhmc_status_t basis_store_dev(const float2 *Q, float2 *basis, long rows, int n, int cap, const int *kdev,
                               cudaStream_t s);
-// tmp (rows x (nshift - 1) n complex) = basis blocks 0 .. nblk-1 times Ccat (library GEMM;
-// emulated: FP32-accurate BF16x9 tensor-core emulation, else FP32 CUDA cores)
-rhmc_status_t basis_gemm(void *handle, const float2 *basis, const float *Ccat, float2 *tmp, long rows, int n,
-                         int cap, int nblk, int nshift, int emulated, cudaStream_t s);
-rhmc_status_t basis_handle_create(void **handle);
-void basis_handle_destroy(void *handle);
-// X^(s) (FP64, [nshift][rows*n]) += / P^(s) (FP32) = the assembled block of shift s
-// from tmp (rows x (nshift - 1) * n complex, row-major), shifts 1 .. nshift - 1
-rhmc_status_t basis_scatter(const float2 *tmp, double2 *X, float2 *P, long rows, int n, int nshift, long fstride,
-                            cudaStream_t s);
 template <typename T>
 rhmc_status_t nxn_reliable(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *rinv,
                            cudaStream_t s);
