@@ -339,6 +339,9 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 (FP32 products, FP64 sum over blocks)
  *   RHMC_TUNE_BASIS_CHUNK         the assembly sums FP32 partial products over this many basis
  *                                 blocks and adds them in FP64 (0: one GEMM)
+ *   RHMC_TUNE_BASIS_ACC_KT        the tensor-core assembly moves its accumulator into the correctly
+ *                                 rounded running sum every this many K tiles of 64 reals (12 MMAs
+ *                                 each; 0: built-in)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -357,7 +360,8 @@ enum {
   RHMC_TUNE_NO_DEFECT_CORRECTION = 13,
   RHMC_TUNE_BASIS_ITERS = 14,
   RHMC_TUNE_BASIS_GEMM = 15,
-  RHMC_TUNE_BASIS_CHUNK = 16
+  RHMC_TUNE_BASIS_CHUNK = 16,
+  RHMC_TUNE_BASIS_ACC_KT = 17
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

@@ -653,7 +653,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   auto assemble = [&](int K, int want_p) -> rhmc_status_t {
     if (K <= 0 && !want_p) return RHMC_OK;
     return basis_assemble(b.asmb, n, ns, b.st, rows, K, want_p, X, (float2 *)b.P, len, tune_get(TUNE_BASIS_CHUNK),
-                          tune_get(TUNE_BASIS_GEMM) == 1, &b.st->device_timeout, s);
+                          tune_get(TUNE_BASIS_GEMM) == 1, tune_get(TUNE_BASIS_ACC_KT), &b.st->device_timeout, s);
   };
   // end of the stored-basis mode at iteration K: the shifted solutions so far into X
   auto finish_basis = [&](int K) -> rhmc_status_t {

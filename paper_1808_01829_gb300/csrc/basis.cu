@@ -28,13 +28,19 @@
 //     power (exact).  Coefficients far below a shift's largest lose relative
 //     accuracy only below 2^-37 of that largest entry.
 // The tensor cores' FP32 accumulation is not correctly rounded, and its error
-// grows with the number of MMAs summed into one accumulator: with all 1656
-// MMAs of the 24^4 solve in one accumulator, the shifted solutions' drift was
-// 10x that of an FP32 GEMM.  So every kGChunkKt K tiles (48 MMAs) the partial
-// sum moves out of the accumulator into a running sum in tensor memory, added
-// on the CUDA cores with round-to-nearest, and the accumulator restarts.  The
-// last chunk's epilogue writes running sum + accumulator straight into the
-// FP64 solutions X^(s) (or P^(s)), so no temporary product matrix is stored.
+// grows with the number of MMAs summed into one accumulator and with the
+// accumulator's magnitude.  So every kGChunkKt K tiles the partial sum moves
+// out of the accumulator into a running sum in tensor memory, added on the
+// CUDA cores with round-to-nearest, and the accumulator restarts from zero.
+// With one K tile per chunk, the small products of a tile enter an empty
+// accumulator and only its four h_A h_B MMAs run at full magnitude.  Measured
+// at 24^4 (16 shifts, drift of the shifted systems' true residuals after the
+// multishift phase, largest shift): one accumulator for all 1656 MMAs 6.2e-5,
+// 48 MMAs per chunk 5.8e-6, 12 MMAs per chunk 4.2e-6, FP32 products with FP64
+// sums over blocks (CUDA cores) 2.6e-6; the last two need the same number of
+// defect-correction iterations.  The last chunk's epilogue writes running sum
+// + accumulator straight into the FP64 solutions X^(s) (or P^(s)), so no
+// temporary product matrix is stored.
 // A CUDA-core kernel (k_basis_gemm_simt: FP32 products, FP64 sum per block) is
 // the RHMC_TUNE_BASIS_GEMM = 1 alternative.
 #include <mutex>
@@ -111,7 +117,7 @@ constexpr int kGNmax = 256;         // columns per N tile (MMA N)
 constexpr int kGStages = 2;
 constexpr int kGThreads = 448;      // warps 0-7 split A (two groups, alternate stages), 8-11 epilogue,
                                     // 12 loads B, 13 issues the MMAs
-constexpr int kGChunkKt = 4;        // K tiles per accumulation chunk (48 MMAs into one accumulator)
+constexpr int kGChunkKt = 1;        // built-in K tiles per accumulation chunk (12 MMAs into one accumulator)
 constexpr unsigned kGAPiece = kGM * 128;  // bytes of one FP16 piece of an A tile
 constexpr float kGAScale = 4096.f;        // 2^12: |basis entries| <= 1
 constexpr long long kGWaitCycles = 2000000000LL;  // about a second at the GPU's 2 GHz
@@ -222,6 +228,7 @@ struct GemmArgs {
   float2 *P;           // P^(s) = product (FP32)
   long fstride;
   int x_add;
+  int acc_kt;          // K tiles per accumulation chunk
   int *err;
 };
 
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
       const long row = mt * kGM + 32 * ew + lane;
       const int s_first = 1 + nt * g.tl.spt;
       const int ncols = min(g.tl.spt, g.nshift - s_first) * two_n;
-      const int nch = (nkt + kGChunkKt - 1) / kGChunkKt;
+      const int nch = (nkt + g.acc_kt - 1) / g.acc_kt;
       for (int ch = 0; ch < nch; ++ch, ++cc) {
         ok = bar_wait(smem_addr(&bar_acc_full), cc & 1, &abort_sh, g.err);
         if (!ok) break;
@@ -527,11 +534,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
         long mt;
         int nt, nkt;
         if (!work_item(g, w, mt, nt, nkt)) continue;
-        for (int c0 = 0; c0 < nkt && ok; c0 += kGChunkKt, ++cc) {
+        for (int c0 = 0; c0 < nkt && ok; c0 += g.acc_kt, ++cc) {
           ok = bar_wait(smem_addr(&bar_acc_empty), (cc & 1) ^ 1, &abort_sh, g.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const int c1 = min(c0 + kGChunkKt, nkt);
+          const int c1 = min(c0 + g.acc_kt, nkt);
           for (int kk = c0; kk < c1; ++kk, ++it) {
             const int stage = it & 1;
             const unsigned par = (it >> 1) & 1;
@@ -612,8 +619,8 @@ __global__ void __launch_bounds__(256) k_basis_gemm_simt(const float2 *__restric
 
 // ------------------------------------------------------------ host
 rhmc_status_t basis_assemble(const BasisBufs &bb, int n, int nshift, const SolverState *st, long rows, int K,
-                             int want_p, double2 *X, float2 *P, long fstride, int chunk_blocks, int simt, int *err,
-                             cudaStream_t s) {
+                             int want_p, double2 *X, float2 *P, long fstride, int chunk_blocks, int simt, int acc_kt,
+                             int *err, cudaStream_t s) {
   if (nshift < 2 || (K <= 0 && !want_p)) return RHMC_OK;
   const long cfstride = bb.cap + 1;
   prof_begin(PROF_NXN_SHIFTS, s);
@@ -662,6 +669,7 @@ rhmc_status_t basis_assemble(const BasisBufs &bb, int n, int nshift, const Solve
   g.X = want_p ? nullptr : X;
   g.P = want_p ? P : nullptr;
   g.fstride = fstride;
+  g.acc_kt = acc_kt > 0 ? acc_kt : kGChunkKt;
   g.err = err;
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);

@@ -119,11 +119,12 @@ size_t basis_pack_bytes(int n, int nshift, int cap);
 // + M2_{i+1} C_{i+1}; X^(s), s >= 1, is overwritten: it is zero before the one assembly of a
 // solve); want_p = 1: P^(s) = sum_{i <= K} Q_i D_i (FP32, D_K = 1, D_i = M2_{i+1} D_{i+1}),
 // active shifts only.  chunk_blocks > 0 (X only): FP32 partial sums over about that many
-// blocks, added in FP64.  simt: CUDA-core kernel instead of tcgen05.  err: device flag set
-// when a bounded wait of the tensor-core kernel gave up.
+// blocks, added in FP64.  simt: CUDA-core kernel instead of tcgen05.  acc_kt: K tiles (of 64
+// reals) per tensor-memory accumulation chunk (0: built-in).  err: device flag set when a
+// bounded wait of the tensor-core kernel gave up.
 rhmc_status_t basis_assemble(const BasisBufs &bb, int n, int nshift, const SolverState *st, long rows, int K,
-                             int want_p, double2 *X, float2 *P, long fstride, int chunk_blocks, int simt, int *err,
-                             cudaStream_t s);
+                             int want_p, double2 *X, float2 *P, long fstride, int chunk_blocks, int simt, int acc_kt,
+                             int *err, cudaStream_t s);
 // Q (rows x n) into column block k of the basis (rows x cap*n, row-major)
 rhmc_status_t basis_store(const float2 *Q, float2 *basis, long rows, int n, int cap, int k, cudaStream_t s);
 // the same with the block index read from *kdev (an iteration counter in device memory)
