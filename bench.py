@@ -12,7 +12,14 @@ Also reported on the same line:
 * e2e: the same step with host (pinned) buffers, copies inside the timed region;
 * roofline: the multi-RHS FP32 hop at 24^4, n = 16 against the measured HBM peak;
 * baseline_fp64_scg: plain per-vector FP64 multishift CG + the same force on
-  this GPU (the comparison of the metric), timed once;
+  this GPU (the comparison of the metric), median of 3 after a warm-up;
+* same_precision: the block algorithm's own gain (Sec. IV.B, Fig. 9 analogue):
+  FP64 block against FP64 per-vector, and mixed block (the timed step)
+  against mixed per-vector (the same solver with one right-hand side per
+  solve: multishift CG in the same reliable-update / defect-correction scheme);
+* alu_peaks and roofline_alu: the measured FP32 / FP64 CUDA-core peaks and the
+  fractions of them reached by the double-float operator (FP32-ALU bound), the
+  FP64 operator of the per-vector baseline and the n x n coefficient chain;
 * cpu_baseline: the FP64 CPU oracle on the host cores, on a bounded sample.
 
 --impl reference times the oracle (the only reference available: the paper
@@ -195,6 +202,47 @@ def cpu_one_thread(cfg, ra):
     return t * vol_ratio, sample
 
 
+def oracle_parity(ctx, cfg, U, Phi, ra, G, ws):
+    """Errors of the timed step's results against the FP64 oracle, per result:
+    every (shift, column) true relative residual of the solutions (oracle operator;
+    it bounds the solution error by tol ||B|| / (4m^2 + sigma) since lambda_min >= 4m^2)
+    over tol, and the force computed on the GPU from those solutions against the
+    oracle's force on 64 sampled links (t-boundary links included)."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    tol, dims, mass = cfg["tol"], cfg["dims"], cfg["mass"]
+    Pd = torch.from_numpy(Phi).to(ctx.device)
+    Xd, _ = ctx.block_multishift_cg(Pd, ra.beta, tol, precision=cfg["precision"])
+    Gx, _, _ = ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, tol, X=Xd, out=G, workspace=ws)
+    lx, ly, lz, lt = dims
+    rng = np.random.default_rng(4242)
+    V = lx * ly * lz * lt
+    links = [((x % lx) + lx * (((3 * x) % ly) + ly * (((5 * x) % lz) + lz * (lt - 1))), 3) for x in range(8)]
+    links += [(int(rng.integers(V)), int(rng.integers(4))) for _ in range(56)]
+    links = np.asarray(links, dtype=np.int64)
+    rows = torch.from_numpy(links[:, 0]).to(ctx.device)
+    mus = torch.from_numpy(links[:, 1]).to(ctx.device)
+    Gs = Gx[rows, mus].cpu().numpy()
+    X = Xd.cpu().numpy()
+    del Xd
+    t0 = time.perf_counter()
+    bn = np.linalg.norm(Phi.reshape(-1, Phi.shape[-1]), axis=0)
+    worst = 0.0
+    for q, sig in enumerate(ra.beta):
+        R = Phi - oracle.apply_A(dims, mass, U, X[q], sigma=sig)
+        worst = max(worst, float(np.max(np.linalg.norm(R.reshape(-1, Phi.shape[-1]), axis=0) / bn)))
+    Go = oracle.force_at(dims, U, X, ra.alpha, links)
+    ferr = float(np.linalg.norm(Gs - Go) / np.linalg.norm(Go))
+    return {"max_true_resid_over_tol": worst / tol, "solution_err_bound_ratio_max": worst / tol,
+            "force_kernel_rel_err_64_links": ferr, "oracle_seconds": time.perf_counter() - t0,
+            "how": "oracle operator on every (shift, column) of the GPU's solutions (the residual bounds the "
+                   "solution error by resid ||B|| / (4m^2 + sigma)); oracle force on 64 links "
+                   "from the same solutions (kernel parity, FP64 bound 1e-12)"}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -311,6 +359,73 @@ def dslash_widths(ctx, dev, widths=(1, 2, 4, 8, 16), reps=10):
     return out
 
 
+# ------------------------------------------------------------------ ALU fractions
+DF_OPS_PER_SITE_RHS = 8 * 9 * 4 * 12  # double-float hop: 8 links x 9 entries x 4 real products x 12 FP32 instructions
+
+
+def alu_fractions(ctx, stats, cfg, lib):
+    """Measured CUDA-core peaks (rhmc_probe_alu_peaks) and the fractions reached by
+    the FP32-ALU-bound double-float hop (FP32 instruction rate), and by the FP64
+    parts: the n x n coefficient chain (estimated flops) and the FP64 hop of the
+    per-vector baseline (570 flops per site and right-hand side)."""
+    import ctypes
+
+    from paper_1808_01829_gb300 import roofline
+
+    f32, f32x2, f64 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.rhmc_probe_alu_peaks(ctx.device.index or 0, ctypes.byref(f32), ctypes.byref(f32x2), ctypes.byref(f64),
+                                  None)
+    if rc != 0:
+        return None
+    peaks = {"fp32_tflops": f32.value, "fp32x2_tflops": f32x2.value, "fp64_tflops": f64.value,
+             "how": "best of 5 launches of independent FMA chains on every SM, CUDA events (2 flops per FMA lane)"}
+    n, ns = cfg["n_pf"], cfg["n_shifts"]
+    vh = ctx.Vh
+    out = {}
+    if "hop_df" in stats:
+        e = stats["hop_df"]
+        ops = e["launches"] * vh * n * DF_OPS_PER_SITE_RHS
+        achieved = ops / (e["ms"] * 1e-3) / 1e12  # T FP32 instructions / s
+        peak = f32.value / 2
+        out["hop_df"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 instr/s",
+                         "frac": achieved / peak, "peak_source": "of measured (rhmc_probe_alu_peaks)",
+                         "count": "8 x 9 x 4 real products x 12 FP32 instructions per site and right-hand side"}
+    if "nxn" in stats:
+        e = stats["nxn"]
+        # per iteration, alpha (LDL^dagger inverse, ~4 n^3/3 complex MACs) and rho (LDL^dagger, triangular
+        # inverse, delta update, ~2 n^3 complex MACs), 8 flops per complex MAC; two launches per iteration
+        flops = e["launches"] / 2 * 8 * (4 / 3 + 2) * n ** 3
+        achieved = flops / (e["ms"] * 1e-3) / 1e12
+        out["nxn"] = {"bound": "latency", "achieved": achieved, "peak": f64.value, "unit": "TFLOP/s (FP64)",
+                      "frac": achieved / f64.value, "peak_source": "of measured (rhmc_probe_alu_peaks)",
+                      "count": "estimated: (4/3 + 2) n^3 complex MACs per iteration; one SM per problem"}
+    if "nxn_shifts" in stats:
+        e = stats["nxn_shifts"]
+        flops = e["launches"] * (ns - 1) * 8 * 10 * n ** 3  # nine products and one inverse per shift
+        achieved = flops / (e["ms"] * 1e-3) / 1e12
+        out["nxn_shifts"] = {"bound": "latency", "achieved": achieved, "peak": f64.value, "unit": "TFLOP/s (FP64)",
+                             "frac": achieved / f64.value, "peak_source": "of measured (rhmc_probe_alu_peaks)",
+                             "count": "estimated: 10 n^3 complex MACs per shift and iteration"}
+    try:  # the FP64 hop of the per-vector baseline (width 1)
+        import torch
+
+        X = torch.randn(ctx.Vh, 3, 1, dtype=torch.complex128, device=ctx.device)
+        ctx.hop(X, 1, precision="fp64")
+        st = roofline.profile(lambda: [ctx.hop(X, r & 1, precision="fp64") for r in range(10)])
+        e = st["hop_fp64"]
+        flops = e["launches"] * vh * 570
+        achieved = flops / (e["ms"] * 1e-3) / 1e12
+        gbs = e["bytes"] / (e["ms"] * 1e-3) / 1e9
+        out["hop_fp64_width1"] = {"bound": "fp64", "achieved": achieved, "peak": f64.value,
+                                  "unit": "TFLOP/s (FP64)", "frac": achieved / f64.value,
+                                  "hbm_GB/s": gbs, "hbm_frac": gbs / roofline.peaks()["hbm_gbs"],
+                                  "peak_source": "of measured (rhmc_probe_alu_peaks)",
+                                  "count": "570 flops per site per right-hand side"}
+    except Exception as ex:  # a measurement beside the bench line: it never fails the line
+        out["hop_fp64_width1"] = {"error": f"{type(ex).__name__}: {ex}"[:200]}
+    return {"peaks": peaks, "fractions": out}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -407,19 +522,67 @@ def run_gpu(args):
         roof_dslash["traffic"] = ratio * roof_dslash["algorithmic_bytes_per_launch"]
         roof_dslash["traffic_source"] = src
 
-    # ---- comparison: per-vector FP64 multishift CG + force (Fig. 9 analogue)
-    base = None
+    # ---- comparisons (Fig. 9 analogue): per-vector FP64 multishift CG + force (the metric's
+    # baseline), and the same-precision pairs that isolate the block algorithm's gain.  Each is
+    # warmed up once (workspace sized outside the timed calls), then the median of `reps`.
+    base, same = None, None
     if not args.no_baseline and rank == 0:
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        Xs, binfo = ctx.multishift_cg_pervector(Pd, ra.beta, cfg["tol"])
-        ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], X=Xs, out=G, workspace=ws)
-        b.record(stream)
-        torch.cuda.synchronize()
-        base = {"ms": a.elapsed_time(b), "iters_total": binfo.iters, "dirac_calls_width1": binfo.dirac_calls,
-                "speedup": a.elapsed_time(b) / ms}
-        del Xs
+        def timed_median(fn, reps=3):
+            fn()
+            out = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                out.append(a.elapsed_time(b))
+            return statistics.median(out), r
+
+        def pervector_fp64():
+            Xs, binfo = ctx.multishift_cg_pervector(Pd, ra.beta, cfg["tol"])
+            ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], X=Xs, out=G, workspace=ws)
+            return binfo
+
+        def block_fp64():
+            _, _, info = ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], precision="fp64", out=G,
+                                   workspace=ws64)
+            return info
+
+        def pervector_mixed():
+            Xs = torch.empty((ns,) + tuple(Pd.shape), dtype=Pd.dtype, device=dev)
+            its = 0
+            for j in range(n):
+                col = Pd[..., j:j + 1].contiguous()
+                Xj, info = ctx.block_multishift_cg(col, ra.beta, cfg["tol"], precision="mixed", workspace=ws1)
+                Xs[..., j:j + 1] = Xj
+                its += info.iters
+            ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], X=Xs, out=G, workspace=ws)
+            return its
+
+        ms_pv, binfo = timed_median(pervector_fp64)
+        base = {"ms": ms_pv, "iters_total": binfo.iters, "dirac_calls_width1": binfo.dirac_calls,
+                "speedup": ms_pv / ms, "timing": "median of 3 after one warm-up"}
+        ws64 = torch.empty(ctx.workspace_bytes(n, ns, "fp64"), dtype=torch.uint8, device=dev)
+        ms_b64, b64info = timed_median(block_fp64)
+        del ws64
+        ws1 = torch.empty(ctx.workspace_bytes(1, ns, "mixed"), dtype=torch.uint8, device=dev)
+        ms_pvm, pvm_iters = timed_median(pervector_mixed)
+        del ws1
+        same = {"fp64": {"block_ms": ms_b64, "pervector_ms": ms_pv, "block_speedup": ms_pv / ms_b64,
+                         "block_iters": b64info.iters, "pervector_iters_total": binfo.iters},
+                "mixed": {"block_ms": ms, "pervector_ms": ms_pvm, "block_speedup": ms_pvm / ms,
+                          "block_iters": last.iters, "pervector_iters_total": pvm_iters},
+                "note": "per-vector mixed = the block solver with one right-hand side per solve (multishift CG "
+                        "with the same FP32 operator, FP64-accurate reliable updates and defect corrections), "
+                        "16 solves in turn, then the same force"}
+        torch.cuda.empty_cache()
+
+    # ---- CUDA-core peaks and the FP32 / FP64 fractions
+    alu = None
+    if rank == 0 and not args.small:
+        alu = alu_fractions(ctx, stats, cfg, lib)
 
     batch = None
     if not args.no_batch and not args.small:
@@ -439,6 +602,10 @@ def run_gpu(args):
         cpu = {"value": est, "unit": "ms", "cores": threads, "kind": "oracle",
                "sample": f"one oracle SBCGrQ iteration ({t_iter:.2f} s) + oracle force ({t_force:.2f} s) at the "
                          f"full workload, scaled by the GPU's {last.iters} iterations"}
+        try:  # per-result error of the timed step's solutions and force against the oracle
+            cpu["parity_vs_oracle"] = oracle_parity(ctx, cfg, U, Phi, ra, G, ws)
+        except Exception as e:  # never fails the line
+            cpu["parity_vs_oracle"] = {"error": f"{type(e).__name__}: {e}"[:200]}
         try:  # the paper's per-core setting, beside the all-cores figure
             t1, sample1 = cpu_one_thread(cfg, ra)
             cpu["one_thread"] = {"value": t1 * last.iters * 1e3, "unit": "ms",
@@ -469,6 +636,9 @@ def run_gpu(args):
                        "phase1_ms": last.phase1_ms, "refine_ms": last.refine_ms,
                        "true_rel_resid_max": last.true_rel_resid_max},
             "baseline_fp64_scg": base,
+            "same_precision": same,
+            "alu_peaks": alu["peaks"] if alu else None,
+            "roofline_alu": alu["fractions"] if alu else None,
             "batched_ensemble": batch,
             "cpu_baseline": cpu,
         }
