@@ -38,7 +38,14 @@
 // multishift phase, largest shift): one accumulator for all 1656 MMAs 6.2e-5,
 // 48 MMAs per chunk 5.8e-6, 12 MMAs per chunk 4.2e-6, FP32 products with FP64
 // sums over blocks (CUDA cores) 2.6e-6; the last two need the same number of
-// defect-correction iterations.  The last chunk's epilogue writes running sum
+// defect-correction iterations.  Two accumulators alternate, so the MMAs of
+// one K tile run while the epilogue moves the other into the running sum:
+// tensor memory holds both and the running sum (3 x 160 of its 512 columns),
+// so an N tile is at most 160 columns (whole shifts: 5 at n = 16); each N
+// tile runs only up to the last iteration that updated one of its shifts.
+// Measured at 24^4: 8.4 ms with double-buffered accumulators against 17.5 ms
+// with one accumulator of 256 columns (whose moves stalled the MMAs) and
+// 17.4 ms for a library FP32-emulating GEMM.  The last chunk's epilogue writes running sum
 // + accumulator straight into the FP64 solutions X^(s) (or P^(s)), so no
 // temporary product matrix is stored.
 // A CUDA-core kernel (k_basis_gemm_simt: FP32 products, FP64 sum per block) is
@@ -113,10 +120,12 @@ __host__ __device__ __forceinline__ unsigned sw128h(int row, int k) {
 namespace {
 constexpr int kGM = 128;            // rows per tile (MMA M)
 constexpr int kGK = 64;             // FP16 K elements per stage (one 128-byte swizzle row)
-constexpr int kGNmax = 256;         // columns per N tile (MMA N)
-constexpr int kGStages = 2;
-constexpr int kGThreads = 448;      // warps 0-7 split A (two groups, alternate stages), 8-11 epilogue,
-                                    // 12 loads B, 13 issues the MMAs
+constexpr int kGNmax = 160;         // columns per N tile (MMA N); tensor memory holds two accumulators and
+                                    // the running sum: 3 x 160 <= 512 columns
+constexpr int kGStages = 3;
+constexpr int kGThreads = 576;      // warps 0-7 split A (two groups, alternate stages), 8-15 epilogue
+                                    // (two per tensor-memory lane quarter, one column half each),
+                                    // 16 loads B, 17 issues the MMAs
 constexpr int kGChunkKt = 1;        // built-in K tiles per accumulation chunk (12 MMAs into one accumulator)
 constexpr unsigned kGAPiece = kGM * 128;  // bytes of one FP16 piece of an A tile
 constexpr float kGAScale = 4096.f;        // 2^12: |basis entries| <= 1
@@ -127,7 +136,7 @@ constexpr long long kGWaitCycles = 2000000000LL;  // about a second at the GPU's
 struct BasisTiles {
   int spt;       // shifts per tile
   int nnt;       // tiles
-  int NT;        // MMA N of a tile (multiple of 16, <= 256)
+  int NT;        // MMA N of a tile (multiple of 16, <= kGNmax)
   int nkt;       // K tiles per N tile in the packed buffer (capacity)
   size_t chunk;  // bytes of the two FP16 pieces of one (N tile, K tile)
 };
@@ -305,6 +314,18 @@ __device__ __forceinline__ void umma_commit(unsigned bar) {
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                  \
       : "r"(taddr))
 
+#define RHMC_TMEM_LD16(taddr, v)                                                                                     \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),       \
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])  \
+               : "r"(taddr))
+
+#define RHMC_TMEM_ST16(taddr, v)                                                                                     \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" \
+               ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),   \
+               "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])          \
+               : "memory")
+
 #define RHMC_TMEM_ST32(taddr, v)                                                                                     \
   asm volatile(                                                                                                      \
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
@@ -356,7 +377,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
   base += (1024 - (smem_addr(smem_raw) & 1023)) & 1023;
   const unsigned stage_bytes = 2 * kGAPiece + 2u * g.tl.NT * 128;
   __shared__ __align__(8) unsigned long long bar_full_a[kGStages], bar_full_b[kGStages], bar_empty[kGStages];
-  __shared__ __align__(8) unsigned long long bar_acc_full, bar_acc_empty, bar_final;
+  __shared__ __align__(8) unsigned long long bar_acc_full[2], bar_acc_empty[2], bar_final;
   __shared__ unsigned tmem_sh;
   __shared__ volatile int abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -370,8 +391,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_full_b[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_empty[q])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_acc_full)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar_acc_empty)), "r"(128));
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_acc_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar_acc_empty[q])), "r"(256));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_final)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_sh = 0;
@@ -386,8 +409,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
 
   if (warp < 8) {
     // ---- A producers: FP32 basis rows -> scaled FP16 pieces (hi, lo) in shared memory.  Group
-    // warp / 4 fills the stages with it & 1 == group, so each group's loads for its next stage are
-    // in flight while the MMAs of the two stages before it run.
+    // warp / 4 fills the K tiles with it & 1 == group (stage slot it % kGStages), so each group's
+    // loads for its next tile are in flight while the MMAs of the tiles before it run.
     const int grp = warp >> 2, cw = warp & 3;
     const int half = lane >> 4, q = lane & 15;
     int it = 0;
@@ -399,8 +422,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
       const long m0 = mt * kGM;
       const bool rows_in = m0 + kGM <= g.rows;
       for (int kk = 0; kk < nkt; ++kk, ++it) {
-        const int stage = it & 1;
-        if (stage != grp) continue;
+        if ((it & 1) != grp) continue;
+        const int stage = it % kGStages;
         const int kt = g.kt0 + kk;
         const int k = kt * kGK + 4 * q;
         float4 v[16];
@@ -412,7 +435,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
 #pragma unroll
           for (int r = 0; r < 16; ++r) v[r] = load_a4(g, m0 + 32 * cw + 2 * r + half, k);
         }
-        ok = bar_wait(smem_addr(&bar_empty[stage]), ((it >> 1) & 1) ^ 1, &abort_sh, g.err);
+        ok = bar_wait(smem_addr(&bar_empty[stage]), ((it / kGStages) & 1) ^ 1, &abort_sh, g.err);
         if (!ok) break;
         unsigned char *ahi = base + stage * stage_bytes, *alo = ahi + kGAPiece;
 #pragma unroll
@@ -426,11 +449,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
         bar_arrive(smem_addr(&bar_full_a[stage]));
       }
     }
-  } else if (warp < 12) {
+  } else if (warp < 16) {
     // ---- epilogue: per chunk, accumulator -> running sum (tensor memory, FP32 round-to-nearest);
     // after the last chunk running sum + accumulator -> X^(s) (FP64) or P^(s) (FP32)
-    const int ew = warp - 8;  // tensor-memory lanes 32 ew .. 32 ew + 31 (warp % 4)
-    const unsigned tacc = tmem + ((unsigned)(32 * ew) << 16), trun = tacc + kGNmax;
+    const int ew = warp & 3;         // tensor-memory lanes 32 ew .. 32 ew + 31 (a warp reaches lanes 32 (warp % 4) ..)
+    const int cb = (warp - 8) >> 2;  // column half of the tile
+    const unsigned tlane = tmem + ((unsigned)(32 * ew) << 16), trun = tlane + 2 * kGNmax;
     int cc = 0;
     bool ok = true;
     for (long w = blockIdx.x; w < total && ok; w += gridDim.x) {
@@ -442,61 +466,60 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
       const int ncols = min(g.tl.spt, g.nshift - s_first) * two_n;
       const int nch = (nkt + g.acc_kt - 1) / g.acc_kt;
       for (int ch = 0; ch < nch; ++ch, ++cc) {
-        ok = bar_wait(smem_addr(&bar_acc_full), cc & 1, &abort_sh, g.err);
+        const int buf = cc & 1;
+        ok = bar_wait(smem_addr(&bar_acc_full[buf]), (cc >> 1) & 1, &abort_sh, g.err);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const bool last = ch + 1 == nch;
-        for (int c0 = 0; c0 < ncols; c0 += 32) {
-          unsigned a[32];
-          RHMC_TMEM_LD32(tacc + (unsigned)c0, a);
+        const unsigned tacc = tlane + (unsigned)(buf * kGNmax);
+        for (int c0 = cb * (kGNmax / 2); c0 < min(ncols, (cb + 1) * (kGNmax / 2)); c0 += 16) {
+          unsigned a[16];
+          RHMC_TMEM_LD16(tacc + (unsigned)c0, a);
           if (ch > 0) {
-            unsigned r[32];
-            RHMC_TMEM_LD32(trun + (unsigned)c0, r);
+            unsigned r[16];
+            RHMC_TMEM_LD16(trun + (unsigned)c0, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int e = 0; e < 32; ++e) a[e] = __float_as_uint(__uint_as_float(a[e]) + __uint_as_float(r[e]));
+            for (int e = 0; e < 16; ++e) a[e] = __float_as_uint(__uint_as_float(a[e]) + __uint_as_float(r[e]));
           } else {
             asm volatile("tcgen05.wait::ld.sync.aligned;");
           }
           if (!last) {
-            RHMC_TMEM_ST32(trun + (unsigned)c0, a);
+            RHMC_TMEM_ST16(trun + (unsigned)c0, a);
             continue;
           }
           if (row >= g.rows) continue;
+          double2 xv[8];
+          if (g.X && g.x_add) {
 #pragma unroll
-          for (int j0 = 0; j0 < 16; j0 += 8) {
-            double2 xv[8];
-            if (g.X && g.x_add) {
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {  // eight loads in flight before their stores
-                const int col = c0 + 2 * (j0 + jj);
-                if (col < ncols) xv[jj] = g.X[(s_first + col / two_n) * g.fstride + row * g.n + ((col % two_n) >> 1)];
-              }
+            for (int jj = 0; jj < 8; ++jj) {  // eight loads in flight before their stores
+              const int col = c0 + 2 * jj;
+              if (col < ncols) xv[jj] = g.X[(s_first + col / two_n) * g.fstride + row * g.n + ((col % two_n) >> 1)];
             }
+          }
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int col = c0 + 2 * (j0 + jj);
-              if (col >= ncols) continue;
-              const int sh = s_first + col / two_n;
-              const long o = sh * g.fstride + row * g.n + ((col % two_n) >> 1);
-              const double sc = g.bscale[sh];
-              double re = (double)__uint_as_float(a[2 * (j0 + jj)]) * sc;
-              double im = (double)__uint_as_float(a[2 * (j0 + jj) + 1]) * sc;
-              if (g.X) {
-                if (g.x_add) re += xv[jj].x, im += xv[jj].y;
-                g.X[o] = make_double2(re, im);
-              } else {
-                g.P[o] = make_float2((float)re, (float)im);
-              }
+          for (int jj = 0; jj < 8; ++jj) {
+            const int col = c0 + 2 * jj;
+            if (col >= ncols) continue;
+            const int sh = s_first + col / two_n;
+            const long o = sh * g.fstride + row * g.n + ((col % two_n) >> 1);
+            const double sc = g.bscale[sh];
+            double re = (double)__uint_as_float(a[2 * jj]) * sc;
+            double im = (double)__uint_as_float(a[2 * jj + 1]) * sc;
+            if (g.X) {
+              if (g.x_add) re += xv[jj].x, im += xv[jj].y;
+              g.X[o] = make_double2(re, im);
+            } else {
+              g.P[o] = make_float2((float)re, (float)im);
             }
           }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        bar_arrive(smem_addr(&bar_acc_empty));
+        bar_arrive(smem_addr(&bar_acc_empty[buf]));
       }
     }
-  } else if (warp == 12) {
+  } else if (warp == 16) {
     // ---- B producer: one bulk copy of the packed FP16 pieces per stage
     if (lane == 0) {
       int it = 0;
@@ -506,8 +529,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
         int nt, nkt;
         if (!work_item(g, w, mt, nt, nkt)) continue;
         for (int kk = 0; kk < nkt; ++kk, ++it) {
-          const int stage = it & 1;
-          ok = bar_wait(smem_addr(&bar_empty[stage]), ((it >> 1) & 1) ^ 1, &abort_sh, g.err);
+          const int stage = it % kGStages;
+          ok = bar_wait(smem_addr(&bar_empty[stage]), ((it / kGStages) & 1) ^ 1, &abort_sh, g.err);
           if (!ok) break;
           const unsigned bar = smem_addr(&bar_full_b[stage]);
           const unsigned dst = smem_addr(base + stage * stage_bytes + 2 * kGAPiece);
@@ -522,7 +545,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
       }
       // copies still in flight (only after a failed wait) land before the CTA's memory is released
       if (abort_sh)
-        for (int j = max(0, it - kGStages); j < it; ++j) bar_drain(smem_addr(&bar_full_b[j & 1]), (j >> 1) & 1);
+        for (int j = max(0, it - kGStages); j < it; ++j)
+          bar_drain(smem_addr(&bar_full_b[j % kGStages]), (j / kGStages) & 1);
     }
   } else {
     // ---- MMA issuer: three FP16 products per K step, one accumulator per chunk of K tiles
@@ -535,13 +559,15 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
         int nt, nkt;
         if (!work_item(g, w, mt, nt, nkt)) continue;
         for (int c0 = 0; c0 < nkt && ok; c0 += g.acc_kt, ++cc) {
-          ok = bar_wait(smem_addr(&bar_acc_empty), (cc & 1) ^ 1, &abort_sh, g.err);
+          const int buf = cc & 1;
+          ok = bar_wait(smem_addr(&bar_acc_empty[buf]), ((cc >> 1) & 1) ^ 1, &abort_sh, g.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
+          const unsigned dt = tmem + (unsigned)(buf * kGNmax);
           const int c1 = min(c0 + g.acc_kt, nkt);
           for (int kk = c0; kk < c1; ++kk, ++it) {
-            const int stage = it & 1;
-            const unsigned par = (it >> 1) & 1;
+            const int stage = it % kGStages;
+            const unsigned par = (it / kGStages) & 1;
             ok = bar_wait(smem_addr(&bar_full_a[stage]), par, &abort_sh, g.err) &&
                  bar_wait(smem_addr(&bar_full_b[stage]), par, &abort_sh, g.err);
             if (!ok) break;
@@ -554,12 +580,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_basis_gemm_tc(const GemmArgs g
             for (int p = 0; p < 3; ++p)
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)  // K = 64 halves = 4 steps of 16 (32 bytes) inside the swizzle row
-                umma_f16(tmem, umma_desc(sa + pa[p] * kGAPiece + ks * 32),
+                umma_f16(dt, umma_desc(sa + pa[p] * kGAPiece + ks * 32),
                          umma_desc(sb + pb[p] * g.tl.NT * 128 + ks * 32), idesc, (kk - c0) | p | ks);
             umma_commit(smem_addr(&bar_empty[stage]));
           }
           if (!ok) break;
-          umma_commit(smem_addr(&bar_acc_full));
+          umma_commit(smem_addr(&bar_acc_full[buf]));
         }
       }
       // every MMA this thread issued has completed before tensor memory is released
