@@ -517,6 +517,7 @@ def run_gpu(args):
         roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
         roof["traffic_source"] = src
     roof_dslash = roofline.entry(stats, "hop_fp32") if "hop_fp32" in stats else None
+    roof_tensor = roofline.tensor_entry(stats, "basis_tc") if stats.get("basis_tc", {}).get("flops") else None
     if roof_dslash and "hop_fp32" in TRAFFIC_RATIO:
         ratio, src = TRAFFIC_RATIO["hop_fp32"]
         roof_dslash["traffic"] = ratio * roof_dslash["algorithmic_bytes_per_launch"]
@@ -627,6 +628,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "roofline": roof,
             "roofline_dslash": roof_dslash,
+            "roofline_tensor": roof_tensor,
             "dslash_widths": widths,
             "kernel_table": kt,
             "clocks": clk,

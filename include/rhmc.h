@@ -393,6 +393,11 @@ int rhmc_ctx_tune_get(const rhmc_ctx_t *ctx, int key);
 rhmc_status_t rhmc_tune_set(int key, int value);
 int rhmc_tune_get(int key);
 rhmc_status_t rhmc_profile_read(int category, long long *launches, double *ms, double *bytes);
+/* Tensor-core flops (multiply and add counted separately) issued by the
+ * recorded launches of one category: nonzero for the tensor-core kernels only
+ * (RHMC_PROF_BASIS_TC: three FP16 products per tile).  Same recording as
+ * rhmc_profile_read. */
+rhmc_status_t rhmc_profile_read_flops(int category, double *flops);
 
 #ifdef __cplusplus
 }

@@ -136,6 +136,8 @@ def load():
         lib.rhmc_profile_enable.restype = I
         lib.rhmc_profile_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), PD, PD]
         lib.rhmc_profile_read.restype = I
+        lib.rhmc_profile_read_flops.argtypes = [I, PD]
+        lib.rhmc_profile_read_flops.restype = I
         for name in ("rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_apply_mdagm_mrhs", "rhmc_hop",
                      "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force"):
             getattr(lib, name).restype = I
@@ -158,5 +160,5 @@ def exported_symbols():
         "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
         "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply", "rhmc_block_multishift_cg_batch", "rhmc_ctx_tune_set", "rhmc_ctx_tune_get",
         "rhmc_rational_solve", "rhmc_rational_solve_bytes", "rhmc_selftest_bounded_wait", "rhmc_force_lie",
-        "rhmc_probe_alu_peaks",
+        "rhmc_probe_alu_peaks", "rhmc_profile_read_flops",
     ]

@@ -47,6 +47,7 @@ struct ProfRec {
   int cat;
   cudaEvent_t a, b;
   double bytes;
+  double flops;  // tensor-core flops issued (tensor kernels), else 0
 };
 static bool g_prof = false;
 static std::vector<ProfRec> g_recs;
@@ -76,7 +77,7 @@ int tune_get(int key) {
 
 void prof_begin(int cat, cudaStream_t s) {
   if (!g_prof) return;
-  ProfRec r{cat, pool_event(), pool_event(), 0.0};
+  ProfRec r{cat, pool_event(), pool_event(), 0.0, 0.0};
   cudaEventRecord(r.a, s);
   g_recs.push_back(r);
 }
@@ -85,6 +86,10 @@ void prof_end(cudaStream_t s, double bytes) {
   if (!g_prof || g_recs.empty()) return;
   cudaEventRecord(g_recs.back().b, s);
   g_recs.back().bytes = bytes;
+}
+
+void prof_flops(double flops) {
+  if (g_prof && !g_recs.empty()) g_recs.back().flops = flops;
 }
 
 void set_error(const char *fmt, ...) {
@@ -1046,6 +1051,17 @@ rhmc_status_t rhmc_profile_read(int cat, long long *launches, double *ms, double
     *ms += t;
     *bytes += r.bytes;
   }
+  return RHMC_OK;
+}
+
+rhmc_status_t rhmc_profile_read_flops(int cat, double *flops) {
+  if (cat < 0 || cat >= rhmc::PROF_NCAT || !flops) {
+    set_error("rhmc_profile_read_flops: bad argument");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  *flops = 0.0;
+  for (auto &r : rhmc::g_recs)
+    if (r.cat == cat) *flops += r.flops;
   return RHMC_OK;
 }
 

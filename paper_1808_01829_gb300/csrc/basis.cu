@@ -712,6 +712,14 @@ rhmc_status_t basis_assemble(const BasisBufs &bb, int n, int nshift, const Solve
     k_basis_gemm_tc<<<grid, kGThreads, smem, s>>>(g);
     prof_end(s, (double)rows * (g.kt1 - kt0) * kGK * sizeof(float) + out_bytes * (kt0 > 0 ? 2 : 1));
     RHMC_LAUNCH_CHECK();
+    if (prof_on()) {  // the MMA flops issued: three FP16 products per (row tile, N tile, K tile)
+      int h[kMaxS];
+      RHMC_CUDA_TRY(cudaMemcpyAsync(h, bb.tile_nkt, sizeof(int) * tl.nnt, cudaMemcpyDeviceToHost, s));
+      RHMC_CUDA_TRY(cudaStreamSynchronize(s));
+      double kts = 0.0;
+      for (int t = 0; t < tl.nnt; ++t) kts += std::max(0, std::min(h[t], g.kt1) - kt0);
+      prof_flops(3.0 * 2.0 * kGM * tl.NT * kGK * kts * mtiles);
+    }
   }
   return RHMC_OK;
 }

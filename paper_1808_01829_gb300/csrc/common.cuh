@@ -131,6 +131,7 @@ enum TuneKey {
 int tune_get(int key);
 void prof_begin(int cat, cudaStream_t s);
 void prof_end(cudaStream_t s, double bytes);
+void prof_flops(double flops);  // tensor-core flops of the launch just recorded
 
 #define RHMC_CUDA_TRY(call)                                                                    \
   do {                                                                                         \

@@ -20,13 +20,30 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_FP32_TFLOPS = 73.0  # FP32 FMA throughput measured with a probe on this GPU model
 
 
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "of measured"}
-    return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "of fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d.get("bf16_tflops", FALLBACK_BF16_TFLOPS)),
+                "source": "of measured"}
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS, "source": "of fallback"}
+
+
+def tensor_entry(stats: dict, name: str, peak=None):
+    """Roofline object for a tensor-core kernel: issued FP16 MMA flops per launch over its
+    event-timed duration, against the measured dense BF16 peak (FP16 runs at the same rate)."""
+    p = peak or peaks()
+    s = stats[name]
+    per_launch_s = s["ms"] / s["launches"] * 1e-3
+    achieved = s["flops"] / s["launches"] / per_launch_s / 1e12
+    return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": p["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / p["bf16_tflops"], "peak_source": p["source"] + " (dense BF16; FP16 same rate)",
+            "flops_per_launch": s["flops"] / s["launches"], "us_per_launch": per_launch_s * 1e6,
+            "launches": s["launches"], "traffic": None}
 
 
 def profile(fn):
@@ -44,7 +61,9 @@ def profile(fn):
             _lib.check(lib.rhmc_profile_read(k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
                        "rhmc_profile_read")
             if n.value:
-                out[name] = {"launches": int(n.value), "ms": ms.value, "bytes": by.value}
+                fl = ctypes.c_double(0)
+                _lib.check(lib.rhmc_profile_read_flops(k, ctypes.byref(fl)), "rhmc_profile_read_flops")
+                out[name] = {"launches": int(n.value), "ms": ms.value, "bytes": by.value, "flops": fl.value}
         lib.rhmc_profile_enable(0)
     return out
 
