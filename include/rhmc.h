@@ -135,7 +135,10 @@ rhmc_status_t rhmc_apply_mdagm_mrhs(rhmc_ctx_t *ctx, const void *X_dev, void *Y_
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.
- * Requires rhmc_set_gauge (NO_GAUGE otherwise). */
+ * The looked-up address belongs to the device's primary context: after a
+ * cudaDeviceReset of that device, do not call this entry point there again.
+ * The context's launch settings (rhmc_ctx_tune_set) apply as in
+ * rhmc_apply_mdagm_mrhs.  Requires rhmc_set_gauge (NO_GAUGE otherwise). */
 rhmc_status_t rhmc_apply_mdagm_mrhs_noalloc(rhmc_ctx_t *ctx, const void *X_dev, void *Y_dev, int n_rhs, double sigma,
                                             rhmc_stream_t s);
 
@@ -382,6 +385,15 @@ rhmc_status_t rhmc_selftest_bounded_wait(int device, double seconds, rhmc_stream
  * The call synchronises s.  INVALID_ARG for a null output pointer. */
 rhmc_status_t rhmc_probe_alu_peaks(int device, double *fp32_tflops, double *fp32x2_tflops, double *fp64_tflops,
                                    rhmc_stream_t s);
+
+/* Self-test of internal arithmetic (no counterpart in the paper): for each of
+ * the `count` doubles x_dev[k] > 0 (device), writes out_dev[q * count + k]
+ * (device, 6 * count doubles) = q = 0: the library's Newton-Raphson FP64
+ * reciprocal of the n x n coefficient step, 1: its square root, 2: its fast
+ * reciprocal, 3: its reciprocal square root, 4: CUDA's IEEE 1.0 / x, 5: CUDA's
+ * IEEE sqrt(x).  Asynchronous on stream s.  INVALID_ARG for null pointers or
+ * count < 1. */
+rhmc_status_t rhmc_selftest_fp64_helpers(const double *x_dev, int count, double *out_dev, rhmc_stream_t s);
 
 /* The same settings for one context only (they take precedence over the
  * process-wide ones in every call on ctx, including the concurrent solves of

@@ -24,6 +24,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -39,8 +40,14 @@ namespace rhmc {
 
 static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
+// launches by the calling host thread (stream capture counts its own kernels with it:
+// refinement lanes on other threads launch concurrently)
+static thread_local long long t_launches = 0;
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
 
 // ------------------------------------------------------------ profiler
 struct ProfRec {
@@ -206,6 +213,9 @@ struct TuneScope {
   explicit TuneScope(const rhmc_ctx *c) : prev(t_tune_override) { t_tune_override = c ? c->tune : nullptr; }
   ~TuneScope() { t_tune_override = prev; }
 };
+
+CtxTuneScope::CtxTuneScope(const rhmc_ctx_t *c) : prev(t_tune_override) { t_tune_override = c ? c->tune : nullptr; }
+CtxTuneScope::~CtxTuneScope() { t_tune_override = prev; }
 
 static rhmc_status_t ensure_pool(rhmc_ctx *c, size_t bytes) {
   if (c->pool_bytes >= bytes) return RHMC_OK;
@@ -582,12 +592,12 @@ static rhmc_status_t run_chunk_graph(rhmc_ctx *c, const SolveBufs &b, double2 *X
       cudaGraphExecDestroy(lru->exec);
       L.graphs.erase(lru);
     }
-    const long long before = rhmc_kernel_launches();
+    const long long before = t_launches;
     RHMC_CUDA_TRY(cudaStreamBeginCapture(L.cap, cudaStreamCaptureModeThreadLocal));
     const rhmc_status_t rc = run_chunk<T>(c, b, X, n, ns, sigma0, chunk_start, len, target, freeze, L.cap);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(L.cap, &g);
-    const long long captured = rhmc_kernel_launches() - before;
+    const long long captured = t_launches - before;
     g_launches.fetch_sub(captured);  // recorded, not run: counted at every replay instead
     if (rc != RHMC_OK) {
       if (g) cudaGraphDestroy(g);
@@ -833,7 +843,11 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   // (stream + host thread each, hardest shifts first), so that the
   // latency-bound parts of one correction overlap the bulk kernels of another.
   const int tl = tune_get(TUNE_REFINE_LANES);
-  const int nl = prof_on() ? 1 : std::min(refine_lanes(ns), tl > 0 ? tl : kRefineLanes);
+  // one lane (no worker threads) under the library's profiler, and when a CUDA injection
+  // library is loaded (a kernel profiler such as Nsight Compute: its replay of kernels
+  // captured concurrently on several host threads ended the process with SIGSEGV)
+  const bool injected = std::getenv("CUDA_INJECTION64_PATH") != nullptr;
+  const int nl = (prof_on() || injected) ? 1 : std::min(refine_lanes(ns), tl > 0 ? tl : kRefineLanes);
   struct LaneWork {
     RefineBufs rb;
     SolveBufs b1;

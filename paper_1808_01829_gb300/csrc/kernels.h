@@ -146,6 +146,14 @@ rhmc_status_t force_links(const Geom &g, const double2 *X, const double2 *Y, int
 rhmc_status_t force_lie(const Geom &g, const double2 *U, const double2 *G, double2 *F, double *partial, int nparts,
                         cudaStream_t s);
 
+// api.cu: the calling thread uses ctx's launch settings (rhmc_ctx_tune_set) while
+// an object of this type lives, as every entry point of api.cu does.
+struct CtxTuneScope {
+  const int *prev;
+  explicit CtxTuneScope(const rhmc_ctx_t *c);
+  ~CtxTuneScope();
+};
+
 // api.cu: read-only view of a context (device, geometry, mass, staged FP64
 // links of the two output parities); NO_GAUGE before rhmc_set_gauge.
 rhmc_status_t ctx_geometry(const rhmc_ctx_t *ctx, int *device, Geom *g, double *mass, const double2 **l64_even,

@@ -23,7 +23,11 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratchBytes 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double2 *g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+// Device address of g_noalloc_scratch, per device, looked up on the first call.
+// The address belongs to the device's primary context: it stays valid as long
+// as that context lives, so a process that resets a device (cudaDeviceReset)
+// must not call this entry point on that device afterwards.
+double2 *g_scratch_ptr[kMaxDevices] = {};
 }  // namespace
 
 }  // namespace rhmc
@@ -76,6 +80,7 @@ extern "C" rhmc_status_t rhmc_apply_mdagm_mrhs_noalloc(rhmc_ctx_t *ctx, const vo
     scratch = g_scratch_ptr[device];
   }
   cudaStream_t s = (cudaStream_t)sv;
+  CtxTuneScope tscope(ctx);  // the context's launch settings, as in rhmc_apply_mdagm_mrhs
   // the intermediate is fully overwritten by the first hop: nothing to clear
   rc = hop<double>(g, 1, lo, (const double2 *)X_dev, scratch, nullptr, 0.0, n_rhs, 1, 0, s);
   if (rc == RHMC_OK)

@@ -721,3 +721,30 @@ RHMC_INST_NXN(float)
 RHMC_INST_NXN(double)
 
 }  // namespace rhmc
+
+// ------------------------------------------------------------ self-test of the FP64 helpers
+namespace rhmc {
+__global__ void k_fp64_helpers(const double *__restrict__ x, int count, double *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const double v = x[k];
+  out[0 * (size_t)count + k] = frcp(v);
+  out[1 * (size_t)count + k] = fsqrt(v);
+  out[2 * (size_t)count + k] = frcp_fast(v);
+  out[3 * (size_t)count + k] = frsqrt(v);
+  out[4 * (size_t)count + k] = 1.0 / v;  // IEEE division
+  out[5 * (size_t)count + k] = sqrt(v);  // IEEE square root
+}
+}  // namespace rhmc
+
+extern "C" rhmc_status_t rhmc_selftest_fp64_helpers(const double *x_dev, int count, double *out_dev,
+                                                    rhmc_stream_t sv) {
+  using namespace rhmc;
+  if (!x_dev || !out_dev || count < 1) {
+    set_error("rhmc_selftest_fp64_helpers: null pointer or count < 1");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  k_fp64_helpers<<<(count + 255) / 256, 256, 0, (cudaStream_t)sv>>>(x_dev, count, out_dev);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}

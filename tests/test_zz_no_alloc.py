@@ -2,15 +2,17 @@
 
 It exists for callers that cannot allocate device memory at call time (stream
 capture, fixed memory budgets, frameworks that own allocation).  Through the
-C ABI it must agree with rhmc_apply_mdagm_mrhs (FP64) to the operator
-tolerance of the other GPU tests (1e-12 relative per column), on two calls in
-a row, and reject problems larger than its fixed scratch with INVALID_ARG.
+C ABI it must agree with rhmc_apply_mdagm_mrhs (FP64) and with the oracle's
+operator to the tolerance of the other GPU tests (1e-12 relative per column),
+on two calls in a row, and reject problems larger than its fixed scratch with INVALID_ARG.
 This file sorts last so that a run stopping at the first failure has already
 run every other test."""
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 from gpu_util import colrel, need_gpu
 
@@ -50,6 +52,9 @@ def test_noalloc_matches_apply_mdagm_twice():
         assert rc == 0, lib.rhmc_last_error()
         torch.cuda.synchronize()
         assert colrel(Y.cpu().numpy(), Yref.cpu().numpy()) <= 1e-12
+        # and directly against the FP64 oracle's (A + sigma) X
+        Yo = oracle.apply_A(dims, mass, U.cpu().numpy(), X.cpu().numpy(), sigma=sigma)
+        assert colrel(Y.cpu().numpy(), Yo) <= 1e-12
     lib.rhmc_destroy(h)
 
 
