@@ -121,6 +121,7 @@ constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
 constexpr double kShiftFreezeMixed = 0.0;  // built-in freeze level of the shifted systems (mixed)
 constexpr int kRefineLanes = 4;       // concurrent defect corrections (built-in and most; 8 measured 2 % faster)
+constexpr int kCorrectionCheckEvery = 3;  // host checks of a defect-correction solve (divides kCheckEvery)
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
 struct Arena {
@@ -419,6 +420,8 @@ struct SolveParams {
   int fixed_iters;  // > 0: exactly this many iterations, no freezing, no checks
   bool verify_at_convergence = true;  // mixed: reliable update before declaring convergence
   const double *acc_w = nullptr;       // accumulating solve: weights of the shifts' solutions
+  bool reliable = true;                // mixed: reliable updates when the residual has dropped
+  int check_every = 0;                 // iterations between host checks (0: RHMC_TUNE_CHECK_EVERY / 6)
 };
 
 struct SolveStats {
@@ -719,7 +722,9 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   const int fz = tune_get(TUNE_SHIFT_FREEZE_NANO);
   const double tol_shift = mixed ? std::max(target, fz > 0 ? 1e-9 * fz : kShiftFreezeMixed) : target;
   double res_at_reliable = 1.0;
-  const int check_every = tune_get(TUNE_CHECK_EVERY) > 0 ? tune_get(TUNE_CHECK_EVERY) : kCheckEvery;
+  const int check_every = prm.check_every > 0                ? prm.check_every
+                          : tune_get(TUNE_CHECK_EVERY) > 0 ? tune_get(TUNE_CHECK_EVERY)
+                                                           : kCheckEvery;
   const int flush_every = tune_get(TUNE_FLUSH_EVERY);
   const double rel_delta = tune_get(TUNE_RELIABLE_DELTA_MILLI) > 0 ? 1e-3 * tune_get(TUNE_RELIABLE_DELTA_MILLI)
                                                                      : kReliableDelta;
@@ -734,8 +739,10 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       RHMC_TRY(assemble(k, 1));
       b.basis = nullptr, b.hist = nullptr, b.cap = 0;
     }
-    const bool graph = use_graphs() && chunk == kCheckEvery && check_every == kCheckEvery && k > 0 &&
-                       k % kCheckEvery == 0;
+    // a captured chunk replays for every later chunk with the same start modulo kCheckEvery
+    // (the k % 2 buffer and k % 3 state-slot patterns), so its length must divide kCheckEvery
+    const bool graph = use_graphs() && chunk == check_every && kCheckEvery % check_every == 0 && k > 0 &&
+                       k % check_every == 0;
     if (graph)
       RHMC_TRY(run_chunk_graph<T>(c, b, X, n, ns, sigma0, k, chunk, tol_shift, freeze, s));
     else
@@ -774,7 +781,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
       stats.iters = k;
       return RHMC_OK;
     }
-    if (mixed && (base < rel_delta * res_at_reliable || converged)) {
+    if (mixed && prm.reliable && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
       for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(apply_A_accurate(c, X, b.AP64, b.T64, b.R64, n, sigma0, s));
@@ -898,6 +905,12 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
       pr.tol = std::min(0.1, 0.5 * ratio_min);
       pr.fixed_iters = 0;
       pr.verify_at_convergence = false;  // the FP64 true residual is checked right after
+      // A correction needs only tol / r (about 1e-3) relative accuracy: far above the
+      // FP32 recursion's own drift (about 1e-6 relative), so it runs without reliable
+      // updates, and it is checked every kCorrectionCheckEvery iterations to stop closer
+      // to its target
+      pr.reliable = false;
+      pr.check_every = kCorrectionCheckEvery;
       SolveStats st1;
       rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls)
                                    : solve_phase1<double>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls);
