@@ -121,7 +121,7 @@ constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
 constexpr double kShiftFreezeMixed = 0.0;  // built-in freeze level of the shifted systems (mixed)
 constexpr int kRefineLanes = 4;       // concurrent defect corrections (built-in and most; 8 measured 2 % faster)
-constexpr int kCorrectionCheckEvery = 3;  // host checks of a defect-correction solve (divides kCheckEvery)
+constexpr int kCorrectionCheckEvery = 2;  // host checks of a defect-correction solve (divides kCheckEvery)
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
 struct Arena {
