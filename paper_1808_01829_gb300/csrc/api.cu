@@ -513,7 +513,12 @@ static rhmc_status_t sbcgrq_iteration(rhmc_ctx *c, const SolveBufs &b, TX *Xacc,
   }
   RHMC_TRY(nxn_rho<T>(b.partial, kGramParts, n, b.st, k, (C<T> *)b.coef, s));
   // base: Q_k = W rho_k^-1, X^(0), P^(0)
-  if (cols) {
+  if (cols && tune_get(TUNE_AXPY_SCALAR) != 1) {
+    // one pass: Q_k = W rho^-1, X^(0), P^(0), and block k of the stored basis (k from the
+    // device counter: graph replays)
+    RHMC_TRY(base_step((const float2 *)W, (float2 *)Qcur, (float2 *)P, (float2 *)Xacc, (const float2 *)b.coef,
+                       b.basis, b.cap, b.basis ? &b.st->kabs[k % kSlots] : nullptr, rows, n, s));
+  } else if (cols) {
     RHMC_TRY(axpy_cols((const float2 *)W, nullptr, (const float2 *)b.coef, (float2 *)Qcur, rows, n, s));
     if (b.basis)  // block k of the stored basis (k from the device counter: graph replays)
       RHMC_TRY(basis_store_dev((const float2 *)Qcur, b.basis, rows, n, b.cap, &b.st->kabs[k % kSlots], s));

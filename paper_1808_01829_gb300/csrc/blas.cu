@@ -734,6 +734,149 @@ static rhmc_status_t launch_update_cols_variant(const float2 *Q, float2 *P, floa
   return rc;
 }
 
+// ------------------------------------------------------------ fused base step
+// The base system's updates of Algorithm 1 after rho_k, in one pass over the
+// rows (FP32, column-owner lanes, packed FP32x2 FMAs):
+//   Q_k = W rho_k^-1                                  (line 5)
+//   X^(0) += P^(0) M1,  M1 = alpha_k delta_{k-1}       (line 6)
+//   P^(0) = Q_k + P^(0) M2,  M2 = rho_k^dagger         (line 7)
+// and, in the stored-basis mode, Q_k into block kb of the basis.  coef holds
+// rho^-1, M1, M2 (n x n each).  Each warp stages a tile of R rows of W, P^(0)
+// and X^(0) by cp.async; pass 1: lane j < n forms column j of Q (stored to Q
+// and the basis) while lane n + j forms column j of X; pass 2: lane n + j
+// forms column j of P from Q's column (a warp shuffle from lane j).  It
+// replaces three passes (Q = W rho^-1, the basis copy, the base update):
+// W, P, X read once, Q, P, X (and the basis block) written once.
+template <int N, int R, int WW>
+__global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restrict__ Wf, float2 *__restrict__ Q,
+                                                        float2 *__restrict__ P, float2 *__restrict__ X,
+                                                        const float2 *__restrict__ coef, float2 *__restrict__ basis,
+                                                        int cap, const int *__restrict__ kdev, long rows) {
+  constexpr int TILE = R * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CS = (3 * N * N + 1) & ~1;  // coefficient area, padded: the tiles start on 16-byte boundaries
+  float2 *cs = reinterpret_cast<float2 *>(smem_raw);  // rho^-1, M1, M2
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 *wt = cs + CS + (size_t)warp * 3 * TILE, *pt = wt + TILE, *xt = pt + TILE;
+  for (int k = threadIdx.x; k < 3 * N * N; k += blockDim.x) cs[k] = coef[k];
+  const int kb = (basis && kdev) ? *kdev : -1;
+  const bool store_basis = kb >= 0 && kb < cap;
+  __syncthreads();
+  const bool lo = lane < N, hi = lane >= N && lane < 2 * N;
+  const int j = lo ? lane : (hi ? lane - N : 0);
+  const long ntiles = (rows + R - 1) / R;
+  for (long tile = (long)blockIdx.x * WW + warp; tile < ntiles; tile += (long)gridDim.x * WW) {
+    const long r0 = tile * R;
+    const int nr = (int)min((long)R, rows - r0);  // rows is a multiple of 8: nr is even
+    const int chunks = nr * N / 2;
+    auto copy_tile = [&](float2 *dst, const float2 *src) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+      const char *s8 = reinterpret_cast<const char *>(src);
+      for (int c = lane; c < chunks; c += 32) cpa16(d + 16u * c, s8 + 16L * c);
+    };
+    copy_tile(wt, Wf + r0 * N);
+    copy_tile(pt, P + r0 * N);
+    copy_tile(xt, X + r0 * N);
+    cp_async_commit();
+    unsigned long long cr[N], ci[N];
+    {  // pass-1 coefficient column: rho^-1 (lanes < N) or M1 (lanes N .. 2N-1)
+      const float2 *m = cs + (hi ? N * N : 0) + j;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float2 c = m[k * N];
+        cr[k] = pack2(c.x, c.x);
+        ci[k] = pack2(c.y, c.y);
+      }
+    }
+    cpa_wait<0>();
+    __syncwarp();
+    // pass 1: row r of W (lanes < N) or of P (lanes N .. 2N-1) times the lane's column
+    float2 qv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      qv[r] = make_float2(0.f, 0.f);
+      if (r < nr && (lo || hi)) {
+        const float2 *u = (lo ? wt : pt) + r * N;
+        unsigned long long a = 0ull, b = 0ull;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const unsigned long long v = *reinterpret_cast<const unsigned long long *>(u + k);
+          a = fma2(v, cr[k], a);
+          b = fma2(v, ci[k], b);
+        }
+        const float2 A = unpack2(a), B = unpack2(b);
+        const float2 prod = make_float2(A.x - B.y, A.y + B.x);
+        const long row = r0 + r;
+        if (lo) {
+          qv[r] = prod;
+          Q[row * N + j] = prod;
+          if (store_basis) basis[row * (long)cap * N + (long)kb * N + j] = prod;
+        } else {
+          const float2 x = xt[r * N + j];
+          X[row * N + j] = make_float2(x.x + prod.x, x.y + prod.y);
+        }
+      }
+    }
+    {  // pass-2 coefficient column: M2 (lanes N .. 2N-1)
+      const float2 *m = cs + 2 * N * N + j;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float2 c = m[k * N];
+        cr[k] = pack2(c.x, c.x);
+        ci[k] = pack2(c.y, c.y);
+      }
+    }
+    // pass 2: P = Q + P M2, Q's column j from lane j
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float qx = __shfl_sync(0xffffffffu, qv[r].x, j);
+      const float qy = __shfl_sync(0xffffffffu, qv[r].y, j);
+      if (r < nr && hi) {
+        const float2 *u = pt + r * N;
+        unsigned long long a = 0ull, b = 0ull;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const unsigned long long v = *reinterpret_cast<const unsigned long long *>(u + k);
+          a = fma2(v, cr[k], a);
+          b = fma2(v, ci[k], b);
+        }
+        const float2 A = unpack2(a), B = unpack2(b);
+        P[(r0 + r) * N + j] = make_float2(qx + A.x - B.y, qy + A.y + B.x);
+      }
+    }
+    __syncwarp();  // the tiles are refilled for the next row tile
+  }
+}
+
+constexpr int kBaseRows = 8, kBaseWarps = 16;
+
+rhmc_status_t base_step(const float2 *W, float2 *Q, float2 *P, float2 *X, const float2 *coef, float2 *basis, int cap,
+                        const int *kdev, long rows, int n, cudaStream_t s) {
+  if (rows % 8) return RHMC_ERR_INVALID_ARG;
+  prof_begin(PROF_UPDATE_SHIFTS32, s);
+  rhmc_status_t rc = RHMC_OK;
+#define L_BASE(NN)                                                                                                 \
+  {                                                                                                                \
+    const int threads = kBaseWarps * 32;                                                                           \
+    const size_t smem = (((3 * NN * NN + 1) & ~1) + (size_t)kBaseWarps * 3 * kBaseRows * NN) * sizeof(float2);    \
+    static std::once_flag attr;                                                                                    \
+    std::call_once(attr, [] {                                                                                      \
+      cudaFuncSetAttribute(k_base_step<NN, kBaseRows, kBaseWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                           100 * 1024);                                                                            \
+    });                                                                                                            \
+    const long ntiles = (rows + kBaseRows - 1) / kBaseRows;                                                        \
+    long grid = (ntiles + kBaseWarps - 1) / kBaseWarps;                                                            \
+    grid = std::min(grid, (long)resident_ctas(k_base_step<NN, kBaseRows, kBaseWarps>, threads, smem));             \
+    k_base_step<NN, kBaseRows, kBaseWarps><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, X, coef, basis, cap,      \
+                                                                                 kdev, rows);                      \
+  }
+  RHMC_DISPATCH_N(n, L_BASE)
+#undef L_BASE
+  prof_end(s, (double)rows * n * sizeof(float2) * (6.0 + (basis ? 1.0 : 0.0)));
+  RHMC_LAUNCH_CHECK();
+  return rc;
+}
+
 static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2 *X, const float2 *coef,
                                               const int *upd, int s_begin, int s_end, long rows, int n, long fstride,
                                               cudaStream_t s);

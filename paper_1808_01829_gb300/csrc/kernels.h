@@ -72,6 +72,10 @@ rhmc_status_t axpy_cols(const float2 *A, const float2 *C, const float2 *M, float
 // Y = C + A M fused with out = Y^dagger Y (n x n FP64, scratch: kGramCtas * n * n partials)
 rhmc_status_t axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows, int n,
                              double2 *scratch, double2 *out, cudaStream_t s);
+// The base step after rho_k in one pass: Q = W rho^-1, X^(0) += P^(0) M1, P^(0) = Q + P^(0) M2
+// (coef: rho^-1, M1, M2), and Q into basis block *kdev when basis is given (capacity cap)
+rhmc_status_t base_step(const float2 *W, float2 *Q, float2 *P, float2 *X, const float2 *coef, float2 *basis, int cap,
+                        const int *kdev, long rows, int n, cudaStream_t s);
 // FP32 shifted updates (lines 11-12) with column-owner lanes and cp.async-staged row tiles
 rhmc_status_t update_shifts_cols(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
                                  int s_begin, int s_end, long rows, int n, long fstride, cudaStream_t s);
