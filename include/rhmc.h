@@ -261,6 +261,123 @@ size_t rhmc_rational_solve_bytes(const rhmc_ctx_t *ctx, int n_pf, int n_shifts);
 rhmc_status_t rhmc_rational_apply(rhmc_ctx_t *ctx, const void *Phi_dev, int n_pf, double alpha0, const double *alpha,
                                   int n_shifts, const void *X_dev, void *Y_dev, rhmc_stream_t s);
 
+/* ------------------------------------------------------------------------
+ * The RHMC trajectory around the pseudofermion force (Sec. II set-up; Sec. IV
+ * run parameters: Wilson gauge action, two-level OMF2 integrator, heatbath and
+ * accept/reject solves at 1e-14).  FP64 throughout.  Fields:
+ *   U   complex128 [V][4][3][3] links, lexicographic sites x + Lx (y + Ly (z + Lz t)),
+ *       periodic in every direction (the antiperiodic temporal boundary
+ *       belongs to the fermion operator only);
+ *   P   complex128 [V][4][3][3] momenta, traceless anti-Hermitian,
+ *       P = sum_a p^a T^a with T^a = i lambda^a / 2 (Gell-Mann lambda^a);
+ *   G   complex128 [V][4][3][3] action derivative dS/dRe U + i dS/dIm U
+ *       (rhmc_force's output for the pseudofermion action).
+ * The molecular dynamics is dU/dtau = P U, dP/dtau = TA(U G^dagger) / 2 with
+ * TA(M) = (M - M^dagger)/2 - tr(M - M^dagger)/6, and conserves
+ * H = K + S_g + S_f, K = -sum tr(P^2) = sum_a (p^a)^2 / 2.
+ * These calls do not need rhmc_set_gauge (the context gives the lattice);
+ * those that return a host scalar synchronise stream s, the others are
+ * asynchronous.  INVALID_ARG for null pointers. */
+
+/* Wilson gauge action S_g = beta sum_{x, mu<nu} (1 - Re tr Pi_{mu nu}(x) / 3),
+ * Pi_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dagger U_nu(x)^dagger (Sec. IV).
+ * Summed per CTA, then on the host in a fixed order (deterministic). */
+rhmc_status_t rhmc_gauge_action(rhmc_ctx_t *ctx, const void *U_dev, double beta, double *S_out, rhmc_stream_t s);
+
+/* Kinetic energy K = -sum_{x,mu} Re tr(P_mu(x)^2), deterministic like the action. */
+rhmc_status_t rhmc_kinetic_energy(rhmc_ctx_t *ctx, const void *P_dev, double *K_out, rhmc_stream_t s);
+
+/* Momentum heatbath from caller-drawn normals: P_mu(x) = sum_a p[x][mu][a] T^a,
+ * p float64 [V][4][8], p^a ~ N(0, 1) for the distribution exp(-K). */
+rhmc_status_t rhmc_momenta_from_normals(rhmc_ctx_t *ctx, const double *p_dev, void *P_dev, rhmc_stream_t s);
+
+/* Gauge-force kick P += eps TA(U G_g^dagger) / 2 with G_g = -(beta / 3) V^dagger,
+ * V_mu(x) the sum of the six staples around U_mu(x):
+ *   V_mu(x) = sum_{nu != mu} [U_nu(x+mu) U_mu(x+nu)^dagger U_nu(x)^dagger
+ *                             + U_nu(x+mu-nu)^dagger U_mu(x-nu)^dagger U_nu(x-nu)]. */
+rhmc_status_t rhmc_gauge_momentum(rhmc_ctx_t *ctx, const void *U_dev, void *P_dev, double beta, double eps,
+                                  rhmc_stream_t s);
+
+/* Kick by a given derivative: P += eps TA(U G^dagger) / 2 (G from rhmc_force). */
+rhmc_status_t rhmc_momentum_update(rhmc_ctx_t *ctx, const void *U_dev, const void *G_dev, void *P_dev, double eps,
+                                   rhmc_stream_t s);
+
+/* Drift U <- exp(eps P) U per link.  The exponential is a degree-16 Taylor
+ * polynomial of eps P / 2^k, k the smallest with |eps P|_F / 2^k <= 1/2, squared
+ * k times (truncation below 1e-19 relative). */
+rhmc_status_t rhmc_link_update(rhmc_ctx_t *ctx, void *U_dev, const void *P_dev, double eps, rhmc_stream_t s);
+
+/* Rational function of Eq. (RA): R(x) = alpha0 + sum_s alpha_s / (x + beta_s). */
+typedef struct {
+  int n_shifts;        /* 1 .. RHMC_MAX_SHIFTS */
+  double alpha0;
+  const double *alpha; /* host [n_shifts] */
+  const double *beta;  /* host [n_shifts], > 0 */
+} rhmc_rational_t;
+
+/* Molecular-dynamics parameters of the two-level OMF2 integrator (Sec. IV). */
+typedef struct {
+  double beta;      /* Wilson gauge coupling */
+  double tau;       /* trajectory length */
+  int n_steps;      /* outer steps, step size dtau = tau / n_steps (pseudofermion force) */
+  int n_gauge;      /* inner steps per outer drift of length dtau / 2 (gauge force) */
+  double lambda;    /* OMF2 parameter (1/6 in the paper's acceptance study) */
+  double tol_md;    /* stopping criterion of the force solves (1e-7 in the paper) */
+  int max_iter;     /* of the force solves; 0 = built-in */
+  rhmc_precision_t precision_md; /* RHMC_FP64 or RHMC_MIXED_FP32 force solves */
+} rhmc_md_params_t;
+
+typedef struct {
+  int force_evals;        /* pseudofermion force evaluations (block multishift solves) */
+  int gauge_force_evals;  /* gauge-force kicks */
+  long long solver_iters; /* SBCGrQ iterations summed over the force solves (incl. corrections) */
+  long long dirac_calls;  /* block operator applications summed over the force solves */
+  double max_rel_resid;   /* largest true relative residual of any force solve */
+} rhmc_md_info_t;
+
+/* Molecular dynamics over one trajectory, (U, P) updated in place.  Per outer
+ * step of length e = tau / n_steps (OMF2, Omelyan's second-order scheme):
+ *   P += lambda e F_f; D(e/2); P += (1 - 2 lambda) e F_f; D(e/2); P += lambda e F_f,
+ * where F_f = TA(U G_f^dagger)/2 is the pseudofermion force of
+ * S_f = sum_i phi_i^dagger R_md(A) phi_i (rhmc_force with `md`) and each drift
+ * D(h) is the same scheme with the gauge force and the link update in n_gauge
+ * steps of length h / n_gauge.  Consecutive kicks at the same links are
+ * merged (one force evaluation for the lambda e kicks that end one step and
+ * start the next), so a trajectory takes 2 n_steps + 1 pseudofermion forces.
+ *   Phi   complex128 [V/2][3][n_pf] pseudofermions, or NULL (n_pf = 0: gauge only)
+ * The context's staged links are replaced (rhmc_set_gauge) at every force
+ * evaluation and hold the final U on return.  Uses the context's buffers (one
+ * G field) and pool.  Status of the first failing solve (NOT_CONVERGED
+ * included) is returned at once, with (U, P) part-way. */
+rhmc_status_t rhmc_md_evolve(rhmc_ctx_t *ctx, void *U_dev, void *P_dev, const void *Phi_dev, int n_pf,
+                             const rhmc_rational_t *md, const rhmc_md_params_t *p, rhmc_md_info_t *info,
+                             rhmc_stream_t s);
+
+typedef struct {
+  double H_old, H_new, dH;  /* H = K + S_g + S_f at the start and end */
+  double K[2], S_g[2], S_f[2];
+  int accepted;             /* 1: U holds the new links */
+  rhmc_md_info_t md;
+} rhmc_hmc_info_t;
+
+/* One RHMC trajectory with accept/reject (Sec. II set-up, Sec. IV):
+ *   1. momenta P = sum_a p^a T^a from the caller's normals p (float64 [V][4][8]);
+ *   2. pseudofermion heatbath Phi = R_hb(A) eta with R_hb ~ x^(+n_f/(8 n_pf)),
+ *      eta complex128 [V/2][3][n_pf] drawn by the caller with density
+ *      exp(-|eta|^2) (real and imaginary parts N(0, 1/2)); FP64 solve at tol_action;
+ *   3. H_old = K + S_g + S_f with S_f = sum_i phi_i^dagger R_act(A) phi_i
+ *      (R_act ~ x^(-n_f/(4 n_pf)), FP64 block solve at tol_action);
+ *   4. rhmc_md_evolve on a copy of U with the MD rational `md`;
+ *   5. H_new as in 3; accept when u_accept < exp(-(H_new - H_old)), with
+ *      u_accept in [0, 1) drawn by the caller.
+ * On accept U is overwritten with the new links; the context's staged links
+ * are those of U on return.  Phi_out optional complex128 [V/2][3][n_pf] (the
+ * heatbath field).  n_pf = 0 (eta NULL) is pure-gauge HMC. */
+rhmc_status_t rhmc_hmc_trajectory(rhmc_ctx_t *ctx, void *U_dev, const double *p_dev, const void *eta_dev, int n_pf,
+                                  const rhmc_rational_t *heatbath, const rhmc_rational_t *md,
+                                  const rhmc_rational_t *action, const rhmc_md_params_t *p, double tol_action,
+                                  double u_accept, void *Phi_out_dev, rhmc_hmc_info_t *info, rhmc_stream_t s);
+
 /* Thread-local message describing the last failing call ("" if none). */
 const char *rhmc_last_error(void);
 

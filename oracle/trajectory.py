@@ -110,15 +110,19 @@ def drift(U, P, eps):
     return expm_ah(eps * P) @ U
 
 
+def momenta_from_normals(p):
+    """P = sum_a p^a T^a, T^a = i lambda^a / 2, for normals p of shape [...][8]."""
+    from paper_1808_01829_gb300 import synthetic as syn
+
+    T = 0.5j * syn.gell_mann()
+    return np.einsum("...a,aij->...ij", p, T)
+
+
 def momenta(dims, seed):
     """p^a ~ N(0, 1), P = sum_a p^a T^a, layout [t][z][y][x][mu][3][3]."""
     from paper_1808_01829_gb300 import synthetic as syn
 
-    lx, ly, lz, lt = dims
-    rng = np.random.default_rng(seed)
-    p = rng.standard_normal((lt, lz, ly, lx, 4, 8))
-    T = 0.5j * syn.gell_mann()
-    return np.einsum("...a,aij->...ij", p, T)
+    return momenta_from_normals(syn.momentum_normals(dims, seed))
 
 
 def _flat(U):
@@ -137,6 +141,18 @@ def fermion_action(dims, mass, U, Phi, ra, tol, bc_t=-1):
     if rc != 0:
         raise RuntimeError(f"oracle sbcgrq: status {rc}")
     return oracle.action(ra.alpha0, ra.alpha, Phi, X)
+
+
+def heatbath(dims, mass, U, eta, ra, tol, bc_t=-1):
+    """Phi = R(A) eta = alpha0 eta + sum_s alpha_s (A + beta_s)^-1 eta, R the heatbath
+    rational (x^(+n_f/(8 n_pf)) so that Phi^dagger A^(-n_f/(4 n_pf)) Phi = |eta|^2)."""
+    X, _, rc = oracle.sbcgrq(dims, mass, _flat(U), eta, ra.beta, tol=tol, max_iter=50000, bc_t=bc_t)
+    if rc != 0:
+        raise RuntimeError(f"oracle sbcgrq: status {rc}")
+    Phi = ra.alpha0 * eta
+    for s, a in enumerate(ra.alpha):
+        Phi = Phi + a * X[s]
+    return Phi
 
 
 def hamiltonian(dims, mass, U, P, Phi, beta, ra_action, tol, bc_t=-1):
@@ -179,3 +195,18 @@ def trajectory(dims, mass, U, P, Phi, beta, ra_md, tau, n_steps, n_gauge, lam, t
     for _ in range(n_steps):
         U, P = omf2(U, P, fforce, gauge_drift, eps, lam)
     return U, P
+
+
+def hmc_trajectory(dims, mass, U, p, eta, beta, ra_hb, ra_md, ra_act, tau, n_steps, n_gauge, lam, tol_md, tol_action,
+                   u, bc_t=-1):
+    """One RHMC trajectory (Sec. II): momenta from the normals p, heatbath Phi from
+    eta (None: pure gauge), H at the start, molecular dynamics, H at the end, and
+    acceptance when u < exp(-dH).  Returns (links after the step, record)."""
+    P = momenta_from_normals(p)
+    Phi = None if eta is None else heatbath(dims, mass, U, eta, ra_hb, tol_action, bc_t)
+    H0 = hamiltonian(dims, mass, U, P, Phi, beta, ra_act, tol_action, bc_t)
+    U1, P1 = trajectory(dims, mass, U, P, Phi, beta, ra_md, tau, n_steps, n_gauge, lam, tol_md, bc_t)
+    H1 = hamiltonian(dims, mass, U1, P1, Phi, beta, ra_act, tol_action, bc_t)
+    dH = H1 - H0
+    acc = bool(dH <= 0 or u < np.exp(-dH))
+    return (U1 if acc else U), {"H_old": H0, "H_new": H1, "dH": dH, "accepted": acc, "Phi": Phi, "U1": U1, "P1": P1}

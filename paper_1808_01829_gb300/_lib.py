@@ -81,6 +81,29 @@ class BatchItem(ctypes.Structure):
     ]
 
 
+class Rational(ctypes.Structure):
+    _fields_ = [("n_shifts", ctypes.c_int), ("alpha0", ctypes.c_double), ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("beta", ctypes.POINTER(ctypes.c_double))]
+
+
+class MdParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("n_steps", ctypes.c_int),
+                ("n_gauge", ctypes.c_int), ("lam", ctypes.c_double), ("tol_md", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("precision_md", ctypes.c_int)]
+
+
+class MdInfo(ctypes.Structure):
+    _fields_ = [("force_evals", ctypes.c_int), ("gauge_force_evals", ctypes.c_int),
+                ("solver_iters", ctypes.c_longlong), ("dirac_calls", ctypes.c_longlong),
+                ("max_rel_resid", ctypes.c_double)]
+
+
+class HmcInfo(ctypes.Structure):
+    _fields_ = [("H_old", ctypes.c_double), ("H_new", ctypes.c_double), ("dH", ctypes.c_double),
+                ("K", ctypes.c_double * 2), ("S_g", ctypes.c_double * 2), ("S_f", ctypes.c_double * 2),
+                ("accepted", ctypes.c_int), ("md", MdInfo)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -140,6 +163,20 @@ def load():
         lib.rhmc_profile_read.restype = I
         lib.rhmc_profile_read_flops.argtypes = [I, PD]
         lib.rhmc_profile_read_flops.restype = I
+        lib.rhmc_gauge_action.argtypes = [P, P, D, PD, P]
+        lib.rhmc_kinetic_energy.argtypes = [P, P, PD, P]
+        lib.rhmc_momenta_from_normals.argtypes = [P, P, P, P]
+        lib.rhmc_gauge_momentum.argtypes = [P, P, P, D, D, P]
+        lib.rhmc_momentum_update.argtypes = [P, P, P, P, D, P]
+        lib.rhmc_link_update.argtypes = [P, P, P, D, P]
+        lib.rhmc_md_evolve.argtypes = [P, P, P, P, I, ctypes.POINTER(Rational), ctypes.POINTER(MdParams),
+                                       ctypes.POINTER(MdInfo), P]
+        lib.rhmc_hmc_trajectory.argtypes = [P, P, P, P, I, ctypes.POINTER(Rational), ctypes.POINTER(Rational),
+                                            ctypes.POINTER(Rational), ctypes.POINTER(MdParams), D, D, P,
+                                            ctypes.POINTER(HmcInfo), P]
+        for name in ("rhmc_gauge_action", "rhmc_kinetic_energy", "rhmc_momenta_from_normals", "rhmc_gauge_momentum",
+                     "rhmc_momentum_update", "rhmc_link_update", "rhmc_md_evolve", "rhmc_hmc_trajectory"):
+            getattr(lib, name).restype = I
         for name in ("rhmc_create", "rhmc_destroy", "rhmc_set_gauge", "rhmc_apply_mdagm_mrhs", "rhmc_hop",
                      "rhmc_block_multishift_cg", "rhmc_multishift_cg_pervector", "rhmc_force"):
             getattr(lib, name).restype = I
@@ -163,4 +200,6 @@ def exported_symbols():
         "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply", "rhmc_block_multishift_cg_batch", "rhmc_ctx_tune_set", "rhmc_ctx_tune_get",
         "rhmc_rational_solve", "rhmc_rational_solve_bytes", "rhmc_selftest_bounded_wait", "rhmc_force_lie",
         "rhmc_probe_alu_peaks", "rhmc_profile_read_flops", "rhmc_selftest_fp64_helpers",
+        "rhmc_gauge_action", "rhmc_kinetic_energy", "rhmc_momenta_from_normals", "rhmc_gauge_momentum",
+        "rhmc_momentum_update", "rhmc_link_update", "rhmc_md_evolve", "rhmc_hmc_trajectory",
     ]

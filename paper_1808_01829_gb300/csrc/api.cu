@@ -106,12 +106,6 @@ void set_error(const char *fmt, ...) {
   va_end(ap);
 }
 
-#define RHMC_TRY(...)                   \
-  do {                                  \
-    rhmc_status_t st_ = (__VA_ARGS__);  \
-    if (st_ != RHMC_OK) return st_;     \
-  } while (0)
-
 constexpr int kParts = 304;           // partial sums of the simple reductions (2 CTAs per SM)
 constexpr int kGramParts = 1;         // the Gram kernels deliver the summed n x n matrix
 constexpr double kReliableDelta = 0.1;
@@ -191,6 +185,8 @@ struct rhmc_ctx {
   int tune[TUNE_NKEYS] = {};       // per-context launch settings (0: the process-wide value)
   std::vector<std::unique_ptr<SolverLane>> lanes;  // concurrent defect corrections
   double *d_parts = nullptr;       // partial sums of rhmc_force_lie's norm (kParts)
+  void *md_buf = nullptr;          // molecular-dynamics fields (momenta, force, trial links)
+  size_t md_bytes = 0;
 };
 
 namespace rhmc {
@@ -1009,6 +1005,38 @@ rhmc_status_t ctx_geometry(const rhmc_ctx_t *c, int *device, Geom *g, double *ma
   return RHMC_OK;
 }
 
+rhmc_status_t ctx_lattice(const rhmc_ctx_t *c, int *device, Geom *g) {
+  if (!c) {
+    set_error("null context");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  *device = c->device;
+  *g = c->g;
+  return RHMC_OK;
+}
+
+rhmc_status_t ctx_partials(rhmc_ctx_t *c, double **parts, int *nparts) {
+  if (!c->d_parts) RHMC_CUDA_TRY(cudaMalloc(&c->d_parts, sizeof(double) * kParts));
+  *parts = c->d_parts;
+  *nparts = kParts;
+  return RHMC_OK;
+}
+
+rhmc_status_t ctx_md_buffer(rhmc_ctx_t *c, size_t bytes, void **buf) {
+  if (c->md_bytes < bytes) {
+    if (c->md_buf) {
+      RHMC_CUDA_TRY(cudaDeviceSynchronize());
+      RHMC_CUDA_TRY(cudaFree(c->md_buf));
+    }
+    c->md_buf = nullptr;
+    c->md_bytes = 0;
+    RHMC_CUDA_TRY(cudaMalloc(&c->md_buf, bytes));
+    c->md_bytes = bytes;
+  }
+  *buf = c->md_buf;
+  return RHMC_OK;
+}
+
 // ------------------------------------------------------------ per-vector SCG baseline
 static size_t scg_bytes(const Geom &g, int ns) {
   Arena a(nullptr);
@@ -1176,6 +1204,7 @@ rhmc_status_t rhmc_destroy(rhmc_ctx_t *c) {
   c->main.release();
   if (c->pool) cudaFree(c->pool);
   if (c->d_parts) cudaFree(c->d_parts);
+  if (c->md_buf) cudaFree(c->md_buf);
   for (int q = 0; q < 3; ++q) {
     if (c->ev_base[q]) cudaEventDestroy(c->ev_base[q]);
     if (c->ev_side[q]) cudaEventDestroy(c->ev_side[q]);

@@ -142,6 +142,12 @@ void prof_flops(double flops);  // tensor-core flops of the launch just recorded
     }                                                                                          \
   } while (0)
 
+#define RHMC_TRY(...)                   \
+  do {                                  \
+    rhmc_status_t st_ = (__VA_ARGS__);  \
+    if (st_ != RHMC_OK) return st_;     \
+  } while (0)
+
 #define RHMC_LAUNCH_CHECK()                                                                    \
   do {                                                                                         \
     ::rhmc::count_launch();                                                                    \

@@ -163,6 +163,14 @@ struct CtxTuneScope {
 rhmc_status_t ctx_geometry(const rhmc_ctx_t *ctx, int *device, Geom *g, double *mass, const double2 **l64_even,
                            const double2 **l64_odd);
 
+// api.cu: device and geometry of a context (no gauge field needed), and its
+// scratch array of per-CTA partial sums (allocated on first use)
+rhmc_status_t ctx_lattice(const rhmc_ctx_t *ctx, int *device, Geom *g);
+rhmc_status_t ctx_partials(rhmc_ctx_t *ctx, double **parts, int *nparts);
+// api.cu: the context's molecular-dynamics buffer, at least `bytes` long (kept
+// across calls, reallocated when too small)
+rhmc_status_t ctx_md_buffer(rhmc_ctx_t *ctx, size_t bytes, void **buf);
+
 // scg.cu (per-vector FP64 multishift CG baseline)
 struct ScgState;
 

@@ -120,6 +120,13 @@ def gaussian_pseudofermions(dims, n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(z[..., 0] + 1j * z[..., 1])
 
 
+def momentum_normals(dims, seed: int) -> np.ndarray:
+    """Standard normals p^a of the momentum heatbath, shape (Lt, Lz, Ly, Lx, 4, 8) float64."""
+    lx, ly, lz, lt = _check_dims(dims)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((lt, lz, ly, lx, 4, 8))
+
+
 def random_gauge_transform(dims, seed: int = SEED_GAUGE_TRANSFORM) -> np.ndarray:
     """Random g(x) in SU(3), shape (Lt, Lz, Ly, Lx, 3, 3) complex128."""
     lx, ly, lz, lt = _check_dims(dims)

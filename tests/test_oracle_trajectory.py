@@ -128,3 +128,36 @@ def test_omf2_with_pseudofermions_dH_scaling_and_reversibility():
     U1, P1 = tr.trajectory(dims, mass, U, P, Phi, beta, ra_md, tau, 2, 2, 1.0 / 6.0, 1e-13)
     U2, P2 = tr.trajectory(dims, mass, U1, -P1, Phi, beta, ra_md, tau, 2, 2, 1.0 / 6.0, 1e-13)
     assert np.abs(U2 - U).max() <= 1e-11 and np.abs(P2 + P).max() <= 1e-11
+
+
+def test_heatbath_inverts_the_action():
+    """Phi = R_hb(A) eta with R_hb ~ x^(1/16) and S_f = Phi^dagger R_act(A) Phi with
+    R_act ~ x^(-1/8): R_hb R_act R_hb ~ 1 on the spectrum, so S_f = |eta|^2 up to the
+    rationals' relative errors (Sec. II heatbath, Sec. IV accuracies)."""
+    dims, mass, n_pf = (4, 4, 4, 4), 0.1, 2
+    ra_hb = rational_approx(1.0 / 16, 1e-3, 64.0, 8)
+    ra_act = rational_approx(-1.0 / 8, 1e-3, 64.0, 8)
+    U = syn.random_links(dims, 0.5, 53)
+    eta = syn.gaussian_pseudofermions(dims, n_pf, 54)
+    Phi = tr.heatbath(dims, mass, U, eta, ra_hb, 1e-13)
+    Sf = tr.fermion_action(dims, mass, U, Phi, ra_act, 1e-13)
+    e2 = float(np.sum(np.abs(eta) ** 2))
+    assert abs(Sf - e2) <= (ra_act.error + 2 * ra_hb.error) * e2 + 1e-10 * e2, (Sf, e2)
+    # a wrong sign of the heatbath power would be far off
+    assert abs(tr.fermion_action(dims, mass, U, eta, ra_act, 1e-13) - e2) > 1e-3 * e2
+
+
+def test_hmc_trajectory_record():
+    """The accept/reject step: H from its parts, acceptance when u < exp(-dH), and the
+    links returned are the trial links on accept and the old ones on reject."""
+    dims, beta = (2, 2, 2, 4), 5.12
+    U = syn.random_links(dims, 0.3, 55)
+    p = syn.momentum_normals(dims, 56)
+    P = tr.momenta_from_normals(p)
+    args = (dims, 0.0, U, p, None, beta, None, None, None, 0.5, 2, 1, 1.0 / 6.0, 0.0, 0.0)
+    Uacc, rec = tr.hmc_trajectory(*args, 0.0)
+    assert abs(rec["H_old"] - (tr.kinetic(P) + tr.gauge_action(U, beta))) <= 1e-12 * rec["H_old"]
+    assert rec["accepted"] and Uacc is rec["U1"]
+    Urej, rec2 = tr.hmc_trajectory(*args, 1.0)
+    assert rec2["dH"] == rec["dH"]
+    assert rec2["accepted"] == (rec["dH"] <= 0) and (Urej is U) == (rec["dH"] > 0)
