@@ -20,6 +20,9 @@ Also reported on the same line:
 * alu_peaks and roofline_alu: the measured FP32 / FP64 CUDA-core peaks and the
   fractions of them reached by the double-float operator (FP32-ALU bound), the
   FP64 operator of the per-vector baseline and the n x n coefficient chain;
+* trajectory: time per RHMC trajectory (Sec. II set-up, Sec. IV parameters) on the
+  paper's 8^4 lattice, the FP64 gauge kernels at 24^4 against the measured FP64
+  peak, and the trajectory oracle on a bounded sample;
 * cpu_baseline: the FP64 CPU oracle on the host cores, on a bounded sample.
 
 --impl reference times the oracle (the only reference available: the paper
@@ -78,6 +81,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 per-vector SCG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-traj", action="store_true", help="skip the RHMC trajectory measurement")
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="rhmc_tune_set(KEY, VALUE) before the run (repeatable; recorded in config)")
     return ap.parse_args()
@@ -337,6 +341,114 @@ def run_batch(dev, reps=3):
     return res
 
 
+# ------------------------------------------------------------------ RHMC trajectory
+TRAJ = {
+    "workload": "RHMC trajectory on 8^4 (the paper's lattice, Sec. IV), beta=5.12, m=0.025, n_pf=4, eps=0.5 links; "
+                "MD/action x^(-1/16), heatbath x^(+1/32), 12 shifts on [2e-3,64]; tau=1, n_steps=10, n_gauge=3, "
+                "lambda=1/6 (two-level OMF2); MD solves mixed 1e-7, heatbath/action FP64 1e-14",
+    "dims": (8, 8, 8, 8), "mass": 0.025, "n_pf": 4, "beta": 5.12, "tau": 1.0, "n_steps": 10, "n_gauge": 3,
+    "lam": 1.0 / 6, "tol_md": 1e-7, "tol_action": 1e-14,
+}
+# real flops per link of the FP64 trajectory kernels (3 x 3 complex product = 27 complex MACs
+# = 216 flops): gauge kick 13 products (six staples of two products each, then U V); link
+# update 17 (degree-16 Taylor polynomial in Horner form, then E U; no squaring at these steps)
+TRAJ_FLOPS = {"gauge_kick": 13 * 216, "link_update": 17 * 216}
+
+
+def run_trajectory(dev, fp64_peak, with_oracle, reps=3):
+    """Time per RHMC trajectory (rhmc_hmc_trajectory) on the 8^4 workload above, the FP64
+    gauge kernels at 24^4 against the measured FP64 peak, and the oracle on a bounded
+    sample (one outer OMF2 step with its gauge drifts, plus the heatbath and the two
+    actions, scaled to n_steps outer steps)."""
+    import torch
+
+    from paper_1808_01829_gb300 import hmc
+    from paper_1808_01829_gb300 import synthetic as syn
+    from paper_1808_01829_gb300.api import RhmcContext
+    from paper_1808_01829_gb300.remez import rational_approx
+
+    T = TRAJ
+    dims, n = T["dims"], T["n_pf"]
+    ra = rational_approx(-1.0 / (4 * n), 2e-3, 64.0, 12)
+    hb = rational_approx(1.0 / (8 * n), 2e-3, 64.0, 12)
+    U0 = syn.random_links(dims, 0.5, syn.seed_gauge(20))
+    p = torch.from_numpy(syn.momentum_normals(dims, 21)).to(dev)
+    eta = torch.from_numpy(syn.gaussian_pseudofermions(dims, n, 22)).to(dev)
+    ctx = RhmcContext(dims, T["mass"], device=dev.index or 0)
+    ctx.set_gauge(torch.from_numpy(U0).to(dev))
+    prm = hmc.MdParams(beta=T["beta"], tau=T["tau"], n_steps=T["n_steps"], n_gauge=T["n_gauge"], lam=T["lam"],
+                       tol_md=T["tol_md"], precision="mixed")
+    stream = torch.cuda.current_stream(dev)
+    times, rec = [], None
+    for it in range(reps + 1):
+        U = torch.from_numpy(U0).to(dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rec = hmc.trajectory(ctx, U, p, eta, hb, ra, ra, prm, tol_action=T["tol_action"], u=0.5)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            times.append(a.elapsed_time(b))
+    ctx.close()
+    out = {"workload": T["workload"], "ms_per_trajectory": statistics.median(times),
+           "timing": f"median of {reps} after one warm-up, CUDA events", "dH": rec["dH"],
+           "accepted_at_u_0.5": rec["accepted"], "force_evals": rec["md"]["force_evals"],
+           "gauge_kicks": rec["md"]["gauge_force_evals"], "md_solver_iters": rec["md"]["solver_iters"],
+           "md_max_rel_resid": rec["md"]["max_rel_resid"]}
+
+    # FP64 gauge kernels at 24^4 (FP64-ALU bound): events around 10 launches each
+    d24 = (24, 24, 24, 24)
+    c24 = RhmcContext(d24, 0.01, device=dev.index or 0)
+    U24 = torch.from_numpy(syn.random_links(d24, 0.5, syn.seed_gauge(3))).to(dev)
+    P24 = hmc.momenta(c24, torch.from_numpy(syn.momentum_normals(d24, 23)).to(dev))
+    links = 4 * c24.V
+    kern = {}
+    for name, fn in (("gauge_kick", lambda: hmc.gauge_kick(c24, U24, P24, T["beta"], 1e-3)),
+                     ("link_update", lambda: hmc.link_update(c24, U24, P24, 1e-3))):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        us = a.elapsed_time(b) * 100.0
+        tf = TRAJ_FLOPS[name] * links / (us * 1e-6) / 1e12
+        kern[name] = {"us_per_launch": us, "bound": "fp64", "achieved": tf, "peak": fp64_peak,
+                      "unit": "TFLOP/s (FP64)", "frac": tf / fp64_peak if fp64_peak else None,
+                      "count": f"{TRAJ_FLOPS[name]} flops per link, {links} links (24^4)"}
+    c24.close()
+    out["kernels_24x24x24x24"] = kern
+
+    # oracle (the trajectory's CPU baseline): one outer OMF2 step (three pseudofermion forces, two
+    # gauge drifts) + heatbath + two actions
+    if not with_oracle:
+        return out
+    try:
+        from oracle import trajectory as tr
+
+        Uc = U0
+        Pc = tr.momenta_from_normals(syn.momentum_normals(dims, 21))
+        etac = syn.gaussian_pseudofermions(dims, n, 22)
+        t0 = time.perf_counter()
+        Phi = tr.heatbath(dims, T["mass"], Uc, etac, hb, T["tol_action"])
+        tr.fermion_action(dims, T["mass"], Uc, Phi, ra, T["tol_action"])
+        t1 = time.perf_counter()
+        tr.trajectory(dims, T["mass"], Uc, Pc, Phi, T["beta"], ra, T["tau"] / T["n_steps"], 1, T["n_gauge"],
+                      T["lam"], T["tol_md"])
+        t2 = time.perf_counter()
+        est = (2 * (t1 - t0) - 0.0) + (t2 - t1) * T["n_steps"]
+        out["cpu_oracle"] = {"value": est * 1e3, "unit": "ms per trajectory", "kind": "oracle",
+                             "cores": os.cpu_count(),
+                             "sample": f"heatbath + one action ({t1 - t0:.2f} s, counted twice for the two "
+                                       f"actions) and one outer OMF2 step ({t2 - t1:.2f} s) x {T['n_steps']}"}
+    except Exception as e:  # a measurement beside the bench line: it never fails the line
+        out["cpu_oracle"] = {"error": f"{type(e).__name__}: {e}"[:200]}
+    return out
+
+
 # ------------------------------------------------------------------ hop widths
 def dslash_widths(ctx, dev, widths=(1, 2, 4, 8, 16), reps=10):
     """FP32 hop at several right-hand-side widths on the bench lattice (the width-1
@@ -589,6 +701,14 @@ def run_gpu(args):
     if not args.no_batch and not args.small:
         batch = run_batch(dev)
 
+    traj = None
+    if not args.no_traj and not args.small and rank == 0:
+        try:
+            traj = run_trajectory(dev, alu["peaks"]["fp64_tflops"] if alu else None,
+                                  with_oracle=not args.no_cpu and world == 1)
+        except Exception as e:  # a measurement beside the bench line: it never fails the line
+            traj = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     widths = None
     if rank == 0 and not args.small:
         try:
@@ -642,6 +762,7 @@ def run_gpu(args):
             "alu_peaks": alu["peaks"] if alu else None,
             "roofline_alu": alu["fractions"] if alu else None,
             "batched_ensemble": batch,
+            "trajectory": traj,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

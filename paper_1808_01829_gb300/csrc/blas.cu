@@ -746,7 +746,9 @@ static rhmc_status_t launch_update_cols_variant(const float2 *Q, float2 *P, floa
 // and the basis) while lane n + j forms column j of X; pass 2: lane n + j
 // forms column j of P from Q's column (a warp shuffle from lane j).  It
 // replaces three passes (Q = W rho^-1, the basis copy, the base update):
-// W, P, X read once, Q, P, X (and the basis block) written once.
+// W, P, X read once, Q, P, X (and the basis block) written once.  The tiles
+// are double-buffered: a warp's next row tile is in flight while the current
+// one is multiplied.
 template <int N, int R, int WW>
 __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restrict__ Wf, float2 *__restrict__ Q,
                                                         float2 *__restrict__ P, float2 *__restrict__ X,
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
   constexpr int CS = (3 * N * N + 1) & ~1;  // coefficient area, padded: the tiles start on 16-byte boundaries
   float2 *cs = reinterpret_cast<float2 *>(smem_raw);  // rho^-1, M1, M2
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2 *wt = cs + CS + (size_t)warp * 3 * TILE, *pt = wt + TILE, *xt = pt + TILE;
+  float2 *wbuf = cs + CS + (size_t)warp * 6 * TILE;  // [2][W, P, X] tiles
   for (int k = threadIdx.x; k < 3 * N * N; k += blockDim.x) cs[k] = coef[k];
   const int kb = (basis && kdev) ? *kdev : -1;
   const bool store_basis = kb >= 0 && kb < cap;
@@ -765,19 +767,29 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
   const bool lo = lane < N, hi = lane >= N && lane < 2 * N;
   const int j = lo ? lane : (hi ? lane - N : 0);
   const long ntiles = (rows + R - 1) / R;
-  for (long tile = (long)blockIdx.x * WW + warp; tile < ntiles; tile += (long)gridDim.x * WW) {
+  const long t0 = (long)blockIdx.x * WW + warp, dt = (long)gridDim.x * WW;
+  auto issue = [&](long tile, int b) {
+    const long r0 = tile * R;
+    const int chunks = (int)min((long)R, rows - r0) * N / 2;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(wbuf + (size_t)b * 3 * TILE);
+    const char *sw = reinterpret_cast<const char *>(Wf + r0 * N);
+    const char *sp = reinterpret_cast<const char *>(P + r0 * N);
+    const char *sx = reinterpret_cast<const char *>(X + r0 * N);
+    for (int c = lane; c < chunks; c += 32) {
+      cpa16(d + 16u * c, sw + 16L * c);
+      cpa16(d + 16u * (TILE / 2 + c), sp + 16L * c);
+      cpa16(d + 16u * (TILE + c), sx + 16L * c);
+    }
+  };
+  if (t0 < ntiles) issue(t0, 0);
+  cp_async_commit();
+  int buf = 0;
+  for (long tile = t0; tile < ntiles; tile += dt, buf ^= 1) {
+    if (tile + dt < ntiles) issue(tile + dt, buf ^ 1);
+    cp_async_commit();
     const long r0 = tile * R;
     const int nr = (int)min((long)R, rows - r0);  // rows is a multiple of 8: nr is even
-    const int chunks = nr * N / 2;
-    auto copy_tile = [&](float2 *dst, const float2 *src) {
-      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-      const char *s8 = reinterpret_cast<const char *>(src);
-      for (int c = lane; c < chunks; c += 32) cpa16(d + 16u * c, s8 + 16L * c);
-    };
-    copy_tile(wt, Wf + r0 * N);
-    copy_tile(pt, P + r0 * N);
-    copy_tile(xt, X + r0 * N);
-    cp_async_commit();
+    const float2 *wt = wbuf + (size_t)buf * 3 * TILE, *pt = wt + TILE, *xt = pt + TILE;
     unsigned long long cr[N], ci[N];
     {  // pass-1 coefficient column: rho^-1 (lanes < N) or M1 (lanes N .. 2N-1)
       const float2 *m = cs + (hi ? N * N : 0) + j;
@@ -788,7 +800,7 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
         ci[k] = pack2(c.y, c.y);
       }
     }
-    cpa_wait<0>();
+    cpa_wait<1>();
     __syncwarp();
     // pass 1: row r of W (lanes < N) or of P (lanes N .. 2N-1) times the lane's column
     float2 qv[R];
@@ -844,8 +856,9 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
         P[(r0 + r) * N + j] = make_float2(qx + A.x - B.y, qy + A.y + B.x);
       }
     }
-    __syncwarp();  // the tiles are refilled for the next row tile
+    __syncwarp();  // buffer buf is refilled for the tile after next
   }
+  cpa_wait<0>();
 }
 
 constexpr int kBaseRows = 8, kBaseWarps = 16;
@@ -858,11 +871,11 @@ rhmc_status_t base_step(const float2 *W, float2 *Q, float2 *P, float2 *X, const 
 #define L_BASE(NN)                                                                                                 \
   {                                                                                                                \
     const int threads = kBaseWarps * 32;                                                                           \
-    const size_t smem = (((3 * NN * NN + 1) & ~1) + (size_t)kBaseWarps * 3 * kBaseRows * NN) * sizeof(float2);    \
+    const size_t smem = (((3 * NN * NN + 1) & ~1) + (size_t)kBaseWarps * 6 * kBaseRows * NN) * sizeof(float2);    \
     static std::once_flag attr;                                                                                    \
     std::call_once(attr, [] {                                                                                      \
       cudaFuncSetAttribute(k_base_step<NN, kBaseRows, kBaseWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                           100 * 1024);                                                                            \
+                           200 * 1024);                                                                            \
     });                                                                                                            \
     const long ntiles = (rows + kBaseRows - 1) / kBaseRows;                                                        \
     long grid = (ntiles + kBaseWarps - 1) / kBaseWarps;                                                            \
