@@ -462,6 +462,8 @@ rhmc_status_t rhmc_profile_enable(int on);
  *   RHMC_TUNE_BASIS_ACC_KT        the tensor-core assembly moves its accumulator into the correctly
  *                                 rounded running sum every this many K tiles of 64 reals (12 MMAs
  *                                 each; 0: built-in)
+ *   RHMC_TUNE_NXN_FP64            mixed precision: the base n x n steps (alpha_k; rho_k, delta_k)
+ *                                 in native FP64 (1) instead of double-float on the FP32 units (0)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -481,7 +483,8 @@ enum {
   RHMC_TUNE_BASIS_ITERS = 14,
   RHMC_TUNE_BASIS_GEMM = 15,
   RHMC_TUNE_BASIS_CHUNK = 16,
-  RHMC_TUNE_BASIS_ACC_KT = 17
+  RHMC_TUNE_BASIS_ACC_KT = 17,
+  RHMC_TUNE_NXN_FP64 = 18
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

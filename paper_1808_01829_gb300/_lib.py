@@ -25,6 +25,7 @@ RHMC_TUNE_NO_DEFECT_CORRECTION = 13
 RHMC_TUNE_BASIS_ITERS = 14
 RHMC_TUNE_BASIS_GEMM = 15
 RHMC_TUNE_BASIS_CHUNK = 16
+RHMC_TUNE_NXN_FP64 = 18
 
 STATUS = {
     0: "OK",

@@ -126,6 +126,7 @@ enum TuneKey {
   TUNE_BASIS_GEMM,            // stored-basis assembly: FP32-accurate tcgen05 kernel (0) or CUDA-core kernel (1)
   TUNE_BASIS_CHUNK,           // stored-basis assembly: blocks per FP32 partial sum (0: one GEMM)
   TUNE_BASIS_ACC_KT,          // stored-basis assembly: K tiles per tensor-memory accumulation chunk (0: built-in)
+  TUNE_NXN_FP64,              // mixed: base n x n steps in native FP64 (1) instead of double-float (0)
   TUNE_NKEYS
 };
 int tune_get(int key);

@@ -672,8 +672,15 @@ rhmc_status_t nxn_qr_init(const double2 *partial, int nparts, int n, int nshift,
   RHMC_LAUNCH_CHECK();
   return RHMC_OK;
 }
+// The mixed solve (FP32 fields) takes the double-float kernels of small_df.cu for
+// the base steps unless RHMC_TUNE_NXN_FP64 = 1.
+template <typename T> static bool use_dd(int nparts) {
+  return sizeof(T) == 4 && nparts == 1 && tune_get(TUNE_NXN_FP64) != 1;
+}
 template <typename T>
 rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *mw, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    if (use_dd<T>(nparts)) return nxn_alpha_dd(partial, n, st, k, mw, s);
   prof_begin(PROF_NXN, s);
   k_nxn_alpha<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, mw);
   prof_end(s, 0.0);
@@ -683,6 +690,8 @@ rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *
 template <typename T>
 rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef,
                       cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    if (use_dd<T>(nparts)) return nxn_rho_dd(partial, n, st, k, coef, s);
   prof_begin(PROF_NXN, s);
   k_nxn_rho<T><<<1, 256, 0, s>>>(partial, nparts, n, st, k, coef);
   prof_end(s, 0.0);

@@ -1,0 +1,339 @@
+// Base-system n x n coefficient steps of SBCGrQ (Algorithm 1, line 4 and
+// lines 5-8) in double-float arithmetic for the mixed-precision solve.
+//
+// The FP64 kernels of small.cu are bound by the FP64 unit: on this GPU a warp
+// FP64 instruction holds its sub-partition's FP64 pipe for about 64 cycles, so
+// each LDL^dagger step costs a few hundred cycles however few its items.  Here
+// every value is an unevaluated pair of floats h + l (|l| <= ulp(h)/2) and the
+// arithmetic runs on the FP32 units: products by TwoProduct (an FMA gives the
+// rounding error of h_a h_b exactly, Ogita, Rump and Oishi 2005), sums by
+// TwoSum (Knuth), about 2^-44 relative per operation.  The mixed solve's Gram
+// matrices are sums of FP32 products, so this is far below their own error;
+// the FP64 solve keeps the FP64 kernels.  The outputs are those of small.cu:
+// the FP64 recursion state (alpha_k, Gram1_k, rho_k, delta_k, the base
+// residuals) for the shifted step and the FP32 coefficients of the bulk kernels.
+#include "common.cuh"
+#include "df.cuh"
+#include "kernels.h"
+
+namespace rhmc {
+namespace {
+
+struct dd {
+  float h, l;
+};
+struct cd {
+  dd r, i;
+};
+
+// The _rn intrinsics keep the compiler from contracting the error-free
+// transformations into FMAs.
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return dd{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return dd{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dadd(dd a, dd b) {
+  const dd s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dd dneg(dd a) { return dd{-a.h, -a.l}; }
+__device__ __forceinline__ dd dsub(dd a, dd b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ dd dmul(dd a, dd b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dhalf(dd a) { return dd{0.5f * a.h, 0.5f * a.l}; }
+// 1/x: r = RN(1/h), then r + r (1 - x r) with 1 - x r formed exactly to first order
+__device__ __forceinline__ dd drcp(dd x) {
+  const float r = __frcp_rn(x.h);
+  const float p = __fmul_rn(x.h, r);
+  const float pe = fmaf(x.h, r, -p);
+  float e = __fsub_rn(1.0f, p);  // p is within 2^-23 of 1: exact
+  e = __fsub_rn(e, pe);
+  e = fmaf(-x.l, r, e);
+  return fast_two_sum(r, __fmul_rn(r, e));
+}
+// 1/sqrt(x): y = rsqrt(h), then one Newton step y + y (1 - x y^2) / 2 with the
+// residual 1 - x y^2 formed from the exact square of y
+__device__ __forceinline__ dd drsqrt(dd x) {
+  const float y = rsqrtf(x.h);
+  const float y2 = __fmul_rn(y, y);
+  const float y2e = fmaf(y, y, -y2);
+  const float t = __fmul_rn(x.h, y2);
+  float te = fmaf(x.h, y2, -t);
+  te = fmaf(x.h, y2e, te);
+  te = fmaf(x.l, y2, te);
+  float r = __fsub_rn(1.0f, t);
+  r = __fsub_rn(r, te);
+  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+}
+__device__ __forceinline__ bool dpos(dd a) { return a.h > 0.0f && isfinite(a.h); }
+
+__device__ __forceinline__ cd cconj(cd a) { return cd{a.r, dneg(a.i)}; }
+__device__ __forceinline__ cd cscale(cd a, dd s) { return cd{dmul(a.r, s), dmul(a.i, s)}; }
+__device__ __forceinline__ cd czero_dd() { return cd{dd{0.f, 0.f}, dd{0.f, 0.f}}; }
+
+// running sums of products (TwoProduct errors and TwoSum errors accumulated in
+// one float, folded in at the end)
+struct acc_t {
+  df::DF r, i;
+};
+__device__ __forceinline__ acc_t acc_zero() { return acc_t{df::DF{0.f, 0.f}, df::DF{0.f, 0.f}}; }
+__device__ __forceinline__ acc_t acc_from(cd v) { return acc_t{df::DF{v.r.h, v.r.l}, df::DF{v.i.h, v.i.l}}; }
+// acc += a b
+__device__ __forceinline__ void acc_mac(acc_t &acc, cd a, cd b) {
+  df::df_add_prod(acc.r, a.r.h, a.r.l, b.r.h, b.r.l);
+  df::df_add_prod(acc.r, -a.i.h, -a.i.l, b.i.h, b.i.l);
+  df::df_add_prod(acc.i, a.r.h, a.r.l, b.i.h, b.i.l);
+  df::df_add_prod(acc.i, a.i.h, a.i.l, b.r.h, b.r.l);
+}
+// acc += conj(a) b
+__device__ __forceinline__ void acc_mac_cj(acc_t &acc, cd a, cd b) {
+  df::df_add_prod(acc.r, a.r.h, a.r.l, b.r.h, b.r.l);
+  df::df_add_prod(acc.r, a.i.h, a.i.l, b.i.h, b.i.l);
+  df::df_add_prod(acc.i, a.r.h, a.r.l, b.i.h, b.i.l);
+  df::df_add_prod(acc.i, -a.i.h, -a.i.l, b.r.h, b.r.l);
+}
+__device__ __forceinline__ cd acc_get(const acc_t &a) {
+  const df::DF r = df::df_norm(a.r), i = df::df_norm(a.i);
+  return cd{dd{r.h, r.e}, dd{i.h, i.e}};
+}
+
+__device__ __forceinline__ dd from_d(double x) {
+  const float2 p = df::df_split1(x);
+  return dd{p.x, p.y};
+}
+__device__ __forceinline__ cd from_z(double2 z) { return cd{from_d(z.x), from_d(z.y)}; }
+__device__ __forceinline__ double to_d(dd a) { return df::df_merge1(a.h, a.l); }
+__device__ __forceinline__ double2 to_z(cd a) { return make_double2(to_d(a.r), to_d(a.i)); }
+__device__ __forceinline__ float2 to_f(cd a) { return make_float2(a.r.h, a.i.h); }
+
+__device__ __forceinline__ int tri_row(int e) {  // row a of a packed lower triangle
+  int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= e) ++a;
+  while (a * (a + 1) / 2 > e) --a;
+  return a;
+}
+
+// LDL^dagger of the Hermitian part of the Gram matrix G (FP64, n x n) into A:
+// on return the strictly lower part of A holds L (unit lower), A[k][k].r the
+// pivot D_k, Li = L^-1 (unit lower) and rd[k] = 1 / D_k.  The work of step k
+// (trailing lower triangle and rows k+1.. of L^-1) is one list of items; the
+// item on the next diagonal entry forms the next pivot's reciprocal, so each
+// step takes one barrier.  Returns false (in all threads) if a pivot is not
+// positive and finite.
+__device__ bool ldl_dd(int n, const double2 *G, cd *A, cd *Li, dd *rd, int *flag) {
+  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  if (t < nn) {
+    const int i = t / n, j = t - (t / n) * n;
+    const cd a = from_z(G[t]), b = from_z(G[j * n + i]);
+    A[t] = (i == j) ? cd{a.r, dd{0.f, 0.f}} : cd{dhalf(dadd(a.r, b.r)), dhalf(dsub(a.i, b.i))};
+    Li[t] = cd{dd{i == j ? 1.f : 0.f, 0.f}, dd{0.f, 0.f}};
+  }
+  __syncthreads();
+  if (t == 0) {
+    const dd d = A[0].r;
+    *flag = !dpos(d);
+    rd[0] = drcp(dpos(d) ? d : dd{1.f, 0.f});
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    if (*flag) return false;
+    const dd r = rd[k];
+    const int m = n - 1 - k;
+    const int ntri = m * (m + 1) / 2, nli = m * (k + 1);
+    for (int e = t; e < ntri + nli; e += nt) {
+      if (e < ntri) {
+        // A[i][j] -= (A[i][k] / D_k) conj(A[j][k]),  i >= j > k
+        const int a = tri_row(e), b = e - a * (a + 1) / 2;
+        const int i = k + 1 + a, j = k + 1 + b;
+        const cd lik = cscale(A[i * n + k], dneg(r));
+        acc_t v = acc_from(A[i * n + j]);
+        acc_mac(v, lik, cconj(A[j * n + k]));
+        const cd w = acc_get(v);
+        A[i * n + j] = w;
+        if (i == k + 1 && j == k + 1) {
+          *flag = !dpos(w.r);
+          rd[k + 1] = drcp(dpos(w.r) ? w.r : dd{1.f, 0.f});
+        }
+      } else {
+        // Li[i][j] -= (A[i][k] / D_k) Li[k][j],  i > k >= j
+        const int e2 = e - ntri;
+        const int a = e2 / (k + 1), j = e2 - a * (k + 1);
+        const int i = k + 1 + a;
+        const cd lik = cscale(A[i * n + k], dneg(r));
+        acc_t v = acc_from(Li[i * n + j]);
+        acc_mac(v, lik, Li[k * n + j]);
+        Li[i * n + j] = acc_get(v);
+      }
+    }
+    __syncthreads();
+  }
+  if (*flag) return false;
+  for (int e = t; e < nn; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (i > j) A[e] = cscale(A[e], rd[j]);
+  }
+  __syncthreads();
+  return true;
+}
+
+// ||M e_j|| * scale[j] of an upper-triangular M (16 lanes per column)
+__device__ void colnorms_upper_dd(int n, const cd *M, double *out, const double *scale) {
+  const int t = threadIdx.x;
+  const int j = t >> 4, i = t & 15;
+  df::DF s{0.f, 0.f};
+  if (j < n && i <= j) {
+    const cd z = M[i * n + j];
+    df::df_add_prod(s, z.r.h, z.r.l, z.r.h, z.r.l);
+    df::df_add_prod(s, z.i.h, z.i.l, z.i.h, z.i.l);
+  }
+  const df::DF sn = df::df_norm(s);
+  dd v = dd{sn.h, sn.e};
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const dd u = dd{__shfl_xor_sync(0xffffffffu, v.h, o, 16), __shfl_xor_sync(0xffffffffu, v.l, o, 16)};
+    v = dadd(v, u);
+  }
+  if (j < n && i == 0) {
+    const dd nv = v.h > 0.f ? dmul(v, drsqrt(v)) : dd{0.f, 0.f};
+    out[j] = to_d(nv) * scale[j];
+  }
+}
+
+constexpr int kNN = 256;  // shared matrix capacity (n <= 16)
+}  // namespace
+
+// line 4: alpha_k = Gram1^-1 (Hermitian part of Gram1 = P^dagger (A + sigma_0) P)
+// = L^-dagger D^-1 L^-1; FP64 alpha_k and Gram1_k into the state, -alpha_k (FP32)
+// for line 5
+__global__ void __launch_bounds__(256) k_nxn_alpha_dd(const double2 *G, int n, SolverState *st, int k,
+                                                      float2 *mw_out) {
+  __shared__ cd A[kNN], Li[kNN], S[kNN];
+  __shared__ dd rd[kMaxN];
+  __shared__ int flag;
+  const int cur = k % kSlots;
+  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  if (t == 0) st->kabs[cur] = st->kabs[(k - 1) % kSlots] + 1;
+  if (t < nn) {  // Gram1_k (Hermitian part) for the shifted step
+    const int i = t / n, j = t - (t / n) * n;
+    const double2 a = G[t], b = G[j * n + i];
+    st->G1[cur][t] = (i == j) ? make_double2(a.x, 0.0) : make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  if (!ldl_dd(n, G, A, Li, rd, &flag)) {
+    if (t == 0) st->breakdown = 2;
+    return;
+  }
+  for (int e = t; e < nn; e += nt) S[e] = cscale(Li[e], rd[e / n]);  // S[q][j] = Li[q][j] / D_q
+  __syncthreads();
+  // alpha[i][j] = sum_{q >= j} conj(Li[q][i]) S[q][j], i <= j (column-major packing)
+  for (int e = t; e < n * (n + 1) / 2; e += nt) {
+    const int j = tri_row(e), i = e - j * (j + 1) / 2;
+    acc_t acc = acc_zero();
+    for (int q = j; q < n; ++q) acc_mac_cj(acc, Li[q * n + i], S[q * n + j]);
+    const cd v = acc_get(acc);
+    const double2 vz = to_z(v);
+    const float2 vf = to_f(v);
+    st->alpha[cur][i * n + j] = vz;
+    mw_out[i * n + j] = make_float2(-vf.x, -vf.y);
+    if (i != j) {
+      st->alpha[cur][j * n + i] = make_double2(vz.x, -vz.y);
+      mw_out[j * n + i] = make_float2(-vf.x, vf.y);
+    }
+  }
+}
+
+// lines 5-8: rho_k = R = D^1/2 L^dagger of the LDL^dagger of W^dagger W (thin QR);
+// coef = [rho_k^-1, M1 = alpha_k delta_{k-1}, rho_k^dagger] (FP32); FP64 rho_k,
+// delta_k = rho_k delta_{k-1} and the base column residuals into the state
+__global__ void __launch_bounds__(256) k_nxn_rho_dd(const double2 *G, int n, SolverState *st, int k, float2 *coef) {
+  __shared__ cd A[kNN], Li[kNN], R[kNN], Dp[kNN];
+  __shared__ dd rd[kMaxN], sd[kMaxN], rsd[kMaxN];
+  __shared__ int flag;
+  const int cur = k % kSlots, prev = (k - 1) % kSlots;
+  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  if (!ldl_dd(n, G, A, Li, rd, &flag)) {
+    if (t == 0) st->breakdown = 3;
+    return;
+  }
+  if (t < n) {
+    const dd d = A[t * n + t].r;
+    const dd y = drsqrt(d);
+    rsd[t] = y;
+    sd[t] = dmul(d, y);
+  }
+  if (t < nn) Dp[t] = from_z(st->delta[prev][t]);
+  __syncthreads();
+  // R = D^1/2 L^dagger (upper) and R^-1 = L^-dagger D^-1/2 (upper)
+  for (int e = t; e < nn; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    cd r = czero_dd(), ri = czero_dd();
+    if (i == j) {
+      r.r = sd[i];
+      ri.r = rsd[i];
+    } else if (i < j) {
+      r = cscale(cconj(A[j * n + i]), sd[i]);
+      ri = cscale(cconj(Li[j * n + i]), rsd[j]);
+    }
+    R[e] = r;
+    st->rho[cur][e] = to_z(r);
+    coef[e] = to_f(ri);
+  }
+  __syncthreads();
+  // A and Li are free now: alpha_k (FP64 state) into A, delta_k into Li below
+  cd *Al = A, *Dk = Li;
+  if (t < nn) {
+    const int i = t / n, j = t - (t / n) * n;
+    coef[2 * nn + t] = to_f(cconj(R[j * n + i]));  // rho^dagger
+    Al[t] = from_z(st->alpha[cur][t]);
+  }
+  __syncthreads();
+  // M1[i][j] = sum_{q <= j} alpha[i][q] delta[q][j];
+  // delta_k[i][j] = sum_{i <= q <= j} rho[i][q] delta[q][j] (upper)
+  for (int e = t; e < nn + n * (n + 1) / 2; e += nt) {
+    if (e < nn) {
+      const int j = e / n, i = e - (e / n) * n;
+      acc_t acc = acc_zero();
+      for (int q = 0; q <= j; ++q) acc_mac(acc, Al[i * n + q], Dp[q * n + j]);
+      coef[nn + i * n + j] = to_f(acc_get(acc));
+    } else {
+      const int e2 = e - nn;
+      const int j = tri_row(e2), i = e2 - j * (j + 1) / 2;
+      acc_t acc = acc_zero();
+      for (int q = i; q <= j; ++q) acc_mac(acc, R[i * n + q], Dp[q * n + j]);
+      const cd v = acc_get(acc);
+      Dk[i * n + j] = v;
+      if (i != j) Dk[j * n + i] = czero_dd();
+    }
+  }
+  __syncthreads();
+  if (t < nn) st->delta[cur][t] = to_z(Dk[t]);
+  colnorms_upper_dd(n, Dk, st->res[0], st->inv_d0);
+  if (t == 0) st->upd[0] = 1;
+}
+
+rhmc_status_t nxn_alpha_dd(const double2 *gram, int n, SolverState *st, int k, float2 *mw, cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
+  k_nxn_alpha_dd<<<1, 256, 0, s>>>(gram, n, st, k, mw);
+  prof_end(s, 0.0);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
+rhmc_status_t nxn_rho_dd(const double2 *gram, int n, SolverState *st, int k, float2 *coef, cudaStream_t s) {
+  prof_begin(PROF_NXN, s);
+  k_nxn_rho_dd<<<1, 256, 0, s>>>(gram, n, st, k, coef);
+  prof_end(s, 0.0);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
+}  // namespace rhmc

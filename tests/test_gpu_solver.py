@@ -365,3 +365,32 @@ def test_force_double_float_matches_native_fp64():
     Go = oracle.force(dims, U, X.cpu().numpy(), ra.alpha).reshape(g_64.shape)
     assert np.linalg.norm(g_df - Go) <= 1e-12 * np.linalg.norm(Go)
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [1, 5, 16])
+def test_nxn_double_float_and_fp64_agree(n):
+    """The mixed solve's base n x n steps (alpha_k; rho_k, delta_k): double-float on the
+    FP32 units (built-in) and native FP64 both reach the tolerance with solutions within
+    the oracle's solution-error bound, in the same number of iterations (the recursions
+    differ by about 1e-13 relative)."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    dims, mass = (8, 4, 4, 6), 0.05
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1210)
+    B = syn.gaussian_pseudofermions(dims, n, 2210)
+    ctx = make_ctx(dims, mass, U)
+    Xo, _, _ = oracle.sbcgrq(dims, mass, U, B, ra.beta, tol=1e-13)
+    iters = []
+    try:
+        for fp64 in (0, 1):
+            ctx.tune_set(_lib.RHMC_TUNE_NXN_FP64, fp64)
+            Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-9, precision="mixed")
+            assert info.true_rel_resid_max <= 1e-9
+            _check_solution(dims, mass, U, B, ra.beta, Xg.cpu().numpy(), 1e-9, Xo)
+            iters.append(info.iters)
+    finally:
+        ctx.tune_set(_lib.RHMC_TUNE_NXN_FP64, 0)
+    assert abs(iters[0] - iters[1]) <= 1, iters
+    ctx.close()
