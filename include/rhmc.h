@@ -464,6 +464,8 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 each; 0: built-in)
  *   RHMC_TUNE_NXN_FP64            mixed precision: the base n x n steps (alpha_k; rho_k, delta_k)
  *                                 in native FP64 (1) instead of double-float on the FP32 units (0)
+ *   RHMC_TUNE_BASE_TILE           fused base step at n = 16: rows per warp tile x warps per CTA,
+ *                                 0 = 8 x 16, 1 = 16 x 12, 2 = 16 x 8, 3 = 8 x 12
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -484,7 +486,8 @@ enum {
   RHMC_TUNE_BASIS_GEMM = 15,
   RHMC_TUNE_BASIS_CHUNK = 16,
   RHMC_TUNE_BASIS_ACC_KT = 17,
-  RHMC_TUNE_NXN_FP64 = 18
+  RHMC_TUNE_NXN_FP64 = 18,
+  RHMC_TUNE_BASE_TILE = 19
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

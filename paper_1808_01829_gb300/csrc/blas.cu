@@ -90,7 +90,11 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // PK (FP32, n = 16): packed FP32x2 FMAs, conj(a) b from the duplicated pairs
-// (a.re, a.re), (a.im, a.im) times the (re, im) pair of b as loaded.
+// (a.re, a.re), (a.im, a.im) times the (re, im) pair of b as loaded.  Every use
+// of the Gram matrix here is Hermitian (P^dagger (A + sigma) P, W^dagger W,
+// B^dagger B), so the packed form computes one circulant half: lane pair i
+// forms G[i][(i + o) mod 16] for o = 0 .. 8 (5 entries per lane instead of 8)
+// and the CTA reduction writes the rest as conjugates.
 template <typename T, int N, bool SAME, bool PK>
 __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
                                               double2 *__restrict__ partial) {
@@ -98,9 +102,10 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   constexpr int E = (N * N + 31) / 32;   // entries per lane
   constexpr bool STRUCT = (N == 16);
   constexpr bool PACKED = PK && STRUCT && sizeof(T) == 4;
-  unsigned long long p1[PACKED ? 8 : 1], p2[PACKED ? 8 : 1];  // (sum a.re b.re, a.re b.im), (a.im b.re, a.im b.im)
+  constexpr int NQ = 5;  // circulant entries per lane (packed form)
+  unsigned long long p1[PACKED ? NQ : 1], p2[PACKED ? NQ : 1];  // (sum a.re b.re, a.re b.im), (a.im b.re, a.im b.im)
 #pragma unroll
-  for (int q = 0; q < (PACKED ? 8 : 1); ++q) p1[q] = p2[q] = 0ull;
+  for (int q = 0; q < (PACKED ? NQ : 1); ++q) p1[q] = p2[q] = 0ull;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int STAGE = (SAME ? 1 : 2) * TE;  // complex per pipeline stage
@@ -144,19 +149,18 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
     __syncwarp();
     const C<T> *ta = sa(st), *tb = sb(st);
     if constexpr (PACKED) {
-      const int i = lane >> 1, j0 = (lane & 1) * 8;
+      // lane pair i: offsets o = 5 h + q (h = lane & 1; o = 9 is computed and dropped)
+      const int i = lane >> 1, o0 = (lane & 1) * NQ;
 #pragma unroll 4
       for (int r = 0; r < kGramTileRows; ++r) {
         const float2 a = *reinterpret_cast<const float2 *>(ta + r * N + i);
         const unsigned long long axx = pack2(a.x, a.x), ayy = pack2(a.y, a.y);
-        const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(tb + r * N + j0);
+        const unsigned long long *br = reinterpret_cast<const unsigned long long *>(tb + r * N);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const ulonglong2 b2 = bp[q];
-          p1[2 * q] = fma2(axx, b2.x, p1[2 * q]);
-          p2[2 * q] = fma2(ayy, b2.x, p2[2 * q]);
-          p1[2 * q + 1] = fma2(axx, b2.y, p1[2 * q + 1]);
-          p2[2 * q + 1] = fma2(ayy, b2.y, p2[2 * q + 1]);
+        for (int q = 0; q < NQ; ++q) {
+          const unsigned long long bv = br[(i + o0 + q) & (N - 1)];
+          p1[q] = fma2(axx, bv, p1[q]);
+          p2[q] = fma2(ayy, bv, p2[q]);
         }
       }
     } else if (STRUCT) {
@@ -183,21 +187,27 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
     st ^= 1;
   }
   cp_async_wait0();
-  if constexpr (PACKED) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float2 u = unpack2(p1[q]), v = unpack2(p2[q]);
-      acc[q].x = u.x + v.y;
-      acc[q].y = u.y - v.x;
-    }
-  }
   __syncthreads();
   // CTA reduction in FP64 (reuses the tile buffers), then one partial per entry
   double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [kGramWarps][N*N]
+  if constexpr (PACKED) {
+    const int i = lane >> 1, o0 = (lane & 1) * NQ;
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const int e = STRUCT ? (lane >> 1) * N + (lane & 1) * 8 + q : lane + 32 * q;
-    if (e < N * N) red[warp * N * N + e] = make_double2((double)acc[q].x, (double)acc[q].y);
+    for (int q = 0; q < NQ; ++q) {
+      const int o = o0 + q;
+      if (o > N / 2) continue;
+      const float2 u = unpack2(p1[q]), v = unpack2(p2[q]);
+      const double gx = (double)(u.x + v.y), gy = (double)(u.y - v.x);
+      const int j = (i + o) & (N - 1);
+      red[warp * N * N + i * N + j] = make_double2(gx, gy);
+      if (o > 0 && 2 * o != N) red[warp * N * N + j * N + i] = make_double2(gx, -gy);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int e = STRUCT ? (lane >> 1) * N + (lane & 1) * 8 + q : lane + 32 * q;
+      if (e < N * N) red[warp * N * N + e] = make_double2((double)acc[q].x, (double)acc[q].y);
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
@@ -863,25 +873,42 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
 
 constexpr int kBaseRows = 8, kBaseWarps = 16;
 
+template <int N, int R, int WW>
+static void launch_base(const float2 *W, float2 *Q, float2 *P, float2 *X, const float2 *coef, float2 *basis, int cap,
+                        const int *kdev, long rows, cudaStream_t s) {
+  const int threads = WW * 32;
+  const size_t smem = (((3 * N * N + 1) & ~1) + (size_t)WW * 6 * R * N) * sizeof(float2);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_base_step<N, R, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  const long ntiles = (rows + R - 1) / R;
+  long grid = (ntiles + WW - 1) / WW;
+  grid = std::min(grid, (long)resident_ctas(k_base_step<N, R, WW>, threads, smem));
+  k_base_step<N, R, WW><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, X, coef, basis, cap, kdev, rows);
+}
+
 rhmc_status_t base_step(const float2 *W, float2 *Q, float2 *P, float2 *X, const float2 *coef, float2 *basis, int cap,
                         const int *kdev, long rows, int n, cudaStream_t s) {
   if (rows % 8) return RHMC_ERR_INVALID_ARG;
   prof_begin(PROF_UPDATE_SHIFTS32, s);
   rhmc_status_t rc = RHMC_OK;
-#define L_BASE(NN)                                                                                                 \
-  {                                                                                                                \
-    const int threads = kBaseWarps * 32;                                                                           \
-    const size_t smem = (((3 * NN * NN + 1) & ~1) + (size_t)kBaseWarps * 6 * kBaseRows * NN) * sizeof(float2);    \
-    static std::once_flag attr;                                                                                    \
-    std::call_once(attr, [] {                                                                                      \
-      cudaFuncSetAttribute(k_base_step<NN, kBaseRows, kBaseWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                           200 * 1024);                                                                            \
-    });                                                                                                            \
-    const long ntiles = (rows + kBaseRows - 1) / kBaseRows;                                                        \
-    long grid = (ntiles + kBaseWarps - 1) / kBaseWarps;                                                            \
-    grid = std::min(grid, (long)resident_ctas(k_base_step<NN, kBaseRows, kBaseWarps>, threads, smem));             \
-    k_base_step<NN, kBaseRows, kBaseWarps><<<(unsigned)grid, threads, smem, s>>>(W, Q, P, X, coef, basis, cap,      \
-                                                                                 kdev, rows);                      \
+  // n = 16: row tile and warps per CTA from RHMC_TUNE_BASE_TILE (0: 8 rows, 16 warps)
+  const int tile = tune_get(TUNE_BASE_TILE);
+#define L_BASE(NN)                                                                               \
+  {                                                                                              \
+    if constexpr (NN == 16) {                                                                    \
+      if (tile == 1)                                                                             \
+        launch_base<NN, 16, 12>(W, Q, P, X, coef, basis, cap, kdev, rows, s);                    \
+      else if (tile == 2)                                                                        \
+        launch_base<NN, 16, 8>(W, Q, P, X, coef, basis, cap, kdev, rows, s);                     \
+      else if (tile == 3)                                                                        \
+        launch_base<NN, 8, 12>(W, Q, P, X, coef, basis, cap, kdev, rows, s);                     \
+      else                                                                                       \
+        launch_base<NN, kBaseRows, kBaseWarps>(W, Q, P, X, coef, basis, cap, kdev, rows, s);     \
+    } else {                                                                                     \
+      launch_base<NN, kBaseRows, kBaseWarps>(W, Q, P, X, coef, basis, cap, kdev, rows, s);       \
+    }                                                                                            \
   }
   RHMC_DISPATCH_N(n, L_BASE)
 #undef L_BASE
@@ -1084,9 +1111,12 @@ __global__ void __launch_bounds__(W * 32, 1) k_axpy_gram_cols(const float2 *__re
   float2 *wrow = wb + 4 * TILE;
   const int h = lane / N, j = lane - (lane / N) * N;
   const bool act = lane < 2 * N;
-  float2 g[N];
+  // W^dagger W is Hermitian: lane j accumulates the circulant half G[(j + o) mod N][j],
+  // o = 0 .. N/2; the reduction writes the other entries as conjugates
+  constexpr int NO = N / 2 + 1;
+  float2 g[NO];
 #pragma unroll
-  for (int k = 0; k < N; ++k) g[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < NO; ++k) g[k] = make_float2(0.f, 0.f);
   float2 cf[PK ? 1 : N];
   unsigned long long cr[PK ? N : 1], ci[PK ? N : 1];
   if (act) load_col<N, PK>(M, j, cf, cr, ci);
@@ -1134,10 +1164,10 @@ __global__ void __launch_bounds__(W * 32, 1) k_axpy_gram_cols(const float2 *__re
       if (act) {
         const float2 *wr = wrow + h * N;
 #pragma unroll
-        for (int i = 0; i < N; ++i) {  // g[i] += conj(Y[r][i]) Y[r][j]
-          const float2 w = wr[i];
-          g[i].x = fmaf(w.x, y.x, fmaf(w.y, y.y, g[i].x));
-          g[i].y = fmaf(w.x, y.y, fmaf(-w.y, y.x, g[i].y));
+        for (int o = 0; o < NO; ++o) {  // g[o] += conj(Y[r][i]) Y[r][j], i = (j + o) mod N
+          const float2 w = wr[j + o < N ? j + o : j + o - N];
+          g[o].x = fmaf(w.x, y.x, fmaf(w.y, y.y, g[o].x));
+          g[o].y = fmaf(w.x, y.y, fmaf(-w.y, y.x, g[o].y));
         }
       }
       __syncwarp();
@@ -1147,15 +1177,20 @@ __global__ void __launch_bounds__(W * 32, 1) k_axpy_gram_cols(const float2 *__re
   cpa_wait<0>();
   // row parities: lane j += lane N + j
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    g[i].x += __shfl_down_sync(0xffffffffu, g[i].x, N);
-    g[i].y += __shfl_down_sync(0xffffffffu, g[i].y, N);
+  for (int o = 0; o < NO; ++o) {
+    g[o].x += __shfl_down_sync(0xffffffffu, g[o].x, N);
+    g[o].y += __shfl_down_sync(0xffffffffu, g[o].y, N);
   }
   __syncthreads();
   double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [W][N * N], reuses the tile buffers
   if (lane < N) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) red[warp * N * N + i * N + lane] = make_double2((double)g[i].x, (double)g[i].y);
+    for (int o = 0; o < NO; ++o) {
+      const int i = lane + o < N ? lane + o : lane + o - N;
+      const double gx = (double)g[o].x, gy = (double)g[o].y;
+      red[warp * N * N + i * N + lane] = make_double2(gx, gy);
+      if (o > 0 && 2 * o != N) red[warp * N * N + lane * N + i] = make_double2(gx, -gy);
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {

@@ -127,6 +127,7 @@ enum TuneKey {
   TUNE_BASIS_CHUNK,           // stored-basis assembly: blocks per FP32 partial sum (0: one GEMM)
   TUNE_BASIS_ACC_KT,          // stored-basis assembly: K tiles per tensor-memory accumulation chunk (0: built-in)
   TUNE_NXN_FP64,              // mixed: base n x n steps in native FP64 (1) instead of double-float (0)
+  TUNE_BASE_TILE,             // fused base step at n = 16: 0 = 8 rows x 16 warps, 1 = 16 x 12, 2 = 16 x 8, 3 = 8 x 12
   TUNE_NKEYS
 };
 int tune_get(int key);
