@@ -99,6 +99,8 @@ rhmc_status_t nxn_alpha(const double2 *partial, int nparts, int n, SolverState *
 // small_df.cu: double-float forms of nxn_alpha / nxn_rho for the mixed solve (summed Gram input)
 rhmc_status_t nxn_alpha_dd(const double2 *gram, int n, SolverState *st, int k, float2 *mw, cudaStream_t s);
 rhmc_status_t nxn_rho_dd(const double2 *gram, int n, SolverState *st, int k, float2 *coef, cudaStream_t s);
+rhmc_status_t nxn_shifts_dd(int n, int nshift, SolverState *st, int k, float2 *coef, double tol_shift, int freeze,
+                            double2 *hist, int cap, cudaStream_t s);
 template <typename T>
 rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k, C<T> *coef, cudaStream_t s);
 // hist (nullable, stored-basis mode): [cap][nshift][2][n*n] FP64, alpha^(s)_k and

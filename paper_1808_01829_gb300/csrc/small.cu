@@ -701,6 +701,9 @@ rhmc_status_t nxn_rho(const double2 *partial, int nparts, int n, SolverState *st
 template <typename T>
 rhmc_status_t nxn_shifts(int n, int nshift, SolverState *st, int k, C<T> *coef, double tol_shift, int freeze,
                          double2 *hist, int cap, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    if (nshift > 1 && tune_get(TUNE_NXN_FP64) != 1)
+      return nxn_shifts_dd(n, nshift, st, k, coef, tol_shift, freeze, hist, cap, s);
   if (nshift > 1) {
     prof_begin(PROF_NXN_SHIFTS, s);
     k_nxn_shifts<T><<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze, hist, cap);

@@ -210,6 +210,105 @@ __device__ void colnorms_upper_dd(int n, const cd *M, double *out, const double 
 }
 
 constexpr int kNN = 256;  // shared matrix capacity (n <= 16)
+
+// Out = op(A) op(B), one element per thread (t < n^2); ca / cb: adjoint of A / B.
+// Out may not alias A or B.  Ends with a barrier.
+__device__ void mm_dd(int n, cd *Out, const cd *A, const cd *B, bool ca = false, bool cb = false) {
+  const int t = threadIdx.x;
+  if (t < n * n) {
+    const int i = t / n, j = t - (t / n) * n;
+    acc_t acc = acc_zero();
+    for (int k = 0; k < n; ++k) {
+      const cd a = ca ? cconj(A[k * n + i]) : A[i * n + k];
+      const cd b = cb ? cconj(B[j * n + k]) : B[k * n + j];
+      acc_mac(acc, a, b);
+    }
+    Out[t] = acc_get(acc);
+  }
+  __syncthreads();
+}
+
+// dst = an FP64 n x n matrix of the state (one element per thread).  Ends with a barrier.
+__device__ void stage(int n, cd *dst, const double2 *src) {
+  if (threadIdx.x < n * n) dst[threadIdx.x] = from_z(src[threadIdx.x]);
+  __syncthreads();
+}
+
+// Ai = A^-1 by Gauss-Jordan elimination with partial pivoting (A is destroyed).
+// Per pivot step: warp 0 finds the pivot row (largest |a|^2 by the leading floats,
+// ties to the lower index), forms the pivot's reciprocal and the elimination
+// factors; the rows are swapped and the pivot row scaled; every other row is then
+// updated.  Returns false (in all threads) for a zero or non-finite pivot.
+__device__ bool inv_general_dd(int n, cd *Ai, cd *A, int *piv, int *flag) {
+  const int t = threadIdx.x, nn = n * n;
+  __shared__ cd fcol[kMaxN];
+  __shared__ cd dinv;
+  if (t < nn) Ai[t] = cd{dd{(t / n) == (t % n) ? 1.f : 0.f, 0.f}, dd{0.f, 0.f}};
+  if (t == 0) *flag = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t < 32) {
+      const int r = t;
+      const cd a = (r < n) ? A[r * n + k] : czero_dd();
+      float v = (r >= k && r < n) ? fmaf(a.r.h, a.r.h, a.i.h * a.i.h) : -1.f;
+      int idx = r;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
+        }
+      }
+      const int p = __shfl_sync(0xffffffffu, idx, 0);
+      const float best = __shfl_sync(0xffffffffu, v, 0);
+      if (r < n) {  // elimination factor of row r after the swap (row p holds the old row k)
+        const int src = (r == p) ? k : r;
+        fcol[r] = (r == k) ? czero_dd() : A[src * n + k];
+      }
+      if (r == 0) {
+        *piv = p;
+        if (!(best > 0.f) || !isfinite(best)) {
+          *flag = 1;
+        } else {
+          const cd d = A[p * n + k];  // conj(d) / |d|^2
+          acc_t m = acc_zero();
+          acc_mac_cj(m, d, d);
+          const dd rr = drcp(acc_get(m).r);
+          dinv = cd{dmul(d.r, rr), dneg(dmul(d.i, rr))};
+        }
+      }
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const int p = *piv;
+    if (t < 2 * n) {  // swap rows k and p, scale the new row k
+      const int col = t % n;
+      cd *M = (t < n) ? A : Ai;
+      const cd rk = M[k * n + col], rp = M[p * n + col];
+      if (p != k) M[p * n + col] = rk;
+      acc_t m = acc_zero();
+      acc_mac(m, rp, dinv);
+      M[k * n + col] = acc_get(m);
+    }
+    __syncthreads();
+    if (t < nn) {
+      const int i = t / n, j = t - (t / n) * n;
+      if (i != k) {
+        const cd f = fcol[i];
+        const cd nf = cd{dneg(f.r), dneg(f.i)};
+        acc_t a1 = acc_from(A[t]), a2 = acc_from(Ai[t]);
+        acc_mac(a1, nf, A[k * n + j]);
+        acc_mac(a2, nf, Ai[k * n + j]);
+        A[t] = acc_get(a1);
+        Ai[t] = acc_get(a2);
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
 }  // namespace
 
 // line 4: alpha_k = Gram1^-1 (Hermitian part of Gram1 = P^dagger (A + sigma_0) P)
@@ -318,6 +417,106 @@ __global__ void __launch_bounds__(256) k_nxn_rho_dd(const double2 *G, int n, Sol
   if (t < nn) st->delta[cur][t] = to_z(Dk[t]);
   colnorms_upper_dd(n, Dk, st->res[0], st->inv_d0);
   if (t == 0) st->upd[0] = 1;
+}
+
+// lines 9-12 for shift s = blockIdx.x + 1 (the FP64 k_nxn_shifts of small.cu in
+// double-float).  With C = alpha_k rho_{k-1} alpha_{k-1}^-1 (alpha_{k-1}^-1 = Gram1_{k-1})
+// and M2_prev = beta^(s)_{k-1} rho_{k-1}^dagger:
+//   T = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,   beta^(s)_k = T^-1   (line 9)
+//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                                   (line 10)
+//   M1 = w_s alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12),
+//   delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (the shifted residual), freezing.
+// The recursion state (alpha^(s), M2_prev, the basis history) stays FP64 in memory.
+__global__ void __launch_bounds__(256) k_nxn_shifts_dd(int n, int nshift, SolverState *st, int k, float2 *coef,
+                                                       double tol_shift, int freeze, double2 *hist, int cap) {
+  __shared__ cd Cs[kNN], A1[kNN], A2[kNN], B[kNN], Bi[kNN], S1[kNN], S2[kNN], S3[kNN];
+  __shared__ int flag, piv;
+  __shared__ float colres[kMaxN];
+  const int s = blockIdx.x + 1;
+  if (s >= nshift) return;
+  const int t = threadIdx.x;
+  const int cur = k % kSlots, prev = (k - 1) % kSlots;
+  const int nn = n * n;
+  if (!st->active[s]) {
+    if (t == 0) st->upd[s] = 0;
+    return;
+  }
+  const int kabs = st->kabs[cur];
+  const dd dsig = from_d(st->sigma[s] - st->sigma[0]);
+  if (t < nn) {
+    S1[t] = from_z(st->alpha[cur][t]);
+    S2[t] = from_z(st->rho[prev][t]);
+    S3[t] = from_z(st->G1[prev][t]);
+  }
+  __syncthreads();
+  mm_dd(n, A1, S1, S2);
+  mm_dd(n, Cs, A1, S3);               // C
+  mm_dd(n, A2, Cs, S2, false, true);  // C rho_{k-1}^dagger
+  stage(n, S3, st->m2_s[s]);
+  mm_dd(n, A1, Cs, S3);  // C M2_prev
+  if (t < nn) {
+    const int i = t / n, j = t - (t / n) * n;
+    cd b = cd{dadd(dmul(dsig, S1[t].r), dsub(A2[t].r, A1[t].r)), dadd(dmul(dsig, S1[t].i), dsub(A2[t].i, A1[t].i))};
+    if (i == j) b.r = dadd(b.r, dd{1.f, 0.f});
+    B[t] = b;
+  }
+  __syncthreads();
+  if (!inv_general_dd(n, Bi, B, &piv, &flag)) {
+    if (t == 0) st->breakdown = 4;
+    return;
+  }
+  stage(n, S3, st->alpha_s[s]);
+  mm_dd(n, A2, Cs, S3);
+  mm_dd(n, A1, Bi, A2);  // alpha^(s)_k
+  stage(n, S2, st->rho[cur]);
+  mm_dd(n, A2, Bi, S2, false, true);  // beta^(s)_k rho_k^dagger
+  const dd w = from_d(st->w1[s]);
+  if (t < nn) {
+    coef[(1 + 2 * s) * nn + t] = to_f(cscale(A1[t], w));
+    coef[(2 + 2 * s) * nn + t] = to_f(A2[t]);
+    const double2 a1 = to_z(A1[t]), a2 = to_z(A2[t]);
+    st->m2_s[s][t] = a2;
+    st->alpha_s[s][t] = a1;
+    if (hist && kabs < cap) {
+      double2 *h = hist + ((size_t)kabs * nshift + s) * 2 * nn;
+      h[t] = a1;
+      h[nn + t] = a2;
+    }
+  }
+  if (t == 0) st->last_k[s] = kabs;
+  stage(n, S3, st->G1[cur]);
+  mm_dd(n, Cs, S2, S3);
+  mm_dd(n, B, Cs, A1);  // delta^(s)_k
+  if (t < n) {
+    df::DF q{0.f, 0.f};
+    for (int i = 0; i < n; ++i) {
+      const cd z = B[i * n + t];
+      df::df_add_prod(q, z.r.h, z.r.l, z.r.h, z.r.l);
+      df::df_add_prod(q, z.i.h, z.i.l, z.i.h, z.i.l);
+    }
+    const df::DF qn = df::df_norm(q);
+    const dd v{qn.h, qn.e};
+    const dd nv = v.h > 0.f ? dmul(v, drsqrt(v)) : dd{0.f, 0.f};
+    const double r = to_d(nv) * st->inv_d0[t];
+    colres[t] = (float)r;
+    st->res[s][t] = r;
+  }
+  __syncthreads();
+  if (t == 0) {
+    float mx = 0.f;
+    for (int j = 0; j < n; ++j) mx = fmaxf(mx, colres[j]);
+    st->upd[s] = 1;
+    if (freeze && (double)mx < tol_shift) st->active[s] = 0;
+  }
+}
+
+rhmc_status_t nxn_shifts_dd(int n, int nshift, SolverState *st, int k, float2 *coef, double tol_shift, int freeze,
+                            double2 *hist, int cap, cudaStream_t s) {
+  prof_begin(PROF_NXN_SHIFTS, s);
+  k_nxn_shifts_dd<<<nshift - 1, 256, 0, s>>>(n, nshift, st, k, coef, tol_shift, freeze, hist, cap);
+  prof_end(s, 0.0);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
 }
 
 rhmc_status_t nxn_alpha_dd(const double2 *gram, int n, SolverState *st, int k, float2 *mw, cudaStream_t s) {
