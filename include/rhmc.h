@@ -466,6 +466,12 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 in native FP64 (1) instead of double-float on the FP32 units (0)
  *   RHMC_TUNE_BASE_TILE           fused base step at n = 16: rows per warp tile x warps per CTA,
  *                                 0 = 8 x 16, 1 = 16 x 12, 2 = 16 x 8, 3 = 8 x 12
+ *   RHMC_TUNE_GRAM_TILE           packed Gram at n = 16: rows per warp tile x warps per CTA,
+ *                                 0 = 16 x 4, 1 = 32 x 8, 2 = 16 x 8, 3 = 8 x 8
+ *   RHMC_TUNE_AXPY_ROWS           fused axpy + Gram at n = 16: 0 = 8-row, 1 = 16-row warp tiles
+ *   RHMC_TUNE_CORRECTION_MARGIN_MILLI  a defect correction of a shift whose true residual is r
+ *                                 stops when its recursive residual is value/1000 x tol / r
+ *                                 (1 .. 999; 0: built-in)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -487,7 +493,10 @@ enum {
   RHMC_TUNE_BASIS_CHUNK = 16,
   RHMC_TUNE_BASIS_ACC_KT = 17,
   RHMC_TUNE_NXN_FP64 = 18,
-  RHMC_TUNE_BASE_TILE = 19
+  RHMC_TUNE_BASE_TILE = 19,
+  RHMC_TUNE_GRAM_TILE = 20,
+  RHMC_TUNE_AXPY_ROWS = 21,
+  RHMC_TUNE_CORRECTION_MARGIN_MILLI = 22
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

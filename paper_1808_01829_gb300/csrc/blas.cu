@@ -95,10 +95,10 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // B^dagger B), so the packed form computes one circulant half: lane pair i
 // forms G[i][(i + o) mod 16] for o = 0 .. 8 (5 entries per lane instead of 8)
 // and the CTA reduction writes the rest as conjugates.
-template <typename T, int N, bool SAME, bool PK>
-__global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
-                                              double2 *__restrict__ partial) {
-  constexpr int TE = kGramTileRows * N;  // complex per tile and operand
+template <typename T, int N, bool SAME, bool PK, int TR = kGramTileRows, int WG = kGramWarps>
+__global__ void __launch_bounds__(WG * 32) k_gram(const C<T> *__restrict__ A, const C<T> *__restrict__ B, long rows,
+                                                  double2 *__restrict__ partial) {
+  constexpr int TE = TR * N;  // complex per tile and operand
   constexpr int E = (N * N + 31) / 32;   // entries per lane
   constexpr bool STRUCT = (N == 16);
   constexpr bool PACKED = PK && STRUCT && sizeof(T) == 4;
@@ -115,13 +115,13 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   C<T> acc[E];
 #pragma unroll
   for (int q = 0; q < E; ++q) acc[q] = czero<T>();
-  const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
-  const long wstride = (long)gridDim.x * kGramWarps;
-  long tile = (long)blockIdx.x * kGramWarps + warp;
+  const long ntiles = (rows + TR - 1) / TR;
+  const long wstride = (long)gridDim.x * WG;
+  long tile = (long)blockIdx.x * WG + warp;
   auto issue = [&](long tl, int st) {
-    const long r0 = tl * kGramTileRows;
-    const int nr = (int)min((long)kGramTileRows, rows - r0);
-    if (nr == kGramTileRows) {
+    const long r0 = tl * TR;
+    const int nr = (int)min((long)TR, rows - r0);
+    if (nr == TR) {
       constexpr int NV = (int)(TE * sizeof(C<T>) / 16);
       const char *ga = reinterpret_cast<const char *>(A + r0 * N);
       const char *gb = reinterpret_cast<const char *>(B + r0 * N);
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
       // lane pair i: offsets o = 5 h + q (h = lane & 1; o = 9 is computed and dropped)
       const int i = lane >> 1, o0 = (lane & 1) * NQ;
 #pragma unroll 4
-      for (int r = 0; r < kGramTileRows; ++r) {
+      for (int r = 0; r < TR; ++r) {
         const float2 a = *reinterpret_cast<const float2 *>(ta + r * N + i);
         const unsigned long long axx = pack2(a.x, a.x), ayy = pack2(a.y, a.y);
         const unsigned long long *br = reinterpret_cast<const unsigned long long *>(tb + r * N);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
     } else if (STRUCT) {
       const int i = lane >> 1, j0 = (lane & 1) * 8;
 #pragma unroll 4
-      for (int r = 0; r < kGramTileRows; ++r) {
+      for (int r = 0; r < TR; ++r) {
         const C<T> a = ta[r * N + i];
         C<T> b[8];
 #pragma unroll
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
       }
     } else {
 #pragma unroll 4
-      for (int r = 0; r < kGramTileRows; ++r)
+      for (int r = 0; r < TR; ++r)
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int e = lane + 32 * q;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   cp_async_wait0();
   __syncthreads();
   // CTA reduction in FP64 (reuses the tile buffers), then one partial per entry
-  double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [kGramWarps][N*N]
+  double2 *red = reinterpret_cast<double2 *>(smem_raw);  // [WG][N*N]
   if constexpr (PACKED) {
     const int i = lane >> 1, o0 = (lane & 1) * NQ;
 #pragma unroll
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_gram(const C<T> *__restrict__ A, const 
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     double2 sum = red[e];
-    for (int w = 1; w < kGramWarps; ++w) {
+    for (int w = 1; w < WG; ++w) {
       sum.x += red[w * N * N + e].x;
       sum.y += red[w * N * N + e].y;
     }
@@ -1229,19 +1229,25 @@ template <int N, bool PK>
 static void launch_axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, float2 *Y, long rows,
                                   double2 *scratch, double2 *out, cudaStream_t s) {
   constexpr int W = axpy_gram_warps<PK>();
-  const int threads = W * 32;
-  const size_t smem = std::max((size_t)W * (4 * kAxpyRows * N + 2 * N) * sizeof(float2),
-                               (size_t)W * N * N * sizeof(double2));
+  // rows per warp tile: 8, or 16 at n = 16 with RHMC_TUNE_AXPY_ROWS = 1
+  constexpr int R = (PK && N == 16) ? 16 : kAxpyRows;
+  const bool big = (PK && N == 16) && tune_get(TUNE_AXPY_ROWS) == 1;
   static std::once_flag attr;
   std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_axpy_gram_cols<N, R, W, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_axpy_gram_cols<N, kAxpyRows, W, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          220 * 1024);
   });
-  const long ntiles = (rows + kAxpyRows - 1) / kAxpyRows;
-  long grid = (ntiles + W - 1) / W;
-  grid = std::min(grid, (long)std::min(kGramCtas, resident_ctas(k_axpy_gram_cols<N, kAxpyRows, W, PK>, threads,
-                                                                  smem)));
-  k_axpy_gram_cols<N, kAxpyRows, W, PK><<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
+  auto run = [&](auto kern, int rr) {
+    const int threads = W * 32;
+    const size_t smem = std::max((size_t)W * (4 * rr * N + 2 * N) * sizeof(float2), (size_t)W * N * N * sizeof(double2));
+    const long ntiles = (rows + rr - 1) / rr;
+    long grid = (ntiles + W - 1) / W;
+    grid = std::min(grid, (long)std::min(kGramCtas, resident_ctas(kern, threads, smem)));
+    kern<<<(unsigned)grid, threads, smem, s>>>(A, C, M, Y, rows, scratch);
+    return grid;
+  };
+  const long grid = big ? run(k_axpy_gram_cols<N, R, W, PK>, R) : run(k_axpy_gram_cols<N, kAxpyRows, W, PK>, kAxpyRows);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, (int)grid, out);
   count_launch();  // the second kernel of this launcher (the caller counts the first)
 }
@@ -1358,28 +1364,43 @@ __global__ void __launch_bounds__(256) k_redot(const double2 *__restrict__ A, co
 
 // ------------------------------------------------------------ launchers
 
-template <typename T, int N, bool PK>
-static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
+template <typename T, int N, bool PK, int TR, int WG>
+static void launch_gram_tw(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
   const bool same = (A == B);
-  const size_t smem = (size_t)kGramWarps * 2 * (same ? 1 : 2) * kGramTileRows * N * sizeof(C<T>);
-  const size_t smem_red = (size_t)kGramWarps * N * N * sizeof(double2);
+  const size_t smem = (size_t)WG * 2 * (same ? 1 : 2) * TR * N * sizeof(C<T>);
+  const size_t smem_red = (size_t)WG * N * N * sizeof(double2);
   const size_t bytes = std::max(smem, smem_red);
   static std::once_flag attr;
   std::call_once(attr, [&] {
-    cudaFuncSetAttribute(k_gram<T, N, true, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_gram<T, N, false, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram<T, N, true, PK, TR, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram<T, N, false, PK, TR, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
-  const long ntiles = (rows + kGramTileRows - 1) / kGramTileRows;
+  const long ntiles = (rows + TR - 1) / TR;
   // one wave: as many CTAs as are resident at once (at most the partials' capacity)
-  const int resident = same ? resident_ctas(k_gram<T, N, true, PK>, 256, bytes)
-                            : resident_ctas(k_gram<T, N, false, PK>, 256, bytes);
-  const int grid = (int)std::min<long>((ntiles + kGramWarps - 1) / kGramWarps, std::min(kGramCtas, resident));
+  const int threads = WG * 32;
+  const int resident = same ? resident_ctas(k_gram<T, N, true, PK, TR, WG>, threads, bytes)
+                            : resident_ctas(k_gram<T, N, false, PK, TR, WG>, threads, bytes);
+  const int grid = (int)std::min<long>((ntiles + WG - 1) / WG, std::min(kGramCtas, resident));
   if (same)
-    k_gram<T, N, true, PK><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+    k_gram<T, N, true, PK, TR, WG><<<grid, threads, bytes, s>>>(A, B, rows, scratch);
   else
-    k_gram<T, N, false, PK><<<grid, 256, bytes, s>>>(A, B, rows, scratch);
+    k_gram<T, N, false, PK, TR, WG><<<grid, threads, bytes, s>>>(A, B, rows, scratch);
   k_gram_sum<<<N * N, 128, 0, s>>>(scratch, grid, out);
   count_launch();  // the second kernel of this launcher (the caller counts the first)
+}
+template <typename T, int N, bool PK>
+static void launch_gram(const C<T> *A, const C<T> *B, long rows, double2 *scratch, double2 *out, cudaStream_t s) {
+  // packed n = 16: tile rows x warps from RHMC_TUNE_GRAM_TILE (0: 16 x 4, measured at 24^4:
+  // 37.6 us against 41.8 for 16 x 8, 38.2 for 32 x 8, 41.5 for 8 x 8)
+  if constexpr (PK && N == 16) {
+    switch (tune_get(TUNE_GRAM_TILE)) {
+      case 1: launch_gram_tw<T, N, PK, 32, 8>(A, B, rows, scratch, out, s); return;
+      case 2: launch_gram_tw<T, N, PK, 16, 8>(A, B, rows, scratch, out, s); return;
+      case 3: launch_gram_tw<T, N, PK, 8, 8>(A, B, rows, scratch, out, s); return;
+      default: launch_gram_tw<T, N, PK, 16, 4>(A, B, rows, scratch, out, s); return;
+    }
+  }
+  launch_gram_tw<T, N, PK, kGramTileRows, kGramWarps>(A, B, rows, scratch, out, s);
 }
 
 // packed FMAs for FP32 at n = 16 unless RHMC_TUNE_AXPY_SCALAR = 1

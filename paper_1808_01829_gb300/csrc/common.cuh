@@ -128,6 +128,9 @@ enum TuneKey {
   TUNE_BASIS_ACC_KT,          // stored-basis assembly: K tiles per tensor-memory accumulation chunk (0: built-in)
   TUNE_NXN_FP64,              // mixed: base n x n steps in native FP64 (1) instead of double-float (0)
   TUNE_BASE_TILE,             // fused base step at n = 16: 0 = 8 rows x 16 warps, 1 = 16 x 12, 2 = 16 x 8, 3 = 8 x 12
+  TUNE_GRAM_TILE,             // packed Gram at n = 16: 0 = 16 rows x 4 warps, 1 = 32 x 8, 2 = 16 x 8, 3 = 8 x 8
+  TUNE_AXPY_ROWS,             // fused axpy + Gram at n = 16: 0 = 8-row tiles, 1 = 16-row tiles
+  TUNE_CORRECTION_MARGIN_MILLI,  // defect corrections stop at this / 1000 x tol / r (0: built-in)
   TUNE_NKEYS
 };
 int tune_get(int key);
