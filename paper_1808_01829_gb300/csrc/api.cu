@@ -122,6 +122,9 @@ constexpr int kCorrectionCheckEvery = 2;  // host checks of a defect-correction 
 // follows only when it does not.  Measured at 24^4 (15 corrections): margin 0.5 took 342
 // iterations, 0.7 266, 0.8 246, 0.9 232 (largest true residual 0.88 tol), 0.95 226.
 constexpr double kCorrectionMargin = 0.9;
+// The multishift phase runs to kPhase1Margin x tol (0.5, 0.7 and 0.9 measured within
+// noise of each other at 24^4: the shifted systems leave it drift-bound either way).
+constexpr double kPhase1Margin = 0.5;
 
 // Bump allocator over a device buffer; with base == nullptr it only measures.
 struct Arena {
@@ -844,7 +847,12 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
   layout_solve(a, c->g, n, ns, prm.mixed, b);
   SolveStats st;
   SolveParams p1 = prm;
-  if (prm.fixed_iters <= 0) p1.tol = 0.5 * prm.tol;
+  if (prm.fixed_iters <= 0) {
+    // the multishift phase runs to kPhase1Margin x tol (recursive residuals; the base system's
+    // is verified by a reliable update at convergence, every shift's by the FP64 check below)
+    const int pm = tune_get(TUNE_PHASE1_MARGIN_MILLI);
+    p1.tol = (pm > 0 && pm < 1000 ? 1e-3 * pm : kPhase1Margin) * prm.tol;
+  }
   PhaseTimer timer(s);
   rhmc_status_t rc = prm.mixed ? solve_phase1<float>(c, B, n, ns, shifts, X, p1, b, st, s)
                                : solve_phase1<double>(c, B, n, ns, shifts, X, p1, b, st, s);

@@ -131,6 +131,7 @@ enum TuneKey {
   TUNE_GRAM_TILE,             // packed Gram at n = 16: 0 = 16 rows x 4 warps, 1 = 32 x 8, 2 = 16 x 8, 3 = 8 x 8
   TUNE_AXPY_ROWS,             // fused axpy + Gram at n = 16: 0 = 8-row tiles, 1 = 16-row tiles
   TUNE_CORRECTION_MARGIN_MILLI,  // defect corrections stop at this / 1000 x tol / r (0: built-in)
+  TUNE_PHASE1_MARGIN_MILLI,   // the multishift phase runs to this / 1000 x tol (0: built-in)
   TUNE_NKEYS
 };
 int tune_get(int key);
