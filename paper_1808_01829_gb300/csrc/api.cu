@@ -696,6 +696,9 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     }
     return RHMC_OK;
   };
+  // FP32 increments to flush into X: in the stored-basis mode those of the shifts s >= 1
+  // stay zero (their solutions come from the assembly), so only the base system's
+  auto nflush = [&]() { return b.basis ? 1 : ns; };
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   // accumulating solve: X^(0) and one field for sum_{s>=1} w_s X^(s)
   RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * (b.accumulate ? std::min(ns, 2) : ns), s));
@@ -782,18 +785,18 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     for (int q = 1; q < ns; ++q) shifts_done = shifts_done && !v.active[q];
     const bool converged = base < target && shifts_done;
     if (mixed && flush_every > 0 && k - last_flush >= flush_every) {
-      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      for (int q = 0; q < nflush(); ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       last_flush = k;
     }
     if (mixed && converged && !prm.verify_at_convergence) {
-      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      for (int q = 0; q < nflush(); ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(finish_basis(k));
       stats.iters = k;
       return RHMC_OK;
     }
     if (mixed && prm.reliable && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
-      for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+      for (int q = 0; q < nflush(); ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
       RHMC_TRY(apply_A_accurate(c, X, b.AP64, b.T64, b.R64, n, sigma0, s));
       RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
       // thin QR of the FP32-rounded true residual (Q is an FP32 basis)
@@ -829,7 +832,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     }
   }
   if (mixed)
-    for (int q = 0; q < ns; ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
+    for (int q = 0; q < nflush(); ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
   RHMC_TRY(finish_basis(k));
   stats.iters = k;
   if (prm.fixed_iters > 0) return RHMC_OK;
