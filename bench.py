@@ -330,9 +330,13 @@ def run_batch(dev, reps=3):
 
     seq_ms, seq = timed(lambda: [c.block_multishift_cg(B, sh, BATCH["tol"], precision="mixed")[1]
                                  for c, B, sh in items])
+    # each member alone (the sum is the sequential time; the largest bounds the batch from below)
+    member_ms = [timed(lambda c=c, B=B, sh=sh: c.block_multishift_cg(B, sh, BATCH["tol"], precision="mixed"))[0]
+                 for c, B, sh in items]
     bat_ms, bat = timed(lambda: [i for _, i in block_multishift_cg_batch(items, BATCH["tol"], precision="mixed")])
     sites_rhs = sum(int(torch.tensor(d).prod()) // 2 * n for d, n in zip(BATCH["dims"], BATCH["n_pf"]))
     res = {"workload": BATCH["workload"], "ms": bat_ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / bat_ms,
+           "member_ms": member_ms,
            "iters": [i.iters for i in bat], "true_rel_resid_max": max(i.true_rel_resid_max for i in bat),
            "autotuned": [{str(k): v for k, v in t.items()} for t in tuned],
            "site_rhs_shifts_per_s": sites_rhs * 12 / (bat_ms * 1e-3)}

@@ -754,7 +754,7 @@ static rhmc_status_t launch_update_cols_variant(const float2 *Q, float2 *P, floa
 // rho^-1, M1, M2 (n x n each).  Each warp stages a tile of R rows of W, P^(0)
 // and X^(0) by cp.async; pass 1: lane j < n forms column j of Q (stored to Q
 // and the basis) while lane n + j forms column j of X; pass 2: lane n + j
-// forms column j of P from Q's column (a warp shuffle from lane j).  It
+// (with lane j) forms column j of P, each lane of the pair half of the sum.  It
 // replaces three passes (Q = W rho^-1, the basis copy, the base update):
 // W, P, X read once, Q, P, X (and the basis block) written once.  The tiles
 // are double-buffered: a warp's next row tile is in flight while the current
@@ -839,32 +839,38 @@ __global__ void __launch_bounds__(WW * 32, 1) k_base_step(const float2 *__restri
         }
       }
     }
-    {  // pass-2 coefficient column: M2 (lanes N .. 2N-1)
+    // pass 2: P = Q + P M2 with the sum over k split between the lane pair (j, N + j):
+    // lane j takes k < N/2, lane N + j the rest; lane j adds Q's column j and stores
+    constexpr int KH = (N + 1) / 2;
+    const int k0 = hi ? N / 2 : 0, k1 = hi ? N : N / 2;
+    {  // pass-2 coefficient half-column of M2 (zero past the lane's range)
       const float2 *m = cs + 2 * N * N + j;
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const float2 c = m[k * N];
-        cr[k] = pack2(c.x, c.x);
-        ci[k] = pack2(c.y, c.y);
+      for (int kk = 0; kk < KH; ++kk) {
+        const int k = k0 + kk;
+        const float2 c = k < k1 ? m[k * N] : make_float2(0.f, 0.f);
+        cr[kk] = pack2(c.x, c.x);
+        ci[kk] = pack2(c.y, c.y);
       }
     }
-    // pass 2: P = Q + P M2, Q's column j from lane j
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const float qx = __shfl_sync(0xffffffffu, qv[r].x, j);
-      const float qy = __shfl_sync(0xffffffffu, qv[r].y, j);
-      if (r < nr && hi) {
-        const float2 *u = pt + r * N;
+      float2 part = make_float2(0.f, 0.f);
+      if (r < nr && (lo || hi)) {
+        const float2 *u = pt + r * N + k0;
         unsigned long long a = 0ull, b = 0ull;
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const unsigned long long v = *reinterpret_cast<const unsigned long long *>(u + k);
-          a = fma2(v, cr[k], a);
-          b = fma2(v, ci[k], b);
+        for (int kk = 0; kk < KH; ++kk) {
+          const unsigned long long v = (k0 + kk < N) ? *reinterpret_cast<const unsigned long long *>(u + kk) : 0ull;
+          a = fma2(v, cr[kk], a);
+          b = fma2(v, ci[kk], b);
         }
         const float2 A = unpack2(a), B = unpack2(b);
-        P[(r0 + r) * N + j] = make_float2(qx + A.x - B.y, qy + A.y + B.x);
+        part = make_float2(A.x - B.y, A.y + B.x);
       }
+      const float ox = __shfl_down_sync(0xffffffffu, part.x, N);
+      const float oy = __shfl_down_sync(0xffffffffu, part.y, N);
+      if (r < nr && lo) P[(r0 + r) * N + j] = make_float2(qv[r].x + part.x + ox, qv[r].y + part.y + oy);
     }
     __syncwarp();  // buffer buf is refilled for the tile after next
   }
