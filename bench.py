@@ -178,6 +178,65 @@ def cpu_sample(cfg, U, Phi, ra, budget_s=20.0):
     return t_iter, t_force, threads
 
 
+# the smaller configurations of the measurement plan (4^4 n_pf=2, 8^4 n_pf=4, 16^3x32 n_pf=8)
+SMALL_CONFIGS = [
+    {"name": "4^4, m=0.1, n_pf=2, 8 shifts of x^(-1/8) on [1e-3,64], eps=0.3", "dims": (4, 4, 4, 4), "mass": 0.1,
+     "n_pf": 2, "ra": (-1.0 / 8, 1e-3, 64.0, 8), "eps": 0.3, "index": 1, "tol": 1e-10, "full": True},
+    {"name": "8^4, m=0.05, n_pf=4, 12 shifts of x^(-1/16) on [2e-3,64], eps=0.5", "dims": (8, 8, 8, 8), "mass": 0.05,
+     "n_pf": 4, "ra": (-1.0 / 16, 2e-3, 64.0, 12), "eps": 0.5, "index": 2, "tol": 1e-10, "full": True},
+    {"name": "16^3x32, m=0.02, n_pf=8, 14 shifts of x^(-1/32) on [1e-3,64], eps=0.5", "dims": (16, 16, 16, 32),
+     "mass": 0.02, "n_pf": 8, "ra": (-1.0 / 32, 1e-3, 64.0, 14), "eps": 0.5, "index": 3, "tol": 1e-8, "full": False},
+]
+
+
+def oracle_configs(reps=3):
+    """The oracle's SBCGrQ (block) and per-vector multishift CG at the smaller
+    configurations, FP64 on all host cores: whole solves with their iteration counts
+    (median of `reps`) at 4^4 and 8^4; at 16^3 x 32, where whole solves take minutes,
+    seconds per iteration from 8 fixed iterations of each (one right-hand side for the
+    per-vector solver)."""
+    import numpy as np
+
+    import oracle
+    from paper_1808_01829_gb300 import synthetic as syn
+    from paper_1808_01829_gb300.remez import rational_approx
+
+    oracle.build()
+    out = []
+    for c in SMALL_CONFIGS:
+        ra = rational_approx(*c["ra"])
+        U = syn.random_links(c["dims"], c["eps"], syn.seed_gauge(c["index"]))
+        B = syn.gaussian_pseudofermions(c["dims"], c["n_pf"], syn.seed_phi(c["index"]))
+        rec = {"config": c["name"], "tol": c["tol"], "cores": oracle.max_threads()}
+        if c["full"]:
+            tb, tp = [], []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                _, it_b, _ = oracle.sbcgrq(c["dims"], c["mass"], U, B, ra.beta, tol=c["tol"], max_iter=50000)
+                tb.append(time.perf_counter() - t0)
+                t0 = time.perf_counter()
+                it_p = 0
+                for j in range(c["n_pf"]):
+                    it_p += oracle.scg(c["dims"], c["mass"], U, np.ascontiguousarray(B[..., j]), ra.beta,
+                                       tol=c["tol"], max_iter=50000)[1]
+                tp.append(time.perf_counter() - t0)
+            rec.update({"sbcgrq_ms": statistics.median(tb) * 1e3, "sbcgrq_iters": it_b,
+                        "pervector_scg_ms": statistics.median(tp) * 1e3, "pervector_scg_iters_total": it_p,
+                        "timing": f"median of {reps}"})
+        else:
+            k = 8
+            t0 = time.perf_counter()
+            oracle.sbcgrq(c["dims"], c["mass"], U, B, ra.beta, fixed_iters=k)
+            t_b = (time.perf_counter() - t0) / k
+            t0 = time.perf_counter()
+            oracle.scg(c["dims"], c["mass"], U, np.ascontiguousarray(B[..., 0]), ra.beta, fixed_iters=k)
+            t_p = (time.perf_counter() - t0) / k
+            rec.update({"sbcgrq_s_per_iter": t_b, "pervector_scg_s_per_iter_per_rhs": t_p,
+                        "timing": f"{k} fixed iterations each, one right-hand side for the per-vector solver"})
+        out.append(rec)
+    return out
+
+
 def cpu_one_thread(cfg, ra):
     """The paper's per-core setting: one oracle SBCGrQ iteration on one thread at a
     lattice of half the extents (1/16 of the volume, same n_pf and shifts), scaled
@@ -731,6 +790,10 @@ def run_gpu(args):
             cpu["parity_vs_oracle"] = oracle_parity(ctx, cfg, U, Phi, ra, G, ws)
         except Exception as e:  # never fails the line
             cpu["parity_vs_oracle"] = {"error": f"{type(e).__name__}: {e}"[:200]}
+        try:  # the oracle's block and per-vector solvers at the smaller configurations
+            cpu["oracle_configs"] = oracle_configs()
+        except Exception as e:  # never fails the line
+            cpu["oracle_configs"] = {"error": f"{type(e).__name__}: {e}"[:200]}
         try:  # the paper's per-core setting, beside the all-cores figure
             t1, sample1 = cpu_one_thread(cfg, ra)
             cpu["one_thread"] = {"value": t1 * last.iters * 1e3, "unit": "ms",

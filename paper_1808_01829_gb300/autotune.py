@@ -5,10 +5,9 @@ profiler, the candidates of
 
 * the FP32 hop: one or two right-hand sides per thread (RHMC_TUNE_HOP_STAGED
   3 / 4), on the FP32 operator;
-* the column-owner shifted-update kernel with packed FP32x2 FMAs: warps per
-  CTA and shifts in flight (RHMC_TUNE_UPDATE_TENSOR variants 5, 10, 11), in a
-  short mixed-precision solve with the given shifts (the scalar-FMA variants
-  are left out: at equal speed per launch they leave a larger FP32 drift);
+* at 16 right-hand sides, the row tiles of the packed Gram (RHMC_TUNE_GRAM_TILE)
+  and of the fused base step (RHMC_TUNE_BASE_TILE), in a short mixed-precision
+  solve with the given shifts;
 
 and keeps the fastest.  The settings are applied to the context
 (rhmc_ctx_tune_set), so ensembles solved together by
@@ -27,9 +26,10 @@ import torch
 from . import _lib, roofline
 
 KEY_HOP = 8          # RHMC_TUNE_HOP_STAGED
-KEY_UPDATE = 6       # RHMC_TUNE_UPDATE_TENSOR
+KEY_BASE_TILE = 19   # RHMC_TUNE_BASE_TILE
+KEY_GRAM_TILE = 20   # RHMC_TUNE_GRAM_TILE
 HOP_CANDIDATES = (3, 4)
-UPDATE_CANDIDATES = (5, 10, 11)
+TILE_CANDIDATES = (0, 1, 2, 3)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rhmc_gb300_autotune.json")
 
 
@@ -51,7 +51,7 @@ def apply(rctx, settings: dict):
 
 
 def reset(rctx):
-    for k in (KEY_HOP, KEY_UPDATE):
+    for k in (KEY_HOP, KEY_BASE_TILE, KEY_GRAM_TILE):
         rctx.tune_set(k, 0)
 
 
@@ -90,21 +90,23 @@ def tune(rctx, n: int, shifts=None, cache: Optional[str] = DEFAULT_CACHE, force:
     if best:
         settings[KEY_HOP] = best[1]
         rctx.tune_set(KEY_HOP, best[1])
-    if shifts:
-        best = None
-        for v in UPDATE_CANDIDATES:
-            rctx.tune_set(KEY_UPDATE, v)
-            try:
-                st = roofline.profile(lambda: rctx.block_multishift_cg(X, shifts, 1e-3, max_iter=12,
-                                                                       precision="mixed", allow_not_converged=True))
-            except _lib.RhmcError:
-                continue
-            t = _per_launch(st, "update_shifts_fp32", per_byte=True)
-            if t is not None and (best is None or t < best[0]):
-                best = (t, v)
-        if best:
-            settings[KEY_UPDATE] = best[1]
-            rctx.tune_set(KEY_UPDATE, best[1])
+    if shifts and n == 16:
+        for tkey, cat in ((KEY_GRAM_TILE, "gram_fp32"), (KEY_BASE_TILE, "update_shifts_fp32")):
+            best = None
+            for v in TILE_CANDIDATES:
+                rctx.tune_set(tkey, v)
+                try:
+                    st = roofline.profile(lambda: rctx.block_multishift_cg(X, shifts, 1e-3, max_iter=12,
+                                                                           precision="mixed",
+                                                                           allow_not_converged=True))
+                except _lib.RhmcError:
+                    continue
+                t = _per_launch(st, cat)
+                if t is not None and (best is None or t < best[0]):
+                    best = (t, v)
+            rctx.tune_set(tkey, best[1] if best else 0)
+            if best:
+                settings[tkey] = best[1]
     if cache:
         db = _load(cache)
         db[key] = {str(k): v for k, v in settings.items()}

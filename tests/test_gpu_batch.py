@@ -70,15 +70,15 @@ def test_autotune_keeps_results(tmp_path):
     need_gpu()
     from paper_1808_01829_gb300 import autotune
 
-    dims, mass, n = (8, 8, 4, 8), 0.05, 8
-    ra = rational_approx(-1.0 / 32, 2e-3, 64.0, 12)
+    dims, mass, n = (8, 8, 4, 8), 0.05, 16
+    ra = rational_approx(-1.0 / 64, 2e-3, 64.0, 12)
     U = syn.random_links(dims, 0.5, 1520)
     B = to_gpu(syn.gaussian_pseudofermions(dims, n, 2520))
     ctx = make_ctx(dims, mass, U)
     try:
         X0, _ = ctx.block_multishift_cg(B, ra.beta, 1e-9, precision="mixed")
         settings = autotune.tune(ctx, n, shifts=ra.beta, cache=str(tmp_path / "tune.json"))
-        assert 8 in settings and 6 in settings
+        assert set(settings) == {8, 19, 20}  # hop, base-step and Gram tiles
         X1, info = ctx.block_multishift_cg(B, ra.beta, 1e-9, precision="mixed")
         assert info.true_rel_resid_max <= 1e-9
         assert np.linalg.norm((X1 - X0).cpu().numpy()) <= 1e-6 * np.linalg.norm(X0.cpu().numpy())

@@ -45,8 +45,9 @@ class FakeCtx:
 
 def test_autotune_picks_applies_and_caches(tmp_path, monkeypatch):
     ctx = FakeCtx()
-    hop_us = {3: 70.0, 4: 60.0}                 # RHMC_TUNE_HOP_STAGED candidates
-    upd_ns_per_byte = {5: 2.0, 10: 1.5, 11: 3.0}  # RHMC_TUNE_UPDATE_TENSOR candidates
+    hop_us = {3: 70.0, 4: 60.0}                  # RHMC_TUNE_HOP_STAGED candidates
+    gram_us = {0: 37.0, 1: 38.0, 2: 41.0, 3: 36.0}  # RHMC_TUNE_GRAM_TILE candidates
+    base_us = {0: 90.0, 1: 99.0, 2: 95.0, 3: 97.0}  # RHMC_TUNE_BASE_TILE candidates
     calls = []
     cur = {"ctx": ctx}  # the context being tuned
 
@@ -55,28 +56,30 @@ def test_autotune_picks_applies_and_caches(tmp_path, monkeypatch):
         solves = c.solves
         fn()
         calls.append(dict(c.tune))
-        if c.solves > solves:  # the update timing (a short solve ran)
-            v = c.tune[autotune.KEY_UPDATE]
-            return {"update_shifts_fp32": {"launches": 3, "ms": upd_ns_per_byte[v] * 1e-6 * 1e6, "bytes": 1e6}}
+        if c.solves > solves:  # a short solve ran: Gram and base-step timings
+            g, b = c.tune.get(autotune.KEY_GRAM_TILE, 0), c.tune.get(autotune.KEY_BASE_TILE, 0)
+            return {"gram_fp32": {"launches": 2, "ms": 2 * gram_us[g] * 1e-3, "bytes": 1e6},
+                    "update_shifts_fp32": {"launches": 2, "ms": 2 * base_us[b] * 1e-3, "bytes": 1e6}}
         m = c.tune[autotune.KEY_HOP]
         return {"hop_fp32": {"launches": 5, "ms": 5 * hop_us[m] * 1e-3, "bytes": 5e8}}
 
     monkeypatch.setattr(autotune.roofline, "profile", fake_profile)
     cache = str(tmp_path / "sub" / "tune.json")
+    want = {autotune.KEY_HOP: 4, autotune.KEY_GRAM_TILE: 3, autotune.KEY_BASE_TILE: 0}
     s = autotune.tune(ctx, 16, shifts=[0.1, 0.2], cache=cache)
-    assert s == {autotune.KEY_HOP: 4, autotune.KEY_UPDATE: 10}
-    assert ctx.tune[autotune.KEY_HOP] == 4 and ctx.tune[autotune.KEY_UPDATE] == 10
+    assert s == want
+    assert all(ctx.tune[k] == v for k, v in want.items())
     with open(cache) as f:
         db = json.load(f)
-    assert list(db.values()) == [{str(autotune.KEY_HOP): 4, str(autotune.KEY_UPDATE): 10}]
+    assert list(db.values()) == [{str(k): v for k, v in want.items()}]
     # a second call reads the cache: no timing, same settings applied to a new context
     n_calls = len(calls)
     ctx2 = FakeCtx()
     cur["ctx"] = ctx2
     assert autotune.tune(ctx2, 16, shifts=[0.1, 0.2], cache=cache) == s
-    assert len(calls) == n_calls and ctx2.tune == {autotune.KEY_HOP: 4, autotune.KEY_UPDATE: 10}
+    assert len(calls) == n_calls and ctx2.tune == want
     autotune.reset(ctx2)
-    assert ctx2.tune == {autotune.KEY_HOP: 0, autotune.KEY_UPDATE: 0}
+    assert ctx2.tune == {k: 0 for k in want}
     # odd width: the two-RHS-per-thread hop is not a candidate
     ctx3 = FakeCtx()
     cur["ctx"] = ctx3
