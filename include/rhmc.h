@@ -474,6 +474,8 @@ rhmc_status_t rhmc_profile_enable(int on);
  *                                 (1 .. 999; 0: built-in)
  *   RHMC_TUNE_PHASE1_MARGIN_MILLI the multishift phase runs to value/1000 x tol before the
  *                                 true-residual checks (1 .. 999; 0: built-in)
+ *   RHMC_TUNE_CORRECTION_CHECK_EVERY  iterations between the host checks of a defect
+ *                                 correction (a divisor of 6 uses captured graphs; 0: built-in 1)
  * Value 0 restores the built-in choice.  INVALID_ARG for an unknown key. */
 enum {
   RHMC_TUNE_HOP_RHS_PER_THREAD = 0,
@@ -499,7 +501,8 @@ enum {
   RHMC_TUNE_GRAM_TILE = 20,
   RHMC_TUNE_AXPY_ROWS = 21,
   RHMC_TUNE_CORRECTION_MARGIN_MILLI = 22,
-  RHMC_TUNE_PHASE1_MARGIN_MILLI = 23
+  RHMC_TUNE_PHASE1_MARGIN_MILLI = 23,
+  RHMC_TUNE_CORRECTION_CHECK_EVERY = 24
 };
 
 /* Self-test of the device-side timeout path used by kernels that wait on

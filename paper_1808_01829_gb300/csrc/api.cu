@@ -115,7 +115,9 @@ constexpr int kGraphCacheMax = 48;
 constexpr int kMaxRefine = 4;
 constexpr double kShiftFreezeMixed = 0.0;  // built-in freeze level of the shifted systems (mixed)
 constexpr int kRefineLanes = 4;       // concurrent defect corrections (built-in and most; 8 measured 2 % faster)
-constexpr int kCorrectionCheckEvery = 2;  // host checks of a defect-correction solve (divides kCheckEvery)
+// host checks of a defect-correction solve (divides kCheckEvery); measured at 24^4 with the
+// 0.9 margin: every 1, 2, 3 iterations took 223, 230, 240 correction iterations (95, 97, 100 ms)
+constexpr int kCorrectionCheckEvery = 1;
 // A defect correction stops when its recursive residual is kCorrectionMargin x tol / r of the
 // residual r it started from.  Its own FP32 drift is about 1e-6 of r (1e-3 of its target),
 // so the true residual after it lands within that margin of tol; a second round
@@ -929,7 +931,8 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
       // updates, and it is checked every kCorrectionCheckEvery iterations to stop closer
       // to its target
       pr.reliable = false;
-      pr.check_every = kCorrectionCheckEvery;
+      pr.check_every = tune_get(TUNE_CORRECTION_CHECK_EVERY) > 0 ? tune_get(TUNE_CORRECTION_CHECK_EVERY)
+                                                                 : kCorrectionCheckEvery;
       SolveStats st1;
       rhmc_status_t rr = prm.mixed ? solve_phase1<float>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls)
                                    : solve_phase1<double>(c, w.rb.Bref, n, 1, &shifts[q], w.rb.E, pr, b1, st1, ls);

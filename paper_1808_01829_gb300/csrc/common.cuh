@@ -132,6 +132,7 @@ enum TuneKey {
   TUNE_AXPY_ROWS,             // fused axpy + Gram at n = 16: 0 = 8-row tiles, 1 = 16-row tiles
   TUNE_CORRECTION_MARGIN_MILLI,  // defect corrections stop at this / 1000 x tol / r (0: built-in)
   TUNE_PHASE1_MARGIN_MILLI,   // the multishift phase runs to this / 1000 x tol (0: built-in)
+  TUNE_CORRECTION_CHECK_EVERY,  // iterations between host checks of a defect correction (0: built-in 1)
   TUNE_NKEYS
 };
 int tune_get(int key);
