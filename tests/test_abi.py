@@ -65,3 +65,44 @@ def test_python_constants_match_header():
     internal = re.findall(r"^\s*(TUNE_[A-Z0-9_]+)", body, re.M)
     header = sorted(((v, k) for k, v in enums.items() if k.startswith("RHMC_TUNE_")))
     assert [k[len("RHMC_"):] for _, k in header] == internal
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's sizes and field
+    offsets (compiled with gcc against include/rhmc.h; no GPU)."""
+    import shutil
+    import subprocess
+
+    from paper_1808_01829_gb300 import _lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {
+        "rhmc_lattice_t": (_lib.Lattice, ["dims", "mass", "bc_t"]),
+        "rhmc_info_t": (_lib.Info, ["iters", "dirac_calls", "reliable_updates", "refinements", "refine_iters",
+                                    "true_rel_resid_max", "phase1_rel_resid_max", "per_shift_resid", "phase1_ms",
+                                    "refine_ms"]),
+        "rhmc_rational_t": (_lib.Rational, ["n_shifts", "alpha0", "alpha", "beta"]),
+        "rhmc_md_params_t": (_lib.MdParams, ["beta", "tau", "n_steps", "n_gauge", "lambda", "tol_md", "max_iter",
+                                             "precision_md"]),
+        "rhmc_md_info_t": (_lib.MdInfo, ["force_evals", "gauge_force_evals", "solver_iters", "dirac_calls",
+                                         "max_rel_resid"]),
+        "rhmc_hmc_info_t": (_lib.HmcInfo, ["H_old", "H_new", "dH", "K", "S_g", "S_f", "accepted", "md"]),
+    }
+    lines = ['#include <stdio.h>', '#include "rhmc.h"', "int main(void) {"]
+    for cname, (_, fields) in checks.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+               if l)
+    for cname, (cls, fields) in checks.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, (pyname, _) in zip(fields, cls._fields_):
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, pyname).offset, (cname, f)
