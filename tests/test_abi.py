@@ -46,6 +46,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.rhmc_create(None, ctypes.byref(lat), 0) == 1
     assert lib.rhmc_workspace_bytes(None, 2, 4, 0) == 0
     assert lib.rhmc_destroy(None) == 0
+    # the trajectory calls reject a null context before touching the device
+    d = ctypes.c_double()
+    assert lib.rhmc_gauge_action(None, None, 5.12, ctypes.byref(d), None) == 1
+    assert lib.rhmc_kinetic_energy(None, None, ctypes.byref(d), None) == 1
+    assert lib.rhmc_momenta_from_normals(None, None, None, None) == 1
+    assert lib.rhmc_gauge_momentum(None, None, None, 5.12, 0.1, None) == 1
+    assert lib.rhmc_momentum_update(None, None, None, None, 0.1, None) == 1
+    assert lib.rhmc_link_update(None, None, None, 0.1, None) == 1
+    prm = _lib.MdParams(5.12, 1.0, 10, 3, 1.0 / 6, 1e-7, 0, 1)
+    assert lib.rhmc_md_evolve(None, None, None, None, 0, None, ctypes.byref(prm), None, None) == 1
+    assert lib.rhmc_hmc_trajectory(None, None, None, None, 0, None, None, None, ctypes.byref(prm), 1e-14, 0.5, None,
+                                   None, None) == 1
+    assert b"null context" in lib.rhmc_last_error()
 
 
 def test_python_constants_match_header():
