@@ -258,3 +258,25 @@ def test_pure_gauge_hmc_full_size():
     assert np.abs(W @ tr._dag(W) - np.eye(3)).max() <= 1e-13
     assert abs(rec["S_g"][1] - tr.gauge_action(U1, BETA)) <= 1e-12 * rec["S_g"][1]
     ctx.close()
+
+
+def test_hmc_trajectory_mixed_md_close_to_oracle():
+    """The bench's setting: force solves in mixed precision at 1e-9 (the MD is then an
+    approximation of the oracle's 1e-12 one at the level of the solves' tolerance) with the
+    heatbath and both actions in FP64 at 1e-13: H at the start agrees to 1e-11, dH to a
+    bound set by the force errors (1e-9 / 4m^2 relative over tau = 0.3)."""
+    need_gpu()
+    hmc = _hmc()
+    dims, mass, n_pf, tau = (4, 4, 4, 4), 0.1, 2, 0.3
+    ra_hb, ra = _rats(n_pf)
+    U = syn.random_links(dims, 0.5, 322)
+    p = syn.momentum_normals(dims, 323)
+    eta = syn.gaussian_pseudofermions(dims, n_pf, 324)
+    ctx = make_ctx(dims, mass, U)
+    prm = hmc.MdParams(beta=BETA, tau=tau, n_steps=2, n_gauge=2, tol_md=1e-9, precision="mixed")
+    rec = hmc.trajectory(ctx, to_gpu(U), to_gpu(p), to_gpu(eta), ra_hb, ra, ra, prm, tol_action=1e-13, u=0.0)
+    _, ro = tr.hmc_trajectory(dims, mass, U, p, eta, BETA, ra_hb, ra, ra, tau, 2, 2, 1.0 / 6, 1e-12, 1e-13, 0.0)
+    assert abs(rec["H_old"] - ro["H_old"]) <= 1e-11 * abs(ro["H_old"])
+    assert abs(rec["dH"] - ro["dH"]) <= 1e-4 * (1.0 + abs(ro["dH"]))
+    assert rec["md"]["max_rel_resid"] <= 1e-9 and rec["md"]["force_evals"] == 5
+    ctx.close()
