@@ -61,7 +61,8 @@ WORKLOAD = {
 # (profiles/); the per-launch traffic of the bench's launches is scaled from it
 # by the units processed.  A kernel changed since its capture has no entry.
 TRAFFIC_RATIO = {
-    "update_shifts_fp32": (0.960, "profiles/k_update_cols_16x16x16x32_n16.md (16^3x32, 15 shifts; scaled by bytes moved)"),
+    "update_shifts_fp32": (0.843, "profiles/k_base_step_24x24x24x24_n16.md (24^4, the fused base step; writes still in "
+                                  "L2 when the launch ends are not counted; scaled by bytes moved)"),
     "hop_fp32": (0.942, "profiles/k_hop_pf_traffic_24x24x24x24_n16.md (24^4, both hop kinds; scaled by bytes moved)"),
 }
 # SBCGrQ iterations of the bench workload (24^4, 16 x 16, tol 1e-8) measured with
