@@ -193,9 +193,10 @@ SMALL_CONFIGS = [
 def oracle_configs(reps=3):
     """The oracle's SBCGrQ (block) and per-vector multishift CG at the smaller
     configurations, FP64 on all host cores: whole solves with their iteration counts
-    (median of `reps`) at 4^4 and 8^4; at 16^3 x 32, where whole solves take minutes,
-    seconds per iteration from 8 fixed iterations of each (one right-hand side for the
-    per-vector solver)."""
+    (median of `reps`), the force, and both solves once more on one thread (the paper's
+    setting) at 4^4 and 8^4; at 16^3 x 32, where whole solves take minutes, seconds per
+    iteration from 8 fixed iterations of each (one right-hand side for the per-vector
+    solver)."""
     import numpy as np
 
     import oracle
@@ -213,7 +214,7 @@ def oracle_configs(reps=3):
             tb, tp = [], []
             for _ in range(reps):
                 t0 = time.perf_counter()
-                _, it_b, _ = oracle.sbcgrq(c["dims"], c["mass"], U, B, ra.beta, tol=c["tol"], max_iter=50000)
+                X, it_b, _ = oracle.sbcgrq(c["dims"], c["mass"], U, B, ra.beta, tol=c["tol"], max_iter=50000)
                 tb.append(time.perf_counter() - t0)
                 t0 = time.perf_counter()
                 it_p = 0
@@ -221,9 +222,27 @@ def oracle_configs(reps=3):
                     it_p += oracle.scg(c["dims"], c["mass"], U, np.ascontiguousarray(B[..., j]), ra.beta,
                                        tol=c["tol"], max_iter=50000)[1]
                 tp.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            oracle.force(c["dims"], U, X, ra.alpha)
+            t_f = time.perf_counter() - t0
+            # the paper's setting: one thread (one run each)
+            threads = oracle.max_threads()
+            oracle.set_threads(1)
+            try:
+                t0 = time.perf_counter()
+                oracle.sbcgrq(c["dims"], c["mass"], U, B, ra.beta, tol=c["tol"], max_iter=50000)
+                t1b = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                for j in range(c["n_pf"]):
+                    oracle.scg(c["dims"], c["mass"], U, np.ascontiguousarray(B[..., j]), ra.beta, tol=c["tol"],
+                               max_iter=50000)
+                t1p = time.perf_counter() - t0
+            finally:
+                oracle.set_threads(threads)
             rec.update({"sbcgrq_ms": statistics.median(tb) * 1e3, "sbcgrq_iters": it_b,
                         "pervector_scg_ms": statistics.median(tp) * 1e3, "pervector_scg_iters_total": it_p,
-                        "timing": f"median of {reps}"})
+                        "force_ms": t_f * 1e3, "timing": f"median of {reps}",
+                        "one_thread": {"sbcgrq_ms": t1b * 1e3, "pervector_scg_ms": t1p * 1e3}})
         else:
             k = 8
             t0 = time.perf_counter()
@@ -791,6 +810,26 @@ def run_gpu(args):
             cpu["parity_vs_oracle"] = oracle_parity(ctx, cfg, U, Phi, ra, G, ws)
         except Exception as e:  # never fails the line
             cpu["parity_vs_oracle"] = {"error": f"{type(e).__name__}: {e}"[:200]}
+        try:  # the oracle's per-vector multishift CG at the full workload: one iteration on one
+            # right-hand side, scaled by the per-vector iteration total of the GPU's FP64 baseline
+            import numpy as np
+
+            import oracle
+
+            if base is None:
+                raise RuntimeError("no per-vector baseline was run")
+            k = 4
+            t0 = time.perf_counter()
+            oracle.scg(cfg["dims"], cfg["mass"], U, np.ascontiguousarray(Phi[..., 0]), ra.beta, fixed_iters=k)
+            t_pv = (time.perf_counter() - t0) / k
+            pv_iters = base["iters_total"]
+            cpu["pervector_scg_estimate"] = {
+                "value": t_pv * pv_iters * 1e3, "unit": "ms",
+                "sample": f"{k} oracle SCG iterations on one right-hand side at the full workload ({t_pv:.3f} s "
+                          f"each), times {pv_iters} per-vector iterations (16 right-hand sides, the GPU baseline's "
+                          f"count), solve only"}
+        except Exception as e:  # never fails the line
+            cpu["pervector_scg_estimate"] = {"error": f"{type(e).__name__}: {e}"[:200]}
         try:  # the oracle's block and per-vector solvers at the smaller configurations
             cpu["oracle_configs"] = oracle_configs()
         except Exception as e:  # never fails the line
