@@ -297,12 +297,26 @@ static rhmc_status_t apply_A_df(const rhmc_ctx *c, const double2 *X, double2 *Y,
   return RHMC_OK;
 }
 
-// FP64-accurate operator for residuals of the mixed path: double-float unless
-// the native-FP64 tuning key is set.
-static rhmc_status_t apply_A_accurate(const rhmc_ctx *c, const double2 *X, double2 *Y, double2 *tmp,
-                                      double2 *split, int n, double sigma, cudaStream_t s) {
-  if (tune_get(TUNE_NATIVE_FP64_RESIDUALS)) return apply_A<double>(c, X, Y, tmp, n, sigma, s);
-  return apply_A_df(c, X, Y, tmp, split, n, sigma, s);
+// R = B - (A + sigma) X with FP64 accuracy for the mixed path; Rf (optional)
+// receives the FP32 rounding of R and npart (optional) the kParts x n column
+// partials of |R|^2.  Y, tmp, split: FP64-field-sized scratch; R may be split.
+// The double-float form subtracts the operator's (hi, lo) result directly.
+static rhmc_status_t residual_accurate(const rhmc_ctx *c, const double2 *B, const double2 *X, double2 *R,
+                                       float2 *Rf, double2 *Y, double2 *tmp, double2 *split, int n, double sigma,
+                                       double *npart, cudaStream_t s) {
+  const long rows = c->g.Vh * 3, len = rows * n;
+  if (tune_get(TUNE_NATIVE_FP64_RESIDUALS)) {
+    RHMC_TRY(apply_A<double>(c, X, Y, tmp, n, sigma, s));
+    RHMC_TRY(sub(B, Y, R, len, s));
+    if (Rf) RHMC_TRY((convert<double, float>(R, Rf, len, s)));
+    if (npart) RHMC_TRY(colnorm2<double>(R, rows, n, npart, kParts, s));
+    return RHMC_OK;
+  }
+  RHMC_TRY(df_split(X, (float4 *)split, len, s));
+  RHMC_TRY(hop_df(c->g, 1, c->ldf[1], (const float4 *)split, (float4 *)tmp, nullptr, 0.0, n, s));
+  RHMC_TRY(hop_df(c->g, 0, c->ldf[0], (const float4 *)tmp, (float4 *)Y, (const float4 *)split,
+                  4.0 * c->mass * c->mass + sigma, n, s));
+  return resid_df(B, (const float4 *)Y, R, Rf, rows, n, npart, kParts, s);
 }
 
 // ------------------------------------------------------------ solver workspace
@@ -435,10 +449,8 @@ struct SolveStats {
   int iters = 0, dirac = 0, reliable = 0;
 };
 
-// Column norms squared of an FP64 block (host result, n entries).
-static rhmc_status_t colnorms(rhmc_ctx *c, const double2 *A, int n, double *out, double *npart, cudaStream_t s) {
-  const long rows = c->g.Vh * 3;
-  RHMC_TRY(colnorm2<double>(A, rows, n, npart, kParts, s));
+// Host sums (fixed order) of the kParts x n column partials written on stream s.
+static rhmc_status_t read_colnorms(rhmc_ctx *c, const double *npart, int n, double *out, cudaStream_t s) {
   RHMC_TRY(ensure_pinned(c, sizeof(double) * kParts * kMaxN));
   RHMC_CUDA_TRY(cudaMemcpyAsync(lane(c).h_pin, npart, sizeof(double) * kParts * n, cudaMemcpyDeviceToHost, s));
   RHMC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -448,6 +460,12 @@ static rhmc_status_t colnorms(rhmc_ctx *c, const double2 *A, int n, double *out,
     out[j] = t;
   }
   return RHMC_OK;
+}
+
+// Column norms squared of an FP64 block (host result, n entries).
+static rhmc_status_t colnorms(rhmc_ctx *c, const double2 *A, int n, double *out, double *npart, cudaStream_t s) {
+  RHMC_TRY(colnorm2<double>(A, c->g.Vh * 3, n, npart, kParts, s));
+  return read_colnorms(c, npart, n, out, s);
 }
 
 struct StateView {
@@ -799,10 +817,8 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
     if (mixed && prm.reliable && (base < rel_delta * res_at_reliable || converged)) {
       // reliable update: flush FP32 increments, FP64 true base residual, re-QR
       for (int q = 0; q < nflush(); ++q) RHMC_TRY(flush(X + q * len, (float2 *)b.Xinc + q * len, len, s));
-      RHMC_TRY(apply_A_accurate(c, X, b.AP64, b.T64, b.R64, n, sigma0, s));
-      RHMC_TRY(sub(B, b.AP64, b.R64, len, s));
       // thin QR of the FP32-rounded true residual (Q is an FP32 basis)
-      RHMC_TRY((convert<double, float>(b.R64, (float2 *)b.W, len, s)));
+      RHMC_TRY(residual_accurate(c, B, X, b.R64, (float2 *)b.W, b.AP64, b.T64, b.R64, n, sigma0, nullptr, s));
       RHMC_TRY(gram<float>((float2 *)b.W, (float2 *)b.W, rows, n, b.gscratch, b.partial, s));
       RHMC_TRY(nxn_reliable<float>(b.partial, kGramParts, n, b.st, k, (float2 *)b.mw, s));
       // (the stored basis keeps the replaced block: P^(s)_k was formed from it, and the
@@ -900,14 +916,17 @@ static rhmc_status_t solve_all(rhmc_ctx *c, const double2 *B, int n, int ns, con
     double2 *Xq = X + q * len;
     SolveBufs &b1 = w.b1;
     for (int round = 0;; ++round) {
-      if (prm.mixed)
-        RHMC_TRY(apply_A_accurate(c, Xq, b1.AP64, b1.T64, b1.R64, n, shifts[q], ls));
-      else
-        RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], ls));
-      RHMC_TRY(sub(B, b1.AP64, w.rb.Bref, len, ls));
-      w.dirac++;
       double rn[kMaxN];
-      RHMC_TRY(colnorms(c, w.rb.Bref, n, rn, b1.npart, ls));
+      if (prm.mixed) {
+        RHMC_TRY(residual_accurate(c, B, Xq, w.rb.Bref, nullptr, b1.AP64, b1.T64, b1.R64, n, shifts[q], b1.npart,
+                                   ls));
+        RHMC_TRY(read_colnorms(c, b1.npart, n, rn, ls));
+      } else {
+        RHMC_TRY(apply_A<double>(c, Xq, b1.AP64, b1.T64, n, shifts[q], ls));
+        RHMC_TRY(sub(B, b1.AP64, w.rb.Bref, len, ls));
+        RHMC_TRY(colnorms(c, w.rb.Bref, n, rn, b1.npart, ls));
+      }
+      w.dirac++;
       double mx = 0.0, ratio_min = 1e300;
       for (int j = 0; j < n; ++j) {
         const double r = std::sqrt(rn[j]) / bn[j];

@@ -57,25 +57,23 @@ __device__ __forceinline__ DF df_norm(const DF &a) {
   return DF{h, __fsub_rn(a.e, __fsub_rn(h, a.h))};
 }
 
-// Split x into hi = RN_float(x) and lo = RN_float(x - hi) with integer
-// operations on the IEEE-754 bit patterns (FP64 conversions run at 1/64 of
-// the FP32 rate on this GPU).  x - hi is d 2^(e - 1075) exactly for the
-// integer d = (mantissa remainder below the float's 24 bits, minus 2^29 if
-// hi rounded up), |d| <= 2^28, so lo = RN(d) 2^(e - 1075).  Zeros,
-// subnormals and values whose hi or lo leaves the normal float range take
-// the FP64 conversion.
+// Split x into hi = RN_float(x) and lo = RN_float(x - hi) with 32-bit integer
+// operations on the two words of the IEEE-754 bit pattern (FP64 conversions run
+// at 1/64 of the FP32 rate on this GPU).  x - hi is d 2^(e - 1075) exactly for
+// the integer d = (mantissa remainder below the float's 24 bits, minus 2^29 if
+// hi rounded up), |d| <= 2^28, so lo = RN(d) 2^(e - 1075), the scaling exact
+// because 2^(e - 1075) is a normal float.  Zeros, subnormals and values whose
+// hi or lo leaves the normal float range take the FP64 conversion.
 __device__ __forceinline__ float2 df_split1(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const int e = (int)((hw >> 20) & 0x7ffu);
   // hi normal (e - 1023 in [-126, 127]) and lo normal (e - 1075 + 28 >= -126)
   if (e < 1023 - 126 + 52 || e > 1023 + 126) {
     const float h = (float)x;
     return make_float2(h, (float)(x - (double)h));
   }
-  const unsigned long long mant = b & ((1ull << 52) - 1);
-  const unsigned sign = (unsigned)(b >> 63);
-  unsigned m23 = (unsigned)(mant >> 29);
-  int rem = (int)(mant & ((1u << 29) - 1));
+  unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);  // leading 23 mantissa bits
+  int rem = (int)(lw & 0x1fffffffu);                   // the 29 bits below them
   int fe = e - 1023 + 127;
   if (rem > (1 << 28) || (rem == (1 << 28) && (m23 & 1u))) {  // round to nearest even
     rem -= 1 << 29;
@@ -84,10 +82,11 @@ __device__ __forceinline__ float2 df_split1(double x) {
       ++fe;
     }
   }
-  const float h = __uint_as_float((sign << 31) | ((unsigned)fe << 23) | m23);
-  float l = ldexpf(__int2float_rn(rem), e - 1075);
-  if (sign) l = -l;
-  return make_float2(h, l);
+  const unsigned sign = hw & 0x80000000u;
+  const float h = __uint_as_float(sign | ((unsigned)fe << 23) | m23);
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e - 1075), e >= 949
+  const float l = __int2float_rn(rem) * scale;
+  return make_float2(h, sign ? -l : l);
 }
 // hi + lo in FP64: the floats are widened by integer operations (exact), one FP64 add
 __device__ __forceinline__ double df_widen1(float f) {

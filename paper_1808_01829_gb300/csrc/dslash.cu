@@ -772,6 +772,70 @@ __global__ void k_df_merge(float4 *__restrict__ io, long len) {
   reinterpret_cast<double2 *>(io)[i] = make_double2(df_merge1(v.x, v.z), df_merge1(v.y, v.w));
 }
 
+// R = B - Y in FP64 for Y in double-float as the second hop writes it:
+// (B - hi) - lo, which needs no FP64 copy of Y.  Optionally Rf, the FP32
+// rounding of R, and per-CTA sums of |R|^2 per column (n interleaved
+// columns; partial[cta * n + column], CTA order fixed, so the host's sum of
+// the partials is deterministic).  Thread t owns column t % n of every
+// (256 / n)-th row; four rows are loaded before any is used.
+__global__ void __launch_bounds__(256) k_resid_df(const double2 *__restrict__ B, const float4 *__restrict__ Y,
+                                                  double2 *__restrict__ R, float2 *__restrict__ Rf, long rows,
+                                                  int n, double *__restrict__ partial) {
+  __shared__ double red[256];
+  const int t = threadIdx.x;
+  const int per = 256 / n;
+  const int c = t % n, g = t / n;
+  const long step = (long)gridDim.x * per;
+  double acc = 0.0;
+  if (g < per) {
+    long r = (long)blockIdx.x * per + g;
+    for (; r + 3 * step < rows; r += 4 * step) {
+      double2 b[4];
+      float4 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        b[u] = B[(r + u * step) * n + c];
+        y[u] = Y[(r + u * step) * n + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double x = (b[u].x - df_widen1(y[u].x)) - df_widen1(y[u].z);
+        const double z = (b[u].y - df_widen1(y[u].y)) - df_widen1(y[u].w);
+        const long i = (r + u * step) * n + c;
+        R[i] = make_double2(x, z);
+        if (Rf) Rf[i] = make_float2((float)x, (float)z);
+        acc += x * x + z * z;
+      }
+    }
+    for (; r < rows; r += step) {
+      const long i = r * n + c;
+      const double2 bv = B[i];
+      const float4 yv = Y[i];
+      const double x = (bv.x - df_widen1(yv.x)) - df_widen1(yv.z);
+      const double z = (bv.y - df_widen1(yv.y)) - df_widen1(yv.w);
+      R[i] = make_double2(x, z);
+      if (Rf) Rf[i] = make_float2((float)x, (float)z);
+      acc += x * x + z * z;
+    }
+  }
+  if (!partial) return;
+  red[t] = acc;
+  __syncthreads();
+  if (t < n) {
+    double sum = 0.0;
+    for (int q = 0; q < per; ++q) sum += red[q * n + t];
+    partial[(long)blockIdx.x * n + t] = sum;
+  }
+}
+
+rhmc_status_t resid_df(const double2 *B, const float4 *Y, double2 *R, float2 *Rf, long rows, int n,
+                       double *partial, int nparts, cudaStream_t s) {
+  if (n < 1 || n > RHMC_MAX_NRHS || nparts < 1) return RHMC_ERR_INVALID_ARG;
+  k_resid_df<<<nparts, 256, 0, s>>>(B, Y, R, Rf, rows, n, partial);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
+
 rhmc_status_t stage_links_df(const Geom &g, const double2 *l64, float4 *ldf, cudaStream_t s) {
   const long len = g.Vh * 72;
   k_df_convert<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(l64, ldf, len);

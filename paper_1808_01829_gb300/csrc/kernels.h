@@ -48,6 +48,10 @@ rhmc_status_t stage_links12(const Geom &g, int bc_t, float2 *const l32[2], float
 rhmc_status_t stage_links_df(const Geom &g, const double2 *l64, float4 *ldf, cudaStream_t s);
 rhmc_status_t df_split(const double2 *in, float4 *out, long len, cudaStream_t s);
 rhmc_status_t df_merge(float4 *io, long len, cudaStream_t s);
+// R = B - Y (Y in double-float, FP64 R), with the optional FP32 copy Rf and per-CTA
+// column sums of |R|^2 (partial: nparts x n; launched with nparts CTAs)
+rhmc_status_t resid_df(const double2 *B, const float4 *Y, double2 *R, float2 *Rf, long rows, int n,
+                       double *partial, int nparts, cudaStream_t s);
 rhmc_status_t hop_df(const Geom &g, int par, const float4 *links, const float4 *in, float4 *out, const float4 *self,
                      double a, int n, cudaStream_t s);
 

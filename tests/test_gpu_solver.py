@@ -193,6 +193,35 @@ def test_mixed_residuals_native_fp64_and_double_float_agree():
     ctx.close()
 
 
+@pytest.mark.parametrize("native", [0, 1])
+def test_mixed_reported_residuals_match_oracle(native):
+    """The per-shift true residuals the mixed solver reports (its FP64-accurate check of
+    the returned solutions: double-float operator and fused subtraction, or native FP64)
+    agree with the oracle's FP64 residuals of the same solutions."""
+    need_gpu()
+    from paper_1808_01829_gb300 import _lib
+
+    lib = _lib.load()
+    dims, mass, n = (8, 8, 8, 8), 0.05, 4
+    ra = rational_approx(-1.0 / 16, 2e-3, 64.0, 12)
+    U = syn.random_links(dims, 0.5, 1212)
+    B = syn.gaussian_pseudofermions(dims, n, 2212)
+    ctx = make_ctx(dims, mass, U)
+    try:
+        lib.rhmc_tune_set(5, native)
+        Xg, info = ctx.block_multishift_cg(to_gpu(B), ra.beta, 1e-9, precision="mixed")
+    finally:
+        lib.rhmc_tune_set(5, 0)
+    Xg = Xg.cpu().numpy()
+    bn = np.linalg.norm(B.reshape(-1, n), axis=0)
+    for s, sig in enumerate(ra.beta):
+        R = B - oracle.apply_A(dims, mass, U, Xg[s], sigma=sig)
+        ro = np.linalg.norm(R.reshape(-1, n), axis=0) / bn
+        rg = np.asarray(info.per_shift_resid[s])
+        assert np.all(np.abs(rg - ro) <= 1e-2 * ro + 1e-13), (s, rg, ro)
+    ctx.close()
+
+
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 4, 10)])
 def test_tensor_core_shift_update_matches_oracle(dims):
     """Mixed solve at n_pf = 16 with the shifted updates on tcgen05 (three-piece TF32 split): same
