@@ -116,26 +116,26 @@ __device__ __forceinline__ double to_d(dd a) { return df::df_merge1(a.h, a.l); }
 __device__ __forceinline__ double2 to_z(cd a) { return make_double2(to_d(a.r), to_d(a.i)); }
 __device__ __forceinline__ float2 to_f(cd a) { return make_float2(a.r.h, a.i.h); }
 
-__device__ __forceinline__ int tri_row(int e) {  // row a of a packed lower triangle
-  int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-  while ((a + 1) * (a + 2) / 2 <= e) ++a;
-  while (a * (a + 1) / 2 > e) --a;
-  return a;
-}
+constexpr int kNN = 256;  // shared matrix capacity (n <= 16)
+constexpr int kS = 16;    // row stride of the shared matrices of the base steps
 
-// LDL^dagger of the Hermitian part of the Gram matrix G (FP64, n x n) into A:
-// on return the strictly lower part of A holds L (unit lower), A[k][k].r the
-// pivot D_k, Li = L^-1 (unit lower) and rd[k] = 1 / D_k.  The work of step k
-// (trailing lower triangle and rows k+1.. of L^-1) is one list of items; the
-// item on the next diagonal entry forms the next pivot's reciprocal, so each
-// step takes one barrier.  Returns false (in all threads) if a pivot is not
+// LDL^dagger of the Hermitian part of the Gram matrix G (FP64, n x n, row-major)
+// in the stride-16 shared matrices, thread t owning entry (i, j) = (t / 16, t % 16)
+// (256 threads).  On return the strictly lower part of A holds L (unit lower),
+// A[k][k].r the pivot D_k, Li = L^-1 (unit lower) and rd[k] = 1 / D_k; h0 is the
+// thread's entry of the Hermitian part.  Step k updates the trailing lower triangle
+// (i >= j > k) and rows i > k of L^-1 (j <= k), one entry per thread on one code
+// path; the thread on the next diagonal entry forms the next pivot's reciprocal, so
+// each step takes one barrier.  Returns false (in all threads) if a pivot is not
 // positive and finite.
-__device__ bool ldl_dd(int n, const double2 *G, cd *A, cd *Li, dd *rd, int *flag) {
-  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
-  if (t < nn) {
-    const int i = t / n, j = t - (t / n) * n;
-    const cd a = from_z(G[t]), b = from_z(G[j * n + i]);
-    A[t] = (i == j) ? cd{a.r, dd{0.f, 0.f}} : cd{dhalf(dadd(a.r, b.r)), dhalf(dsub(a.i, b.i))};
+__device__ bool ldl16(int n, const double2 *G, cd *A, cd *Li, dd *rd, int *flag, cd &h0) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  const bool in = i < n && j < n;
+  h0 = czero_dd();
+  if (in) {
+    const cd a = from_z(G[i * n + j]), b = from_z(G[j * n + i]);
+    h0 = (i == j) ? cd{a.r, dd{0.f, 0.f}} : cd{dhalf(dadd(a.r, b.r)), dhalf(dsub(a.i, b.i))};
+    A[t] = h0;
     Li[t] = cd{dd{i == j ? 1.f : 0.f, 0.f}, dd{0.f, 0.f}};
   }
   __syncthreads();
@@ -147,52 +147,42 @@ __device__ bool ldl_dd(int n, const double2 *G, cd *A, cd *Li, dd *rd, int *flag
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
     if (*flag) return false;
-    const dd r = rd[k];
-    const int m = n - 1 - k;
-    const int ntri = m * (m + 1) / 2, nli = m * (k + 1);
-    for (int e = t; e < ntri + nli; e += nt) {
-      if (e < ntri) {
-        // A[i][j] -= (A[i][k] / D_k) conj(A[j][k]),  i >= j > k
-        const int a = tri_row(e), b = e - a * (a + 1) / 2;
-        const int i = k + 1 + a, j = k + 1 + b;
-        const cd lik = cscale(A[i * n + k], dneg(r));
-        acc_t v = acc_from(A[i * n + j]);
-        acc_mac(v, lik, cconj(A[j * n + k]));
-        const cd w = acc_get(v);
-        A[i * n + j] = w;
-        if (i == k + 1 && j == k + 1) {
-          *flag = !dpos(w.r);
-          rd[k + 1] = drcp(dpos(w.r) ? w.r : dd{1.f, 0.f});
-        }
-      } else {
-        // Li[i][j] -= (A[i][k] / D_k) Li[k][j],  i > k >= j
-        const int e2 = e - ntri;
-        const int a = e2 / (k + 1), j = e2 - a * (k + 1);
-        const int i = k + 1 + a;
-        const cd lik = cscale(A[i * n + k], dneg(r));
-        acc_t v = acc_from(Li[i * n + j]);
-        acc_mac(v, lik, Li[k * n + j]);
-        Li[i * n + j] = acc_get(v);
+    // A[i][j] -= (A[i][k] / D_k) conj(A[j][k])  (i >= j > k)
+    // Li[i][j] -= (A[i][k] / D_k) Li[k][j]      (i > k >= j)
+    const bool upd_a = j > k && i >= j;
+    if (in && i > k && (upd_a || j <= k)) {
+      const cd lik = cscale(A[i * kS + k], dneg(rd[k]));
+      cd *X = upd_a ? A : Li;
+      const cd y = upd_a ? cconj(A[j * kS + k]) : Li[k * kS + j];
+      acc_t v = acc_from(X[t]);
+      acc_mac(v, lik, y);
+      const cd w = acc_get(v);
+      X[t] = w;
+      if (i == k + 1 && j == k + 1) {
+        *flag = !dpos(w.r);
+        rd[k + 1] = drcp(dpos(w.r) ? w.r : dd{1.f, 0.f});
       }
     }
     __syncthreads();
   }
   if (*flag) return false;
-  for (int e = t; e < nn; e += nt) {
-    const int i = e / n, j = e - (e / n) * n;
-    if (i > j) A[e] = cscale(A[e], rd[j]);
-  }
+  if (in && i > j) A[t] = cscale(A[t], rd[j]);
   __syncthreads();
   return true;
 }
 
-// ||M e_j|| * scale[j] of an upper-triangular M (16 lanes per column)
-__device__ void colnorms_upper_dd(int n, const cd *M, double *out, const double *scale) {
+// the value of the sum of two running sums (kept apart as independent dependency chains)
+__device__ __forceinline__ cd acc_join(const acc_t &a, const acc_t &b) {
+  return acc_get(acc_t{df::df_add(a.r, b.r), df::df_add(a.i, b.i)});
+}
+
+// ||M e_j|| * scale[j] of an upper-triangular M (stride ld; 16 lanes per column)
+__device__ void colnorms_upper_dd(int n, const cd *M, int ld, double *out, const double *scale) {
   const int t = threadIdx.x;
   const int j = t >> 4, i = t & 15;
   df::DF s{0.f, 0.f};
   if (j < n && i <= j) {
-    const cd z = M[i * n + j];
+    const cd z = M[i * ld + j];
     df::df_add_prod(s, z.r.h, z.r.l, z.r.h, z.r.l);
     df::df_add_prod(s, z.i.h, z.i.l, z.i.h, z.i.l);
   }
@@ -209,7 +199,6 @@ __device__ void colnorms_upper_dd(int n, const cd *M, double *out, const double 
   }
 }
 
-constexpr int kNN = 256;  // shared matrix capacity (n <= 16)
 
 // Out = op(A) op(B), one element per thread (t < n^2); ca / cb: adjoint of A / B.
 // Out may not alias A or B.  Ends with a barrier.
@@ -313,32 +302,33 @@ __device__ bool inv_general_dd(int n, cd *Ai, cd *A, int *piv, int *flag) {
 
 // line 4: alpha_k = Gram1^-1 (Hermitian part of Gram1 = P^dagger (A + sigma_0) P)
 // = L^-dagger D^-1 L^-1; FP64 alpha_k and Gram1_k into the state, -alpha_k (FP32)
-// for line 5
+// for line 5.  Thread t owns entry (t / 16, t % 16) throughout.
 __global__ void __launch_bounds__(256) k_nxn_alpha_dd(const double2 *G, int n, SolverState *st, int k,
                                                       float2 *mw_out) {
   __shared__ cd A[kNN], Li[kNN], S[kNN];
   __shared__ dd rd[kMaxN];
   __shared__ int flag;
   const int cur = k % kSlots;
-  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
+  const int t = threadIdx.x, i = t >> 4, j = t & 15;
+  const bool in = i < n && j < n;
   if (t == 0) st->kabs[cur] = st->kabs[(k - 1) % kSlots] + 1;
-  if (t < nn) {  // Gram1_k (Hermitian part) for the shifted step
-    const int i = t / n, j = t - (t / n) * n;
-    const double2 a = G[t], b = G[j * n + i];
-    st->G1[cur][t] = (i == j) ? make_double2(a.x, 0.0) : make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-  }
-  if (!ldl_dd(n, G, A, Li, rd, &flag)) {
+  cd h0;
+  if (!ldl16(n, G, A, Li, rd, &flag, h0)) {
     if (t == 0) st->breakdown = 2;
     return;
   }
-  for (int e = t; e < nn; e += nt) S[e] = cscale(Li[e], rd[e / n]);  // S[q][j] = Li[q][j] / D_q
+  if (in) S[t] = cscale(Li[t], rd[i]);  // S[q][j] = Li[q][j] / D_q
   __syncthreads();
-  // alpha[i][j] = sum_{q >= j} conj(Li[q][i]) S[q][j], i <= j (column-major packing)
-  for (int e = t; e < n * (n + 1) / 2; e += nt) {
-    const int j = tri_row(e), i = e - j * (j + 1) / 2;
-    acc_t acc = acc_zero();
-    for (int q = j; q < n; ++q) acc_mac_cj(acc, Li[q * n + i], S[q * n + j]);
-    const cd v = acc_get(acc);
+  // alpha[i][j] = sum_{q >= j} conj(Li[q][i]) S[q][j], i <= j (two running sums)
+  if (in && i <= j) {
+    acc_t a0 = acc_zero(), a1 = acc_zero();
+    int q = j;
+    for (; q + 1 < n; q += 2) {
+      acc_mac_cj(a0, Li[q * kS + i], S[q * kS + j]);
+      acc_mac_cj(a1, Li[(q + 1) * kS + i], S[(q + 1) * kS + j]);
+    }
+    if (q < n) acc_mac_cj(a0, Li[q * kS + i], S[q * kS + j]);
+    const cd v = acc_join(a0, a1);
     const double2 vz = to_z(v);
     const float2 vf = to_f(v);
     st->alpha[cur][i * n + j] = vz;
@@ -348,74 +338,78 @@ __global__ void __launch_bounds__(256) k_nxn_alpha_dd(const double2 *G, int n, S
       mw_out[j * n + i] = make_float2(-vf.x, vf.y);
     }
   }
+  if (in) st->G1[cur][i * n + j] = to_z(h0);  // Gram1_k (Hermitian part) for the shifted step
 }
 
 // lines 5-8: rho_k = R = D^1/2 L^dagger of the LDL^dagger of W^dagger W (thin QR);
 // coef = [rho_k^-1, M1 = alpha_k delta_{k-1}, rho_k^dagger] (FP32); FP64 rho_k,
-// delta_k = rho_k delta_{k-1} and the base column residuals into the state
+// delta_k = rho_k delta_{k-1} and the base column residuals into the state.
+// Thread t owns entry (t / 16, t % 16) throughout.
 __global__ void __launch_bounds__(256) k_nxn_rho_dd(const double2 *G, int n, SolverState *st, int k, float2 *coef) {
-  __shared__ cd A[kNN], Li[kNN], R[kNN], Dp[kNN];
+  __shared__ cd A[kNN], Li[kNN], Al[kNN], Dp[kNN];
   __shared__ dd rd[kMaxN], sd[kMaxN], rsd[kMaxN];
   __shared__ int flag;
   const int cur = k % kSlots, prev = (k - 1) % kSlots;
-  const int t = threadIdx.x, nt = blockDim.x, nn = n * n;
-  if (!ldl_dd(n, G, A, Li, rd, &flag)) {
+  const int t = threadIdx.x, i = t >> 4, j = t & 15, nn = n * n;
+  const bool in = i < n && j < n;
+  // alpha_k and delta_{k-1} do not depend on the factorisation (ldl16's barriers publish them)
+  if (in) {
+    Al[t] = from_z(st->alpha[cur][i * n + j]);
+    Dp[t] = from_z(st->delta[prev][i * n + j]);
+  }
+  cd h0;
+  if (!ldl16(n, G, A, Li, rd, &flag, h0)) {
     if (t == 0) st->breakdown = 3;
     return;
   }
   if (t < n) {
-    const dd d = A[t * n + t].r;
+    const dd d = A[t * kS + t].r;
     const dd y = drsqrt(d);
     rsd[t] = y;
     sd[t] = dmul(d, y);
   }
-  if (t < nn) Dp[t] = from_z(st->delta[prev][t]);
   __syncthreads();
-  // R = D^1/2 L^dagger (upper) and R^-1 = L^-dagger D^-1/2 (upper)
-  for (int e = t; e < nn; e += nt) {
-    const int i = e / n, j = e - (e / n) * n;
+  cd dk = czero_dd();
+  if (in) {
+    // R = D^1/2 L^dagger (upper) and R^-1 = L^-dagger D^-1/2 (upper)
     cd r = czero_dd(), ri = czero_dd();
     if (i == j) {
       r.r = sd[i];
       ri.r = rsd[i];
     } else if (i < j) {
-      r = cscale(cconj(A[j * n + i]), sd[i]);
-      ri = cscale(cconj(Li[j * n + i]), rsd[j]);
+      r = cscale(cconj(A[j * kS + i]), sd[i]);
+      ri = cscale(cconj(Li[j * kS + i]), rsd[j]);
     }
-    R[e] = r;
-    st->rho[cur][e] = to_z(r);
-    coef[e] = to_f(ri);
-  }
-  __syncthreads();
-  // A and Li are free now: alpha_k (FP64 state) into A, delta_k into Li below
-  cd *Al = A, *Dk = Li;
-  if (t < nn) {
-    const int i = t / n, j = t - (t / n) * n;
-    coef[2 * nn + t] = to_f(cconj(R[j * n + i]));  // rho^dagger
-    Al[t] = from_z(st->alpha[cur][t]);
-  }
-  __syncthreads();
-  // M1[i][j] = sum_{q <= j} alpha[i][q] delta[q][j];
-  // delta_k[i][j] = sum_{i <= q <= j} rho[i][q] delta[q][j] (upper)
-  for (int e = t; e < nn + n * (n + 1) / 2; e += nt) {
-    if (e < nn) {
-      const int j = e / n, i = e - (e / n) * n;
-      acc_t acc = acc_zero();
-      for (int q = 0; q <= j; ++q) acc_mac(acc, Al[i * n + q], Dp[q * n + j]);
-      coef[nn + i * n + j] = to_f(acc_get(acc));
-    } else {
-      const int e2 = e - nn;
-      const int j = tri_row(e2), i = e2 - j * (j + 1) / 2;
-      acc_t acc = acc_zero();
-      for (int q = i; q <= j; ++q) acc_mac(acc, R[i * n + q], Dp[q * n + j]);
-      const cd v = acc_get(acc);
-      Dk[i * n + j] = v;
-      if (i != j) Dk[j * n + i] = czero_dd();
+    st->rho[cur][i * n + j] = to_z(r);
+    coef[i * n + j] = to_f(ri);
+    coef[2 * nn + j * n + i] = to_f(cconj(r));  // rho^dagger
+    // M1[i][j] = sum_{q <= j} alpha[i][q] delta_{k-1}[q][j] (delta_{k-1} upper)
+    acc_t m0 = acc_zero(), m1 = acc_zero();
+    int q = 0;
+    for (; q + 1 <= j; q += 2) {
+      acc_mac(m0, Al[i * kS + q], Dp[q * kS + j]);
+      acc_mac(m1, Al[i * kS + q + 1], Dp[(q + 1) * kS + j]);
     }
+    if (q <= j) acc_mac(m0, Al[i * kS + q], Dp[q * kS + j]);
+    coef[nn + i * n + j] = to_f(acc_join(m0, m1));
+    // delta_k[i][j] = sum_{i <= q <= j} R[i][q] delta_{k-1}[q][j]
+    //              = sd[i] (delta_{k-1}[i][j] + sum_{i < q <= j} conj(L[q][i]) delta_{k-1}[q][j])
+    if (i <= j) {
+      acc_t d0 = acc_from(Dp[i * kS + j]), d1 = acc_zero();
+      q = i + 1;
+      for (; q + 1 <= j; q += 2) {
+        acc_mac_cj(d0, A[q * kS + i], Dp[q * kS + j]);
+        acc_mac_cj(d1, A[(q + 1) * kS + i], Dp[(q + 1) * kS + j]);
+      }
+      if (q <= j) acc_mac_cj(d0, A[q * kS + i], Dp[q * kS + j]);
+      dk = cscale(acc_join(d0, d1), sd[i]);
+    }
+    st->delta[cur][i * n + j] = to_z(dk);
   }
+  __syncthreads();  // A, Li, Al are read above: reuse Li for delta_k
+  Li[t] = dk;
   __syncthreads();
-  if (t < nn) st->delta[cur][t] = to_z(Dk[t]);
-  colnorms_upper_dd(n, Dk, st->res[0], st->inv_d0);
+  colnorms_upper_dd(n, Li, kS, st->res[0], st->inv_d0);
   if (t == 0) st->upd[0] = 1;
 }
 
