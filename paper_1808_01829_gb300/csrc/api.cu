@@ -1713,8 +1713,10 @@ rhmc_status_t rhmc_force(rhmc_ctx_t *c, const void *Phi, int n, double alpha0, c
     const rhmc_status_t rc = block_solve_entry(c, (const double2 *)Phi, n, ns, beta, X, tol, max_iter,
                                                p == RHMC_MIXED_FP32, 0, rest, info, s);
     if (rc != RHMC_OK) return rc;
-  } else if (info) {
-    std::memset(info, 0, sizeof(*info) - sizeof(double *));
+  } else if (info) {  // no solve: every field zero except the caller's array pointer
+    double *user = info->per_shift_resid;
+    std::memset(info, 0, sizeof(*info));
+    info->per_shift_resid = user;
   }
   // Y^(s) = D_oe X^(s), then the outer-product sum; FP64-accurate in
   // double-float arithmetic on the FP32 units (native FP64 with

@@ -9,6 +9,7 @@ force from the GPU's own X matches to 1e-12 (kernel-level parity); the full
 GPU force matches the oracle's within the solution-error bound."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from gpu_util import check_solution, colrel, make_ctx, need_gpu, to_gpu
@@ -140,6 +141,36 @@ def test_force_kernel_parity_from_given_solutions():
     G, _, _ = ctx.force(to_gpu(X[0]), 0.5, alpha, [0.1, 0.2, 0.3], 1e-8, X=to_gpu(X))
     Go = oracle.force(dims, U, X, alpha)
     assert np.linalg.norm(G.cpu().numpy() - Go) <= 1e-12 * np.linalg.norm(Go)
+    ctx.close()
+
+
+def test_force_given_solutions_resets_info():
+    """With the solutions supplied (no solve) rhmc_force zeroes every info field except the
+    caller's per_shift_resid pointer, which it leaves in place."""
+    need_gpu()
+    import ctypes
+
+    from paper_1808_01829_gb300 import _lib
+    from paper_1808_01829_gb300.api import PRECISION, _doubles, _ptr, _stream
+
+    dims, ns, n = (4, 4, 4, 4), 2, 3
+    U = syn.random_links(dims, 0.5, 1206)
+    X = to_gpu(np.stack([syn.gaussian_pseudofermions(dims, n, 2206 + s) for s in range(ns)]))
+    ctx = make_ctx(dims, 0.1, U)
+    G = torch.empty((ctx.V, 4, 3, 3), dtype=torch.complex128, device=X.device)
+    buf = (ctypes.c_double * (ns * n))(*([-1.0] * (ns * n)))
+    info = _lib.Info()
+    info.iters, info.phase1_ms, info.refine_ms = 7, 2.0, 3.5
+    info.per_shift_resid = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
+    S = ctypes.c_double(0.0)
+    rc = ctx.lib.rhmc_force(ctx._h, _ptr(X[0]), n, 0.5, _doubles([0.3, 1.1]), _doubles([0.1, 0.2]), ns, 1e-8, 0,
+                            PRECISION["mixed"], _ptr(X), _ptr(G), ctypes.byref(S), None, ctypes.byref(info),
+                            _stream(X))
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert ctypes.cast(info.per_shift_resid, ctypes.c_void_p).value == ctypes.addressof(buf)
+    assert (info.iters, info.phase1_ms, info.refine_ms) == (0, 0.0, 0.0)
+    assert list(buf) == [-1.0] * (ns * n)
     ctx.close()
 
 
