@@ -1,15 +1,18 @@
 #!/usr/bin/env python3
 """Benchmark: time per pseudofermion-force evaluation at 24^4, n_pf = 16.
 
-One step = one full force evaluation through the C ABI (rhmc_force): the
-block multishift solve SBCGrQ (Algorithm 1) of (A + beta_s) X^(s) = Phi for
-all 16 pseudofermions and all 16 shifts to a true relative residual of 1e-8
-(mixed precision: FP32 operator and block updates in an FP64 reliable-update
-/ defect-correction loop), then the force G of Eq. (force) in FP64.
-Phi and U are resident on the device when the timed region starts.
+One step = one full force evaluation through the C ABI: the staging of the
+resident FP64 links into the operator's FP32 and double-float records
+(rhmc_set_gauge), then rhmc_force: the block multishift solve SBCGrQ
+(Algorithm 1) of (A + beta_s) X^(s) = Phi for all 16 pseudofermions and all 16
+shifts to a true relative residual of 1e-8 (mixed precision: FP32 operator and
+block updates in an FP64 reliable-update / defect-correction loop), then the
+force G of Eq. (force) in FP64.  Phi and U are resident on the device when the
+timed region starts.
 
 Also reported on the same line:
-* e2e: the same step with host (pinned) buffers, copies inside the timed region;
+* e2e: the same step from host (pinned) U and Phi to G in host memory, copies
+  inside the timed region;
 * roofline: the multi-RHS FP32 hop at 24^4, n = 16 against the measured HBM peak;
 * baseline_fp64_scg: plain per-vector FP64 multishift CG + the same force on
   this GPU (the comparison of the metric), median of 3 after a warm-up;
@@ -656,6 +659,9 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
+        # one force evaluation: FP32 (and double-float) link staging from the resident FP64
+        # links, the solve, the force
+        ctx.set_gauge(Ud)
         return ctx.force(Pd, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], precision=cfg["precision"], out=G,
                          workspace=ws)
 
@@ -681,16 +687,20 @@ def run_gpu(args):
     ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     last = infos[-1]
 
-    # ---- end to end: pinned host Phi -> device, force, G -> pinned host
+    # ---- end to end: pinned host U and Phi -> device, staging, force, G -> pinned host
+    Uh = torch.from_numpy(U).pin_memory()
     Ph = torch.from_numpy(Phi).pin_memory()
     Gh = torch.empty((ctx.V, 4, 3, 3), dtype=torch.complex128).pin_memory()
+    Ud2 = torch.empty_like(Ud)
     Pd2 = torch.empty_like(Pd)
     e2e = []
     for it in range(max(2, min(3, args.steps)) + 1):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
+        Ud2.copy_(Uh, non_blocking=True)
         Pd2.copy_(Ph, non_blocking=True)
+        ctx.set_gauge(Ud2)
         ctx.force(Pd2, ra.alpha0, ra.alpha, ra.beta, cfg["tol"], precision=cfg["precision"], out=G, workspace=ws)
         Gh.copy_(G, non_blocking=True)
         b.record(stream)
@@ -842,13 +852,14 @@ def run_gpu(args):
             cpu["one_thread"] = {"error": f"{type(e).__name__}: {e}"[:200]}
 
     if rank == 0:
-        len_b = Phi.nbytes
+        len_b = Phi.nbytes + U.nbytes
         line = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "force_evals_per_s": world * 1000.0 / ms,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": cfg["workload"], "precision": cfg["precision"],
+                       "step": "link staging (FP64 links resident) + solve to tol for every (shift, column) + force",
                        "l2": "inputs larger than L2 (U 191 MB, fields 64-127 MB each)",
                        "parallelism": f"replicas x{world}", **({"tune": args.tune} if args.tune else {})},
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": len_b, "d2h_bytes_per_step": G.numel() * 16},

@@ -533,6 +533,21 @@ rhmc_status_t rhmc_probe_alu_peaks(int device, double *fp32_tflops, double *fp32
  * count < 1. */
 rhmc_status_t rhmc_selftest_fp64_helpers(const double *x_dev, int count, double *out_dev, rhmc_stream_t s);
 
+/* Self-test of the double-float arithmetic (no counterpart in the paper): a
+ * value is an unevaluated pair of floats hi + lo; products by an FMA-based
+ * TwoProduct (Ogita, Rump and Oishi 2005), sums by TwoSum (Knuth).  The mixed
+ * solve's FP64-accurate residuals and force, and its base n x n steps, run on
+ * it.  For the `count` pairs a = x_dev[k], b = y_dev[k] (device doubles; the
+ * stated accuracy holds for magnitudes within 2^-30 .. 2^30, where the low parts
+ * and the products' rounding errors stay normal floats), writes
+ * out_dev[q * count + k] (device, 8 * count doubles) = q = 0: hi of
+ * a's split (RN_float(a)), 1: lo (RN_float(a - hi)), 2: hi + lo, 3: a + b,
+ * 4: a b, 5: 1 / a, 6: 1 / sqrt(a) for a > 0 (else 0), 7: a b + b b as a
+ * running sum of two products; 2-7 in double-float, returned in FP64.
+ * Asynchronous on stream s.  INVALID_ARG for null pointers or count < 1. */
+rhmc_status_t rhmc_selftest_df_helpers(const double *x_dev, const double *y_dev, int count, double *out_dev,
+                                       rhmc_stream_t s);
+
 /* The same settings for one context only (they take precedence over the
  * process-wide ones in every call on ctx, including the concurrent solves of
  * rhmc_block_multishift_cg_batch, so each ensemble can run its own tuned

@@ -138,6 +138,8 @@ def load():
         lib.rhmc_selftest_bounded_wait.restype = I
         lib.rhmc_selftest_fp64_helpers.argtypes = [P, I, P, P]
         lib.rhmc_selftest_fp64_helpers.restype = I
+        lib.rhmc_selftest_df_helpers.argtypes = [P, P, I, P, P]
+        lib.rhmc_selftest_df_helpers.restype = I
         lib.rhmc_probe_alu_peaks.argtypes = [I, PD, PD, PD, P]
         lib.rhmc_probe_alu_peaks.restype = I
         lib.rhmc_ctx_tune_set.argtypes = [P, I, I]
@@ -200,7 +202,7 @@ def exported_symbols():
         "rhmc_profile_enable", "rhmc_profile_read", "rhmc_tune_set", "rhmc_tune_get",
         "rhmc_apply_mdagm_mrhs_noalloc", "rhmc_rational_apply", "rhmc_block_multishift_cg_batch", "rhmc_ctx_tune_set", "rhmc_ctx_tune_get",
         "rhmc_rational_solve", "rhmc_rational_solve_bytes", "rhmc_selftest_bounded_wait", "rhmc_force_lie",
-        "rhmc_probe_alu_peaks", "rhmc_profile_read_flops", "rhmc_selftest_fp64_helpers",
+        "rhmc_probe_alu_peaks", "rhmc_profile_read_flops", "rhmc_selftest_fp64_helpers", "rhmc_selftest_df_helpers",
         "rhmc_gauge_action", "rhmc_kinetic_energy", "rhmc_momenta_from_normals", "rhmc_gauge_momentum",
         "rhmc_momentum_update", "rhmc_link_update", "rhmc_md_evolve", "rhmc_hmc_trajectory",
     ]

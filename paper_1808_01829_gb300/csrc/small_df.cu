@@ -529,4 +529,38 @@ rhmc_status_t nxn_rho_dd(const double2 *gram, int n, SolverState *st, int k, flo
   return RHMC_OK;
 }
 
+// ------------------------------------------------------------ self-test of the double-float helpers
+__global__ void k_df_helpers(const double *__restrict__ x, const double *__restrict__ y, int count,
+                             double *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const double a = x[k], b = y[k];
+  const dd da = from_d(a), db = from_d(b);
+  const size_t c = (size_t)count;
+  out[0 * c + k] = (double)da.h;  // the split: hi = RN_float(a)
+  out[1 * c + k] = (double)da.l;  //            lo = RN_float(a - hi)
+  out[2 * c + k] = to_d(da);      // hi + lo in FP64
+  out[3 * c + k] = to_d(dadd(da, db));
+  out[4 * c + k] = to_d(dmul(da, db));
+  out[5 * c + k] = to_d(drcp(da));
+  out[6 * c + k] = a > 0.0 ? to_d(drsqrt(da)) : 0.0;
+  df::DF acc{0.f, 0.f};  // running sum of products, as the double-float hop and force form them
+  df::df_add_prod(acc, da.h, da.l, db.h, db.l);
+  df::df_add_prod(acc, db.h, db.l, db.h, db.l);
+  const df::DF an = df::df_norm(acc);
+  out[7 * c + k] = to_d(dd{an.h, an.e});
+}
+
 }  // namespace rhmc
+
+extern "C" rhmc_status_t rhmc_selftest_df_helpers(const double *x_dev, const double *y_dev, int count,
+                                                  double *out_dev, rhmc_stream_t sv) {
+  using namespace rhmc;
+  if (!x_dev || !y_dev || !out_dev || count < 1) {
+    set_error("rhmc_selftest_df_helpers: null pointer or count < 1");
+    return RHMC_ERR_INVALID_ARG;
+  }
+  k_df_helpers<<<(count + 255) / 256, 256, 0, (cudaStream_t)sv>>>(x_dev, y_dev, count, out_dev);
+  RHMC_LAUNCH_CHECK();
+  return RHMC_OK;
+}
