@@ -419,14 +419,14 @@ int orc_sbcgrq(const int *dims, double mass, int bc_t, const double *Uv, const d
   const long rows = l.Vh * 3, len = rows * n;
   const double s0 = shifts[0];
   std::vector<cd> Q(len), P(len * nshift), AP(len), W(len), tmp;
-  // line 2: X = 0, {Q_0, delta_0} = qr(B), P^(s) = Q_0
+  // initialisation: X = 0, {Q_0, delta_0} = qr(B), P^(s) = Q_0
   std::fill(X, X + len * nshift, cd(0.0));
   Mat delta;
   if (!thin_qr(B, Q.data(), delta, rows, n)) return 3;
   for (int s = 0; s < nshift; ++s) std::copy(Q.begin(), Q.end(), P.begin() + s * len);
   std::vector<double> d0(n);
   for (int j = 0; j < n; ++j) d0[j] = colnorm(delta, n, j);
-  // line 3: rho_0 = delta_0, alpha_0 = alpha^(s)_0 = beta^(s)_0 = 1
+  // initial coefficients: rho_0 = delta_0, alpha_0 = alpha^(s)_0 = beta^(s)_0 = 1
   Mat rho = delta, alpha = eye(n);
   std::vector<Mat> alpha_s(nshift, eye(n)), beta_s(nshift, eye(n));
   std::vector<char> active(nshift, 1);
@@ -436,23 +436,23 @@ int orc_sbcgrq(const int *dims, double mass, int bc_t, const double *Uv, const d
   while (k < kmax) {
     ++k;
     cd *P0 = P.data();
-    // line 4: alpha_k = (P^dagger (A + sigma_0) P)^-1
+    // alpha_k = (P^dagger (A + sigma_0) P)^-1
     apply_A(l, U, P0, AP.data(), n, s0, tmp);
     bool ok;
     Mat alpha_k = inv(gram(P0, AP.data(), rows, n), n, ok);
     if (!ok) { status = 3; break; }
-    // line 5: {Q_k, rho_k} = qr(Q_{k-1} - (A + sigma_0) P alpha_k)
+    // block QR: {Q_k, rho_k} = qr(Q_{k-1} - (A + sigma_0) P alpha_k)
     block_axpy(W.data(), Q.data(), -1.0, AP.data(), alpha_k, rows, n);
     Mat rho_k;
     if (!thin_qr(W.data(), Q.data(), rho_k, rows, n)) { status = 3; break; }
-    // line 6: X^(0) += P alpha_k delta_{k-1}
+    // base solution: X^(0) += P alpha_k delta_{k-1}
     block_axpy(X, X, 1.0, P0, mul(alpha_k, delta, n), rows, n);
-    // line 7: P^(0) = Q_k + P rho_k^dagger
+    // base search block: P^(0) = Q_k + P rho_k^dagger
     block_axpy(P0, nullptr, 1.0, P0, adj(rho_k, n), rows, n);  // P0 <- P0 rho^dag (row-wise, in place safe)
     for (long q = 0; q < len; ++q) P0[q] += Q[q];
-    // line 8: delta_k = rho_k delta_{k-1}
+    // residual factor: delta_k = rho_k delta_{k-1}
     Mat delta_k = mul(rho_k, delta, n);
-    // lines 9-12 for every shifted system
+    // the shifted systems
     Mat coupling = mul(mul(alpha_k, rho, n), (inv(alpha, n, ok)), n);  // alpha_k rho_{k-1} alpha_{k-1}^-1
     if (!ok) { status = 3; break; }
     bool all_done = true;
@@ -460,18 +460,18 @@ int orc_sbcgrq(const int *dims, double mass, int bc_t, const double *Uv, const d
     for (int j = 0; j < n; ++j) base_res = std::max(base_res, colnorm(delta_k, n, j) / d0[j]);
     for (int s = 1; s < nshift; ++s) {
       if (!active[s]) continue;
-      // line 9: beta^(s)_k = (1 + (sigma_s - sigma_0) alpha_k + coupling (1 - beta^(s)_{k-1}) rho_{k-1}^dagger)^-1
+      // beta^(s)_k = (1 + (sigma_s - sigma_0) alpha_k + coupling (1 - beta^(s)_{k-1}) rho_{k-1}^dagger)^-1
       Mat t = add(eye(n), scale(alpha_k, shifts[s] - s0, n), n);
       t = add(t, mul(mul(coupling, add(eye(n), beta_s[s], n, -1.0), n), adj(rho, n), n), n);
       Mat beta_k = inv(t, n, ok);
       if (!ok) { status = 3; break; }
-      // line 10: alpha^(s)_k = beta^(s)_k coupling alpha^(s)_{k-1}
+      // alpha^(s)_k = beta^(s)_k coupling alpha^(s)_{k-1}
       Mat alpha_sk = mul(mul(beta_k, coupling, n), alpha_s[s], n);
       cd *Ps = P.data() + s * len;
       cd *Xs = X + s * len;
-      // line 11: X^(s) += P^(s) alpha^(s)_k
+      // shifted solution: X^(s) += P^(s) alpha^(s)_k
       block_axpy(Xs, Xs, 1.0, Ps, alpha_sk, rows, n);
-      // line 12: P^(s) = Q_k + P^(s) beta^(s)_k rho_k^dagger
+      // shifted search block: P^(s) = Q_k + P^(s) beta^(s)_k rho_k^dagger
       block_axpy(Ps, nullptr, 1.0, Ps, mul(beta_k, adj(rho_k, n), n), rows, n);
       for (long q = 0; q < len; ++q) Ps[q] += Q[q];
       beta_s[s] = beta_k;

@@ -2,13 +2,15 @@
 //
 // rhmc_block_multishift_cg runs SBCGrQ (Algorithm 1) for all right-hand sides
 // and shifts at once.  Per iteration k (device work only, no host round trip):
-//   AP = (A + sigma_0) P^(0)                      two hops, axpy fused   (line 4)
-//   Gram1 = P^(0)dagger AP -> alpha_k            gram + n x n kernel     (line 4)
-//   W = Q_{k-1} - AP alpha_k                      block axpy             (line 5)
+//   AP = (A + sigma_0) P^(0)                      two hops, axpy fused   (alpha_k step)
+//   Gram1 = P^(0)dagger AP -> alpha_k            gram + n x n kernel     (alpha_k step)
+//   W = Q_{k-1} - AP alpha_k                      block axpy             (block QR)
 //   Gram2 = W^dagger W -> rho_k (Cholesky QR), base and shifted
-//   coefficients                                  gram + n x n kernels   (lines 5-10)
+//   coefficients                                  gram + n x n kernels   (block QR, delta_k,
+//                                                                         beta^(s)_k, alpha^(s)_k)
 //   Q_k = W rho_k^-1; for every live shift
-//   X^(s) += P^(s) M1^(s), P^(s) = Q_k + P^(s) M2^(s)   one fused pass   (lines 6-7, 11-12)
+//   X^(s) += P^(s) M1^(s), P^(s) = Q_k + P^(s) M2^(s)   one fused pass   (base and shifted
+//                                                                         updates)
 // The host reads the residual estimates every few iterations to decide on
 // convergence (and, in mixed precision, on reliable updates).
 //
@@ -722,7 +724,7 @@ static rhmc_status_t solve_phase1(rhmc_ctx *c, const double2 *B, int n, int ns, 
   RHMC_CUDA_TRY(cudaMemcpyAsync(b.st->sigma, shifts, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
   // accumulating solve: X^(0) and one field for sum_{s>=1} w_s X^(s)
   RHMC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * len * (b.accumulate ? std::min(ns, 2) : ns), s));
-  // line 2: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
+  // initialisation: {Q_0, delta_0} = qr(B) (FP64 Gram), P^(s) = Q_0
   if (mixed) {
     // the FP32 basis only needs FP32 orthonormality: QR of the rounded block
     RHMC_TRY((convert<double, float>(B, (float2 *)b.W, len, s)));

@@ -1,6 +1,6 @@
 // Stored-basis assembly of the shifted solutions (mixed precision).
 //
-// Algorithm 1, lines 11-12, for a shift s: X^(s) += P^(s) alpha^(s)_k and
+// Algorithm 1's shifted updates for a shift s: X^(s) += P^(s) alpha^(s)_k and
 // P^(s) = Q_k + P^(s) M2_k, M2_k = beta^(s)_k rho_k^dagger, starting from
 // P^(s)_0 = Q_0, X^(s) = 0.  Unrolled, P^(s)_k = sum_{i <= k} Q_i D_{i,k}
 // with D_{k,k} = 1, D_{i,k} = M2_{i+1} ... M2_k, and after the shift's last

@@ -3,12 +3,12 @@
 // over rows with an n x n coefficient matrix held in shared memory.
 //
 //   gram        G = A^dagger B (n x n), per-CTA partial sums in FP64
-//               (lines 4-5: P^dagger (A + sigma_0) P and the Cholesky-QR Gram W^dagger W)
-//   block_axpy  Y = C + A M (line 5: W = Q - (A + sigma_0) P alpha; also Q = R rho^-1)
+//               (P^dagger (A + sigma_0) P of the alpha_k step, the Cholesky-QR Gram W^dagger W)
+//   block_axpy  Y = C + A M (block QR: W = Q - (A + sigma_0) P alpha; also Q = R rho^-1)
 //   update_all  Q = W rho^-1, then for every shift still being updated
 //               X^(s) += P^(s) M1^(s),  P^(s) = Q + P^(s) M2^(s)
-//               (lines 6-7 for s = 0 with M1 = alpha_k delta_{k-1}, M2 = rho_k^dagger;
-//                lines 11-12 with M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger)
+//               (base updates for s = 0 with M1 = alpha_k delta_{k-1}, M2 = rho_k^dagger;
+//                shifted updates with M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger)
 //   flush       X64 += X32, X32 = 0 (mixed precision reliable-update flush)
 #include <algorithm>
 
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256) k_update_all(const C<T> *__restrict__ W, 
 }
 
 // ------------------------------------------------------------ shifted updates, column owners
-// FP32 shifted updates of Algorithm 1 lines 11-12 for every live shift:
+// FP32 shifted updates of Algorithm 1 for every live shift:
 //   X^(s) += P^(s) M1^(s),   P^(s) = Q + P^(s) M2^(s)
 // (M1 = alpha^(s)_k, M2 = beta^(s)_k rho_k^dagger).  Each warp owns tiles of
 // R rows; lane l < 2N owns output column j = l mod N of M1 (l < N) or M2
@@ -747,9 +747,9 @@ static rhmc_status_t launch_update_cols_variant(const float2 *Q, float2 *P, floa
 // ------------------------------------------------------------ fused base step
 // The base system's updates of Algorithm 1 after rho_k, in one pass over the
 // rows (FP32, column-owner lanes, packed FP32x2 FMAs):
-//   Q_k = W rho_k^-1                                  (line 5)
-//   X^(0) += P^(0) M1,  M1 = alpha_k delta_{k-1}       (line 6)
-//   P^(0) = Q_k + P^(0) M2,  M2 = rho_k^dagger         (line 7)
+//   Q_k = W rho_k^-1                                  (block QR)
+//   X^(0) += P^(0) M1,  M1 = alpha_k delta_{k-1}       (base solution)
+//   P^(0) = Q_k + P^(0) M2,  M2 = rho_k^dagger         (base search block)
 // and, in the stored-basis mode, Q_k into block kb of the basis.  coef holds
 // rho^-1, M1, M2 (n x n each).  Each warp stages a tile of R rows of W, P^(0)
 // and X^(0) by cp.async; pass 1: lane j < n forms column j of Q (stored to Q
@@ -973,7 +973,7 @@ static rhmc_status_t update_shifts_cols_range(const float2 *Q, float2 *P, float2
 }
 
 // ------------------------------------------------------------ Y = C + A M, column owners
-// FP32 tall-skinny update (Algorithm 1 line 5, W = Q - (AP) alpha, and
+// FP32 tall-skinny update (Algorithm 1's block QR step, W = Q - (AP) alpha, and
 // Q = W rho^-1): lane l < 2N owns column j = l mod N of M (kept in registers)
 // for rows of parity l / N of each row pair; the warp's tiles of R rows of A
 // and C are staged by cp.async two tiles deep; every lane reads the A row as
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(W * 32, PK ? 1 : 2) k_axpy_cols(const float2 *
   cpa_wait<0>();
 }
 
-// Y = C + A M fused with the Gram G = Y^dagger Y (the thin-QR Gram of line 5):
+// Y = C + A M fused with the Gram G = Y^dagger Y (the thin-QR Gram of the block QR step):
 // after a row pair of Y is formed, it is written to the warp's row buffer and
 // lane (h, j) adds conj(Y[r][i]) Y[r][j] for all i to its FP32 column of G;
 // the columns are combined across the row parities, the warps (FP64, shared

@@ -80,7 +80,7 @@ rhmc_status_t axpy_gram_cols(const float2 *A, const float2 *C, const float2 *M, 
 // (coef: rho^-1, M1, M2), and Q into basis block *kdev when basis is given (capacity cap)
 rhmc_status_t base_step(const float2 *W, float2 *Q, float2 *P, float2 *X, const float2 *coef, float2 *basis, int cap,
                         const int *kdev, long rows, int n, cudaStream_t s);
-// FP32 shifted updates (lines 11-12) with column-owner lanes and cp.async-staged row tiles
+// FP32 shifted updates (Algorithm 1) with column-owner lanes and cp.async-staged row tiles
 rhmc_status_t update_shifts_cols(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,
                                  int s_begin, int s_end, long rows, int n, long fstride, cudaStream_t s);
 rhmc_status_t update_shifts_tc(const float2 *Q, float2 *P, float2 *X, const float2 *coef, const int *upd,

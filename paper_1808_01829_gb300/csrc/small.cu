@@ -12,12 +12,14 @@
 // k are written to slot k % 3 and those of k-1 read from slot (k-1) % 3, so a
 // launch never overwrites what a launch still running on the other stream reads.
 //
-//   qr_init   {Q_0, delta_0} = qr(B) by Cholesky of B^dagger B   (line 2)
-//   alpha     alpha_k = (P^dagger (A + sigma_0) P)^-1            (line 4)
-//   rho       rho_k from the Cholesky of W^dagger W (thin QR),     (lines 5-8)
-//             base coefficients alpha_k delta_{k-1}, rho_k^dagger, delta_k
-//   shifts    beta^(s)_k, alpha^(s)_k and the coefficients of      (lines 9-12)
-//             lines 11-12, one CTA per shift; shifted residual
+//   qr_init   {Q_0, delta_0} = qr(B) by Cholesky of B^dagger B   (initialisation)
+//   alpha     alpha_k = (P^dagger (A + sigma_0) P)^-1            (alpha_k step)
+//   rho       rho_k from the Cholesky of W^dagger W (thin QR),     (block QR, base updates,
+//             base coefficients alpha_k delta_{k-1}, rho_k^dagger,  delta_k)
+//             delta_k
+//   shifts    beta^(s)_k, alpha^(s)_k and the coefficients of      (shifted coefficients
+//             the shifted updates, one CTA per shift; shifted       and updates)
+//             residual
 //             delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (Sec. III), freezing
 //   reliable  delta_k replaced by the R factor of the true residual
 #include "common.cuh"
@@ -415,7 +417,7 @@ __device__ void colnorms_upper(int n, const double2 *M, double *out, const doubl
 
 // ------------------------------------------------------------ kernels
 
-// line 2: {Q_0, delta_0} = qr(B): delta_0 = R of the Cholesky QR of B^dagger B;
+// initialisation: {Q_0, delta_0} = qr(B): delta_0 = R of the Cholesky QR of B^dagger B;
 // writes delta_0^-1 (for Q_0 = B delta_0^-1) and initialises the state.
 template <typename T>
 __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int nparts, int n, int nshift,
@@ -463,9 +465,9 @@ __global__ void __launch_bounds__(256) k_qr_init(const double2 *partial, int npa
   }
 }
 
-// line 4: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P (Hermitian part),
+// alpha_k step: alpha_k = Gram1^-1, Gram1 = P^dagger (A + sigma_0) P (Hermitian part),
 // from Gram1 = L D L^dagger: alpha = L^-dagger D^-1 L^-1, only i <= j formed;
-// also -alpha for line 5.
+// also -alpha for the block QR step.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int nparts, int n, SolverState *st, int k,
                                                    C<T> *mw_out) {
@@ -511,9 +513,10 @@ __global__ void __launch_bounds__(256) k_nxn_alpha(const double2 *partial, int n
   }
 }
 
-// lines 5-8: rho_k = R factor of the Cholesky QR of W^dagger W; base coefficients
-// rho_k^-1 (Q_k = W rho_k^-1), M1 = alpha_k delta_{k-1} (line 6), M2 = rho_k^dagger
-// (line 7); delta_k = rho_k delta_{k-1} (line 8) and the base column residuals.
+// block QR and base updates: rho_k = R factor of the Cholesky QR of W^dagger W; base
+// coefficients rho_k^-1 (Q_k = W rho_k^-1), M1 = alpha_k delta_{k-1} (base solution),
+// M2 = rho_k^dagger (base search block); delta_k = rho_k delta_{k-1} and the base column
+// residuals.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int nparts, int n, SolverState *st, int k,
                                                  C<T> *coef) {
@@ -570,12 +573,12 @@ __global__ void __launch_bounds__(256) k_nxn_rho(const double2 *partial, int npa
   colnorms_upper(n, Dk, st->res[0], st->inv_d0, nullptr);
   if (t == 0) st->upd[0] = 1;
 }
-// lines 9-12 for shift s = blockIdx.x + 1.  With C = alpha_k rho_{k-1} alpha_{k-1}^-1
-// and M2_prev = beta^(s)_{k-1} rho_{k-1}^dagger (kept in FP64 from the last update):
+// shifted coefficients and updates for shift s = blockIdx.x + 1.  With
+// C = alpha_k rho_{k-1} alpha_{k-1}^-1 and M2_prev = beta^(s)_{k-1} rho_{k-1}^dagger (kept in FP64 from the last update):
 //   T = 1 + dsig alpha_k + C (1 - beta^(s)_{k-1}) rho_{k-1}^dagger
-//     = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,      beta^(s)_k = T^-1   (line 9)
-//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                                      (line 10)
-//   M1 = alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12),
+//     = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,      beta^(s)_k = T^-1
+//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}
+//   M1 = alpha^(s)_k (shifted solution), M2 = beta^(s)_k rho_k^dagger (shifted search block),
 //   delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (the shifted residual).
 // Nine n x n products and one inverse per shift.
 template <typename T>

@@ -1,5 +1,6 @@
-// Base-system n x n coefficient steps of SBCGrQ (Algorithm 1, line 4 and
-// lines 5-8) in double-float arithmetic for the mixed-precision solve.
+// Base-system n x n coefficient steps of SBCGrQ (Algorithm 1: the alpha_k step,
+// the block QR, the base updates and delta_k) in double-float arithmetic for the
+// mixed-precision solve, and its shifted coefficient step.
 //
 // The FP64 kernels of small.cu are bound by the FP64 unit: on this GPU a warp
 // FP64 instruction holds its sub-partition's FP64 pipe for about 64 cycles, so
@@ -300,9 +301,9 @@ __device__ bool inv_general_dd(int n, cd *Ai, cd *A, int *piv, int *flag) {
 }
 }  // namespace
 
-// line 4: alpha_k = Gram1^-1 (Hermitian part of Gram1 = P^dagger (A + sigma_0) P)
+// alpha_k step: alpha_k = Gram1^-1 (Hermitian part of Gram1 = P^dagger (A + sigma_0) P)
 // = L^-dagger D^-1 L^-1; FP64 alpha_k and Gram1_k into the state, -alpha_k (FP32)
-// for line 5.  Thread t owns entry (t / 16, t % 16) throughout.
+// for the block QR step.  Thread t owns entry (t / 16, t % 16) throughout.
 __global__ void __launch_bounds__(256) k_nxn_alpha_dd(const double2 *G, int n, SolverState *st, int k,
                                                       float2 *mw_out) {
   __shared__ cd A[kNN], Li[kNN], S[kNN];
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(256) k_nxn_alpha_dd(const double2 *G, int n, S
   if (in) st->G1[cur][i * n + j] = to_z(h0);  // Gram1_k (Hermitian part) for the shifted step
 }
 
-// lines 5-8: rho_k = R = D^1/2 L^dagger of the LDL^dagger of W^dagger W (thin QR);
+// block QR and base updates: rho_k = R = D^1/2 L^dagger of the LDL^dagger of W^dagger W (thin QR);
 // coef = [rho_k^-1, M1 = alpha_k delta_{k-1}, rho_k^dagger] (FP32); FP64 rho_k,
 // delta_k = rho_k delta_{k-1} and the base column residuals into the state.
 // Thread t owns entry (t / 16, t % 16) throughout.
@@ -413,12 +414,12 @@ __global__ void __launch_bounds__(256) k_nxn_rho_dd(const double2 *G, int n, Sol
   if (t == 0) st->upd[0] = 1;
 }
 
-// lines 9-12 for shift s = blockIdx.x + 1 (the FP64 k_nxn_shifts of small.cu in
+// shifted coefficients and updates for shift s = blockIdx.x + 1 (the FP64 k_nxn_shifts of small.cu in
 // double-float).  With C = alpha_k rho_{k-1} alpha_{k-1}^-1 (alpha_{k-1}^-1 = Gram1_{k-1})
 // and M2_prev = beta^(s)_{k-1} rho_{k-1}^dagger:
-//   T = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,   beta^(s)_k = T^-1   (line 9)
-//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}                                   (line 10)
-//   M1 = w_s alpha^(s)_k (line 11), M2 = beta^(s)_k rho_k^dagger (line 12),
+//   T = 1 + dsig alpha_k + C rho_{k-1}^dagger - C M2_prev,   beta^(s)_k = T^-1
+//   alpha^(s)_k = beta^(s)_k C alpha^(s)_{k-1}
+//   M1 = w_s alpha^(s)_k (shifted solution), M2 = beta^(s)_k rho_k^dagger (shifted search block),
 //   delta^(s)_k = rho_k alpha_k^-1 alpha^(s)_k (the shifted residual), freezing.
 // The recursion state (alpha^(s), M2_prev, the basis history) stays FP64 in memory.
 __global__ void __launch_bounds__(256) k_nxn_shifts_dd(int n, int nshift, SolverState *st, int k, float2 *coef,

@@ -1,6 +1,6 @@
 // Shifted updates of SBCGrQ on the 5th-generation tensor cores (tcgen05).
 //
-// Algorithm 1, lines 11-12, for every shift updated in this iteration:
+// Algorithm 1's shifted updates for every shift updated in this iteration:
 //   X^(s) += P^(s) alpha^(s)_k,   P^(s) = Q_k + P^(s) beta^(s)_k rho_k^dagger.
 // Per 128-row tile of P^(s) (n = 16 complex = 32 reals per row) this is one
 // real GEMM  D[128 x 64] = P[128 x 32] * B[32 x 64]  with B the real embedding

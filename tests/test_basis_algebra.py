@@ -1,5 +1,5 @@
 """The expansion behind the stored-basis assembly of the shifted solutions
-(Algorithm 1, lines 11-12), checked in FP64 on random blocks: running the
+(Algorithm 1's shifted updates), checked in FP64 on random blocks: running the
 recurrences
     X^(s) += P^(s) alpha_k,   P^(s) = Q_k + P^(s) M2_k      (k = 1 .. L, P^(s)_0 = Q_0)
 gives the same X^(s) and P^(s) as the sums over the stored blocks
